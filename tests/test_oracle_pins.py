@@ -1,0 +1,357 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed
+forms, brute force, textbook identities, library routines, invariants and
+the worked example the paper prints (Fig. arrowhead_matrices).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+from scipy import stats
+
+from synth import build, config_model, fd_stencil
+from oracle import bta, dense, fd, scalar
+from oracle import model as M
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small(n_t=3, nx=4, n_b=2, m=150, lik="gaussian", seed=0):
+    return build("small", n_t, nx, n_b, m, lik, seed=seed)
+
+
+def read_patterns(path):
+    pats, name, rows = {}, None, []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if set(line) <= set("x."):
+            rows.append([c == "x" for c in line])
+        else:
+            if name:
+                pats[name] = np.array(rows)
+            name, rows = line, []
+    pats[name] = np.array(rows)
+    return pats
+
+
+def random_spd_with_pattern(pattern, rng):
+    n = pattern.shape[0]
+    Q = np.where(pattern, rng.uniform(-1, 1, (n, n)), 0.0)
+    Q = np.tril(Q) + np.tril(Q, -1).T
+    np.fill_diagonal(Q, 0.0)
+    Q += np.diag(np.abs(Q).sum(1) + 1.0)       # strictly diagonally dominant
+    return Q
+
+
+# ---------------------------------------------------------------- Fig. arrowhead
+
+def test_arrowhead_fill_matches_paper_figure():
+    pats = read_patterns(os.path.join(GOLDEN, "arrowhead_fill.txt"))
+    rng = np.random.default_rng(1)
+    for q, l in (("Q1", "L1"), ("Q2", "L2")):
+        Q = random_spd_with_pattern(pats[q], rng)
+        assert np.array_equal(Q != 0, pats[q])
+        assert np.array_equal(scalar.fill_pattern(Q), pats[l])
+        assert np.array_equal(np.linalg.cholesky(Q) != 0, pats[l])
+
+
+def test_bta_pattern_has_no_fill_with_arrow_last():
+    mdl = small(n_t=3, nx=3, n_b=2, m=80)
+    A = M.obs_matrix(mdl)
+    Qc = (M.prior_Q(mdl, mdl.theta_true) + math.exp(1.0) * (A.T @ A)).toarray()
+    blocks, outside = bta.from_sparse(sp.csr_matrix(Qc), mdl.n_t, mdl.n_s, mdl.n_b)
+    assert outside == 0
+    L = np.linalg.cholesky(Qc)
+    Lb, out_L = bta.from_sparse(sp.csr_matrix(np.where(np.abs(L) > 0, L, 0.0) + np.tril(L, -1).T),
+                                mdl.n_t, mdl.n_s, mdl.n_b)
+    assert out_L == 0
+    # arrow first: the fixed effects couple every block, the factor fills in
+    n, nb = mdl.n, mdl.n_b
+    perm = np.r_[np.arange(n - nb, n), np.arange(n - nb)]
+    Lf = np.linalg.cholesky(Qc[np.ix_(perm, perm)])
+    lower = np.tril(np.ones((n, n), bool))
+    assert np.count_nonzero(Lf[lower] == 0.0) < 0.01 * lower.sum()
+
+
+# ---------------------------------------------------------------- model pieces
+
+def test_ar1_precision_inverts_to_geometric_correlation():
+    for n_t, rho in ((1, 0.3), (2, 0.5), (7, 0.82)):
+        Qt = M.temporal_Q(n_t, rho).toarray()
+        i = np.arange(n_t)
+        R = rho ** np.abs(i[:, None] - i[None, :])
+        assert np.allclose(np.linalg.inv(Qt), R, rtol=1e-12, atol=1e-12)
+        assert np.isclose(np.linalg.slogdet(Qt)[1], -(n_t - 1) * math.log(1 - rho * rho), atol=1e-12)
+
+
+def test_spatial_precision_coefficients():
+    mdl = small(nx=6)
+    th = np.array([0.0, -0.7, 0.3, 0.0])
+    h = M.hyper(th)
+    Qs = M.spatial_Q(mdl, th).toarray()
+    C, G = (x.toarray() for x in M.fem_matrices(mdl))
+    # G 1 = 0, so Q_s 1 = tau^2 kappa^4 C 1 and the total is kappa^2 / (4 pi sigma^2)
+    assert np.isclose(Qs.sum(), h["kappa"] ** 2 / (4 * math.pi * h["sigma"] ** 2), rtol=1e-11)
+    # factored form (kappa^2 C + G) C^-1 (kappa^2 C + G) of the alpha = 2 operator
+    K = h["kappa"] ** 2 * C + G
+    assert np.allclose(Qs, h["tau2"] * K @ np.linalg.inv(C) @ K, rtol=1e-11, atol=1e-9)
+
+
+def test_spde_marginal_variance_is_sigma_squared_in_interior():
+    # Matern nu = 1 in 2-D: marginal variance 1/(4 pi kappa^2 tau^2) = sigma^2
+    mdl = build("fine", 1, 41, 0, 10)
+    sigma = 1.3
+    th = np.array([0.0, math.log(0.25), math.log(sigma), 0.0])
+    v = np.diag(np.linalg.inv(M.spatial_Q(mdl, th).toarray())).reshape(41, 41)
+    assert abs(v[20, 20] / sigma ** 2 - 1.0) < 0.12
+
+
+def test_log_prior_and_poisson_loglik_match_scipy():
+    mdl = small(lik="poisson")
+    th = np.array([-6.0, -1.2, 0.4, 2.0])
+    ref = stats.norm.logpdf(th, mdl.prior_mean, mdl.prior_sd).sum()
+    assert np.isclose(M.log_prior(mdl, th), ref, rtol=1e-14)
+    eta = np.linspace(-1, 1, mdl.m)
+    ref = stats.poisson.logpmf(mdl.y, mdl.E * np.exp(eta)).sum()
+    assert np.isclose(M.poisson_loglik(mdl, eta), ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("lik", ["gaussian", "poisson"])
+def test_dQ_matches_finite_difference_of_Q(lik):
+    mdl = small(lik=lik)
+    th = mdl.theta_true + np.array([0.1, 0.05, -0.1, 0.2])
+    eps = 1e-5
+    for j in range(4):
+        e = np.zeros(4); e[j] = eps
+        num = (M.prior_Q(mdl, th + e) - M.prior_Q(mdl, th - e)).toarray() / (2 * eps)
+        ana = M.dQ_dtheta(mdl, th, j).toarray()
+        assert np.allclose(ana, num, rtol=1e-7, atol=1e-7 * np.abs(num).max() + 1e-12)
+
+
+# ---------------------------------------------------------------- Sec. 2.4 log-det, solves
+
+def test_logdet_three_ways_on_tiny_matrix():
+    mdl = small(n_t=2, nx=3, n_b=1, m=40)
+    A = M.obs_matrix(mdl)
+    Qc = (M.prior_Q(mdl, mdl.theta_true) + 2.0 * (A.T @ A)).toarray()
+    _, ld_chol = dense.chol_logdet(Qc)
+    lu, piv = sla.lu_factor(Qc)
+    ld_lu = float(np.sum(np.log(np.abs(np.diag(lu)))))
+    ld_eig = float(np.sum(np.log(np.linalg.eigvalsh(Qc))))
+    ld_el = 2 * float(np.sum(np.log(np.diag(scalar.cholesky(Qc)))))
+    for v in (ld_lu, ld_eig, ld_el):
+        assert np.isclose(ld_chol, v, rtol=1e-12, atol=1e-10)
+
+
+def test_bta_factor_equals_dense_factor():
+    mdl = small(n_t=3, nx=3, n_b=2, m=90)
+    A = M.obs_matrix(mdl)
+    Qc = (M.prior_Q(mdl, mdl.theta_true) + 3.0 * (A.T @ A)).tocsr()
+    blocks, _ = bta.from_sparse(Qc, mdl.n_t, mdl.n_s, mdl.n_b)
+    Lb, ld = bta.cholesky(blocks)
+    L = scalar.cholesky(Qc.toarray())
+    n_s, N = mdl.n_s, mdl.n_t * mdl.n_s
+    for t in range(mdl.n_t):
+        assert np.allclose(Lb.D[t], L[t * n_s:(t + 1) * n_s, t * n_s:(t + 1) * n_s], atol=1e-12)
+        assert np.allclose(Lb.R[t], L[N:, t * n_s:(t + 1) * n_s], atol=1e-12)
+        if t < mdl.n_t - 1:
+            assert np.allclose(Lb.B[t], L[(t + 1) * n_s:(t + 2) * n_s, t * n_s:(t + 1) * n_s], atol=1e-12)
+    assert np.allclose(Lb.T, L[N:, N:], atol=1e-12)
+    assert np.isclose(ld, 2 * np.sum(np.log(np.diag(L))), rtol=1e-13)
+    b = np.random.default_rng(0).normal(size=mdl.n)
+    assert np.allclose(bta.solve(Lb, b), np.linalg.solve(Qc.toarray(), b), rtol=1e-11, atol=1e-11)
+
+
+def test_kronecker_logdet_identity():
+    for n_t, nx, n_b in ((1, 4, 0), (5, 5, 3), (8, 6, 2)):
+        mdl = build("k", n_t, nx, n_b, 20)
+        th = np.array([0.5, -0.8, 0.2, 0.7])
+        h = M.hyper(th)
+        blocks, _ = bta.from_sparse(M.prior_Q(mdl, th), n_t, mdl.n_s, n_b)
+        _, ld = bta.cholesky(blocks)
+        ld_t = -(n_t - 1) * math.log(1 - h["rho"] ** 2)
+        ld_s = np.linalg.slogdet(M.spatial_Q(mdl, th).toarray())[1]
+        assert np.isclose(ld, mdl.n_s * ld_t + n_t * ld_s + n_b * math.log(h["tau_b"]), rtol=1e-12)
+
+
+def test_backward_solve_samples_have_covariance_q_inverse():
+    # Eq. backward_solve: x = L^-T z with Cov(z) = I has Cov(x) = L^-T L^-1 = Q^-1
+    rng = np.random.default_rng(3)
+    Q = random_spd_with_pattern(np.ones((6, 6), bool), rng)
+    L = scalar.cholesky(Q)
+    X = np.column_stack([scalar.backward_solve(L, e) for e in np.eye(6)])
+    assert np.allclose(X @ X.T, np.linalg.inv(Q), rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Sec. 2.4.2 selected inversion
+
+def test_scalar_recursions_equal_dense_inverse_and_each_other():
+    mdl = small(n_t=2, nx=3, n_b=1, m=30)
+    A = M.obs_matrix(mdl)
+    Q = (M.prior_Q(mdl, mdl.theta_true) + (A.T @ A)).toarray()
+    L = scalar.cholesky(Q)
+    inv = np.linalg.inv(Q)
+    S1, S2 = scalar.sel_inv_cov(L), scalar.takahashi(L)
+    assert np.allclose(S1, inv, rtol=1e-11, atol=1e-13)
+    assert np.allclose(S2, inv, rtol=1e-11, atol=1e-13)
+    # selected: only the pattern of L is computed, and it equals the same entries of the inverse
+    P1, P2 = scalar.sel_inv_cov(L, selected=True), scalar.takahashi(L, selected=True)
+    need = np.isfinite(P1)
+    assert np.array_equal(need, np.isfinite(P2))
+    assert np.array_equal(need, (L != 0) | (L.T != 0))
+    assert need.sum() < need.size
+    assert np.allclose(P1[need], inv[need], rtol=1e-11, atol=1e-13)
+    assert np.allclose(P2[need], inv[need], rtol=1e-11, atol=1e-13)
+
+
+def test_block_selinv_equals_dense_inverse_on_pattern():
+    mdl = small(n_t=4, nx=3, n_b=2, m=100)
+    A = M.obs_matrix(mdl)
+    Qc = (M.prior_Q(mdl, mdl.theta_true) + 2.7 * (A.T @ A)).tocsr()
+    blocks, _ = bta.from_sparse(Qc, mdl.n_t, mdl.n_s, mdl.n_b)
+    Lb, _ = bta.cholesky(blocks)
+    S = bta.selinv(Lb)
+    inv = np.linalg.inv(Qc.toarray())
+    Sinv, _ = bta.from_sparse(sp.csr_matrix(inv), mdl.n_t, mdl.n_s, mdl.n_b)
+    for t in range(mdl.n_t):
+        assert np.allclose(S.D[t], Sinv.D[t], rtol=1e-11, atol=1e-14)
+        assert np.allclose(S.R[t], Sinv.R[t], rtol=1e-11, atol=1e-14)
+        if t < mdl.n_t - 1:
+            assert np.allclose(S.B[t], Sinv.B[t], rtol=1e-11, atol=1e-14)
+    assert np.allclose(S.T, Sinv.T, rtol=1e-11)
+    # Q Sigma = I read on the pattern: (Q_c Sigma_full)_ij = delta_ij there, and the
+    # selected values are those of Sigma_full
+    QS = Qc.toarray() @ inv
+    pat = np.abs(Qc.toarray()) > 0
+    assert np.allclose(QS[pat], np.eye(mdl.n)[pat], atol=1e-10)
+    # tip: inverse of the Schur complement of the latent block
+    N = mdl.n_t * mdl.n_s
+    Qd = Qc.toarray()
+    schur = Qd[N:, N:] - Qd[N:, :N] @ np.linalg.solve(Qd[:N, :N], Qd[:N, N:])
+    assert np.allclose(S.T, np.linalg.inv(schur), rtol=1e-10)
+
+
+def test_prior_marginal_variances_are_kronecker():
+    mdl = build("k", 4, 4, 2, 20)
+    th = np.array([0.0, -0.5, 0.1, 0.4])
+    h = M.hyper(th)
+    blocks, _ = bta.from_sparse(M.prior_Q(mdl, th), 4, mdl.n_s, 2)
+    Lb, _ = bta.cholesky(blocks)
+    v = bta.diag_of(bta.selinv(Lb))
+    vt = np.diag(np.linalg.inv(M.temporal_Q(4, h["rho"]).toarray()))
+    vs = np.diag(np.linalg.inv(M.spatial_Q(mdl, th).toarray()))
+    assert np.allclose(v[:-2], np.kron(vt, vs), rtol=1e-11)
+    assert np.allclose(v[-2:], 1.0 / h["tau_b"], rtol=1e-12)
+
+
+def test_prior_trace_closed_forms():
+    mdl = build("k", 5, 4, 2, 20)
+    th = np.array([0.0, -0.5, 0.1, 0.9])
+    h = M.hyper(th)
+    rho = h["rho"]
+    blocks, _ = bta.from_sparse(M.prior_Q(mdl, th), 5, mdl.n_s, 2)
+    Lb, _ = bta.cholesky(blocks)
+    S = bta.selinv(Lb)
+    tr = lambda j: bta.contract(S, bta.from_sparse(M.dQ_dtheta(mdl, th, j), 5, mdl.n_s, 2)[0])
+    assert np.isclose(tr(2), -2.0 * mdl.n_t * mdl.n_s, rtol=1e-11)
+    expect = mdl.n_s * rho * (1 - rho) * 2 * (mdl.n_t - 1) * rho / (1 - rho * rho)
+    assert np.isclose(tr(3), expect, rtol=1e-11)
+
+
+# ---------------------------------------------------------------- f(theta), Eq. post_theta_approx
+
+def test_gaussian_f_equals_closed_form_marginal_likelihood_config1():
+    mdl = config_model(1)
+    th = mdl.theta_true
+    cf = dense.gaussian_closed_form(mdl, th)
+    d = dense.gaussian_eval(mdl, th, want_var=False)
+    b = bta.gaussian(mdl, th)
+    assert abs(d["f"] - cf) / abs(cf) < 1e-11
+    assert abs(b["f"] - cf) / abs(cf) < 1e-11
+    A = M.obs_matrix(mdl)
+    tau_y = math.exp(th[0])
+    Qc = M.prior_Q(mdl, th) + tau_y * (A.T @ A)
+    rhs = tau_y * (A.T @ mdl.y)
+    assert np.linalg.norm(Qc @ b["x"] - rhs) / np.linalg.norm(rhs) < 1e-13
+
+
+def test_gaussian_bta_matches_dense_definition():
+    mdl = small(n_t=4, nx=4, n_b=3, m=300)
+    th = mdl.theta_true + np.array([-0.2, 0.1, 0.05, -0.3])
+    d = dense.gaussian_eval(mdl, th)
+    b = bta.gaussian(mdl, th, want_var=True)
+    assert abs(d["f"] - b["f"]) < 1e-11 * abs(d["f"])
+    assert np.allclose(d["x"], b["x"], rtol=1e-11, atol=1e-12 * np.abs(d["x"]).max())
+    assert np.allclose(d["var"], b["var"], rtol=1e-11)
+
+
+@pytest.mark.parametrize("lik", ["gaussian", "poisson"])
+def test_adjoint_gradient_matches_central_differences(lik):
+    mdl = small(n_t=3, nx=4, n_b=2, m=200, lik=lik)
+    th = mdl.theta_true + np.array([0.1, -0.1, 0.05, 0.2])
+    g = bta.evaluate(mdl, th, want_grad=True)["grad"]
+    f = lambda t: bta.evaluate(mdl, t)["f"]
+    errs = []
+    for eps in (1e-2, 1e-3):
+        errs.append(np.abs(fd.central_gradient(f, th, eps) - g).max())
+    assert errs[-1] < 1e-5 * max(1.0, np.abs(g).max())
+    assert errs[1] < errs[0] / 20.0          # O(eps^2) until round-off
+
+
+def test_fd_stencil_layout_and_gradient():
+    th = np.array([0.3, -0.2, 0.1, 1.0])
+    pts = fd_stencil(th, 1e-3)
+    quad = lambda t: float(t @ np.diag([1.0, 2.0, 3.0, 4.0]) @ t + t.sum())
+    g = fd.gradient_from_stencil([quad(p) for p in pts], 1e-3)
+    assert np.allclose(g, 2 * np.array([1.0, 2.0, 3.0, 4.0]) * th + 1.0, rtol=1e-9)
+
+
+# ---------------------------------------------------------------- Poisson (Laplace, Sec. 2.2)
+
+def test_poisson_mode_is_stationary_and_matches_dense_newton():
+    mdl = small(n_t=3, nx=4, n_b=2, m=250, lik="poisson")
+    th = mdl.theta_true + np.array([0.5, 0.0, 0.1, 0.0])
+    b = bta.poisson(mdl, th, want_var=True)
+    d = dense.poisson_eval(mdl, th)
+    A = M.obs_matrix(mdl)
+    Q = M.prior_Q(mdl, th)
+    grad = Q @ b["x"] - A.T @ (mdl.y - mdl.E * np.exp(A @ b["x"]))
+    assert np.abs(grad).max() < 1e-8 * max(1.0, np.abs(A.T @ mdl.y).max())
+    assert b["converged"] and d["converged"]
+    assert abs(b["f"] - d["f"]) < 1e-11 * abs(d["f"])
+    assert np.allclose(b["x"], d["x"], atol=1e-10)
+    assert np.allclose(b["var"], d["var"], rtol=1e-10)
+
+
+def test_poisson_laplace_matches_generic_laplace_formula():
+    # log p(y|theta) ~ h(x*) + (n/2) log 2 pi - 1/2 log|-h''(x*)|, with
+    # h(x) = log pi(x|theta) + log p(y|x, theta), mode from a generic optimiser
+    from scipy.optimize import minimize
+    mdl = small(n_t=2, nx=3, n_b=1, m=60, lik="poisson")
+    th = mdl.theta_true + np.array([1.0, 0.0, 0.0, 0.0])
+    Q = M.prior_Q(mdl, th).toarray()
+    A = M.obs_matrix(mdl).toarray()
+    n = mdl.n
+    logdetQ = np.linalg.slogdet(Q)[1]
+
+    def h(x):
+        eta = A @ x
+        return (-0.5 * n * math.log(2 * math.pi) + 0.5 * logdetQ - 0.5 * x @ Q @ x
+                + stats.poisson.logpmf(mdl.y, mdl.E * np.exp(eta)).sum())
+
+    def dh(x):
+        return -Q @ x + A.T @ (mdl.y - mdl.E * np.exp(A @ x))
+
+    res = minimize(lambda x: -h(x), np.zeros(n), jac=lambda x: -dh(x), method="BFGS",
+                   options=dict(gtol=1e-11, maxiter=10000))
+    xs = res.x
+    Hn = Q + A.T @ np.diag(mdl.E * np.exp(A @ xs)) @ A
+    laplace = h(xs) + 0.5 * n * math.log(2 * math.pi) - 0.5 * np.linalg.slogdet(Hn)[1]
+    expect_f = -M.log_prior(mdl, th) - laplace
+    assert abs(bta.poisson(mdl, th)["f"] - expect_f) < 1e-7 * abs(expect_f)
