@@ -1,0 +1,199 @@
+/*
+ * inla_gpu.h -- C ABI of the GB300 library for INLA's hyperparameter phase.
+ *
+ * What it computes (Gaedke-Merzhaeuser et al., "Parallelized integrated
+ * nested Laplace approximations for fast Bayesian inference"):
+ *
+ *   For each hyperparameter point theta of a batch, the objective
+ *     f(theta) = -log pi~(theta | y)                          (Sec. 3.1)
+ *   where pi~ is the Laplace approximation of Eq. post_theta_approx,
+ *     pi~(theta|y) = pi(theta) pi(x|theta) pi(y|x,theta) / pi_G(x|theta,y) at x = x*(theta),
+ *   together with its gradient (central differences, Eq. central_diff, or
+ *   an adjoint of the same formula), the latent mode x*(theta) (Sec. 2.2;
+ *   Newton iteration for a Poisson likelihood), and the marginal variances
+ *   diag(Q_c(theta)^-1) by selected inversion (Sec. 2.3, Sec. 2.4.2,
+ *   Eq. sel_inv_cov / Eq. takahashi_recursion).
+ *
+ * The model is the spatio-temporal latent Gaussian model of Sec. 2.1 with
+ *   Q(theta)   = Q_t(rho) (x) Q_s(kappa, tau) (+) tau_b I_{n_b},
+ *   Q_s        = tau^2 (kappa^4 C + 2 kappa^2 G + G C^-1 G)   (SPDE, alpha = 2),
+ *   Q_t        = stationary AR(1) precision, unit marginal variance,
+ *   Q_c(theta) = Q(theta) + A^T D A,  D = tau_y I (Gaussian) or diag(E e^eta) (Poisson),
+ * latent vector ordered time-major with the n_b fixed effects last, so
+ * Q and Q_c are block tridiagonal with an arrowhead (Fig. arrowhead_matrices).
+ * theta = (theta_1..theta_4): Gaussian: (log tau_y, log range, log sigma,
+ * logit rho) with kappa = sqrt(8)/range, tau^2 = 1/(4 pi kappa^2 sigma^2) and
+ * tau_b fixed by the model; Poisson: theta_1 = log tau_b instead of log tau_y.
+ * The prior pi(theta) is a product of independent normals.
+ *
+ * Conventions
+ *   - Every function returns an inla_status; 0 = INLA_OK.  On a non-OK
+ *     return, inla_last_error() gives a message (thread-local).
+ *   - Argument, size and allocation errors are reported synchronously.
+ *     Numerical failures are reported per point in out->status[b]:
+ *     INLA_ERR_NOT_SPD (a pivot block lost positive definiteness),
+ *     INLA_ERR_NO_CONVERGENCE (Newton did not reach the tolerance); such a
+ *     point gets f = +inf and NaN in its other outputs.  Kernels never trap
+ *     and contain no unbounded waits.
+ *   - Pointers named *_dev are device pointers, all others host pointers.
+ *     All floating point is IEEE binary64 ("double"), arrays are dense and
+ *     contiguous (row-major where two-dimensional).
+ *   - A model is not re-entrant: calls on one model must not overlap
+ *     (one stream at a time).  Distinct models are independent.
+ */
+#ifndef INLA_GPU_H
+#define INLA_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  INLA_OK = 0,
+  INLA_ERR_ARG = 1,             /* invalid argument or inconsistent sizes      */
+  INLA_ERR_CUDA = 2,            /* a CUDA runtime call failed                  */
+  INLA_ERR_OOM = 3,             /* device allocation failed                    */
+  INLA_ERR_NOT_SPD = 4,         /* per point: Q or Q_c not positive definite   */
+  INLA_ERR_NO_CONVERGENCE = 5,  /* per point: Newton iteration did not converge */
+  INLA_ERR_UNSUPPORTED = 7      /* option not available in this build          */
+} inla_status;
+
+enum { INLA_LIK_GAUSSIAN = 0, INLA_LIK_POISSON = 1 };
+enum { INLA_GRAD_NONE = 0, INLA_GRAD_FD_CENTRAL = 1, INLA_GRAD_ADJOINT = 2 };
+/* How log|Q| and tr(Q^-1 dQ) of the prior are obtained.  KRONECKER uses
+ * log|Q_t (x) Q_s| = n_s log|Q_t| + n_t log|Q_s| with one dense n_s x n_s
+ * inversion of Q_s; BTA runs the same block factorisation (and selected
+ * inversion, for the gradient) on Q as on Q_c.  Both are exact. */
+enum { INLA_PRIOR_KRONECKER = 0, INLA_PRIOR_BTA = 1 };
+enum { INLA_FP64 = 0 };
+
+/* Model description.  Every pointer is a HOST pointer; the arrays are read
+ * (and copied to the device) by inla_model_create and may be freed after it
+ * returns. */
+typedef struct {
+  int32_t n_t;            /* number of time steps (>= 1)                          */
+  int32_t n_s;            /* number of mesh vertices (>= 1)                       */
+  int32_t n_b;            /* number of fixed effects (>= 0)                       */
+  int32_t lik;            /* INLA_LIK_GAUSSIAN or INLA_LIK_POISSON                */
+  int64_t m;              /* number of observations (>= 1)                        */
+  const double *C_diag;   /* [n_s] lumped mass matrix C (all > 0)                 */
+  const int32_t *G_rowptr;/* [n_s+1] CSR row pointers of the stiffness matrix G   */
+  const int32_t *G_col;   /* [nnz(G)] column indices (symmetric pattern)          */
+  const double *G_val;    /* [nnz(G)] values                                       */
+  const int64_t *A_rowptr;/* [m+1] CSR row pointers of A (m x n, n = n_t n_s + n_b)*/
+  const int32_t *A_col;   /* column indices: each row has 1..3 spatial entries in  */
+                          /* one time block [t n_s, (t+1) n_s) and any number of   */
+                          /* fixed-effect entries in [n_t n_s, n)                   */
+  const double *A_val;    /* values                                                */
+  const double *y;        /* [m] observations (Poisson: non-negative integers)     */
+  const double *E;        /* [m] exposures (Poisson, > 0); NULL for Gaussian       */
+  double tau_b;           /* fixed-effect prior precision (Gaussian; > 0)          */
+  double prior_mean[4];   /* hyperprior: theta_j ~ N(prior_mean[j], prior_sd[j]^2) */
+  double prior_sd[4];
+} inla_model_desc;
+
+typedef struct {
+  int32_t grad;           /* INLA_GRAD_NONE / _FD_CENTRAL / _ADJOINT               */
+  int32_t prior_mode;     /* INLA_PRIOR_KRONECKER or INLA_PRIOR_BTA                */
+  int32_t precision;      /* INLA_FP64                                             */
+  int32_t want_mode;      /* nonzero: write x*(theta) to out->x_mode               */
+  int32_t want_marg_var;  /* nonzero: write diag(Q_c^-1) to out->marg_var          */
+  int32_t max_newton;     /* Poisson: iteration limit (<= 0: 50)                   */
+  double newton_tol;      /* Poisson: stop when ||x^{k+1} - x^k||_2 < tol (<= 0: 1e-8) */
+  double fd_eps;          /* central-difference step (<= 0: 1e-3)                  */
+} inla_eval_opts;
+
+/* Outputs of inla_eval_batch: DEVICE pointers owned by the caller.  Layout
+ * is [B] or [B][n] / [B][4] row-major.  x_mode, marg_var, grad and
+ * newton_iters may be NULL when not wanted. */
+typedef struct {
+  double *f_dev;          /* [B]    f(theta_b)                                     */
+  double *grad_dev;       /* [B][4] gradient (needs opts.grad != NONE)             */
+  double *x_mode_dev;     /* [B][n] latent mode x*(theta_b)                        */
+  double *marg_var_dev;   /* [B][n] diag(Q_c(theta_b)^-1), latent order            */
+  int32_t *status_dev;    /* [B]    per-point inla_status (required)               */
+  int32_t *newton_iters_dev; /* [B] Newton iterations (Poisson), 0 for Gaussian     */
+} inla_eval_out;
+
+/* Host-buffer twin of inla_eval_out (all HOST pointers, same layout). */
+typedef struct {
+  double *f;
+  double *grad;
+  double *x_mode;
+  double *marg_var;
+  int32_t *status;
+  int32_t *newton_iters;
+} inla_eval_out_host;
+
+typedef struct inla_model inla_model;
+
+/* Build a model on CUDA device `device`: validates the description, sorts
+ * the observations by time, builds the index structures on the host and
+ * computes every theta-free value (G C^-1 G, A^T A, A^T y, ...) with device
+ * kernels.  On success *out owns all device memory of the model.
+ * Errors: INLA_ERR_ARG (bad sizes / indices / values), INLA_ERR_OOM,
+ * INLA_ERR_CUDA.  Synchronous. */
+int inla_model_create(const inla_model_desc *desc, int device, inla_model **out);
+
+/* Bytes of device workspace that inla_eval_batch allocates (and keeps in
+ * the model for reuse) for a batch of B points with these options.  FD mode
+ * evaluates B * 9 points.  Errors: INLA_ERR_ARG. */
+int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *opts, size_t *bytes);
+
+/* Evaluate B points.  theta_dev: DEVICE [B][4].  out: DEVICE buffers as
+ * above.  stream: a cudaStream_t (NULL = legacy default stream).  Work is
+ * enqueued on `stream`; the call returns after enqueueing, except for the
+ * Poisson likelihood, whose Newton loop reads a convergence flag back to
+ * the host once per iteration.  The workspace grows on first use (device
+ * allocation), so the first call with a larger B may allocate.
+ * With opts->grad == INLA_GRAD_FD_CENTRAL each point is the centre of a
+ * 2d+1 = 9 point stencil (Eq. central_diff); f, x_mode and marg_var are
+ * those of the centre.  Errors: INLA_ERR_ARG, INLA_ERR_OOM, INLA_ERR_CUDA,
+ * INLA_ERR_UNSUPPORTED; numerical failures go to out->status_dev. */
+int inla_eval_batch(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
+                    const inla_eval_out *out, void *stream);
+
+/* Same as inla_eval_batch with HOST buffers: copies theta to the device,
+ * evaluates on the model's internal stream, copies the results back and
+ * synchronises.  theta: HOST [B][4]. */
+int inla_eval_batch_host(inla_model *model, int B, const double *theta, const inla_eval_opts *opts,
+                         const inla_eval_out_host *out);
+
+/* Latent dimension n = n_t n_s + n_b of a model. */
+int64_t inla_model_latent_dim(const inla_model *model);
+
+/* Number of kernel launches the last inla_eval_batch issued (diagnostics). */
+int64_t inla_last_launch_count(const inla_model *model);
+
+/* Live kernel timing (diagnostics, off by default).  While enabled, the
+ * launches of the kernels below are bracketed by CUDA events on the launch
+ * stream; inla_profile_read synchronises those events and returns, for one
+ * kernel, the summed event time in ms, the number of launches and the
+ * number of algorithmic units processed (a unit is one 64 x 64 x 64 tile
+ * product, 2 * 64^3 flops).  Enabling resets the records.
+ *   kernel 0: rank-64 tile update of the block sweep inversion
+ *   kernel 1: 64 x 64 tile GEMM of the selected inversion
+ *   kernel 2: pivot-block inversion        kernel 3: pivot-panel product */
+int inla_profile_enable(inla_model *model, int enable);
+int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *launches, double *units);
+
+/* Free every device resource of the model.  NULL is allowed. */
+void inla_model_destroy(inla_model *model);
+
+/* Message of the last non-OK return on this thread ("" if none). */
+const char *inla_last_error(void);
+
+/* Measurement utility (no counterpart in the paper): sustained FP64 FMA
+ * throughput of this GPU in TFLOP/s, timed with CUDA events on a
+ * register-resident loop over every SM, so that roofline fractions can be
+ * quoted against a measured FP64 peak.  use_tensor != 0 times the
+ * warp-level double-precision MMA instruction instead of scalar FMA. */
+int inla_measure_fp64_peak(int device, int use_tensor, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INLA_GPU_H */

@@ -1,0 +1,209 @@
+"""Python binding of the C ABI: model construction, batched evaluation and a
+``torch.autograd.Function`` for f(theta).
+
+PyTorch only provides device memory and the stream; the arithmetic runs in
+libinla_gpu.so.  There is no CPU fallback: without the library (or without
+a CUDA device) every call raises.
+"""
+import ctypes
+from ctypes import byref, c_double, c_size_t, c_void_p
+
+import numpy as np
+
+from . import capi as C
+
+_GRAD = {"none": C.INLA_GRAD_NONE, "fd": C.INLA_GRAD_FD_CENTRAL, "adjoint": C.INLA_GRAD_ADJOINT}
+_PRIOR = {"kronecker": C.INLA_PRIOR_KRONECKER, "bta": C.INLA_PRIOR_BTA}
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def make_opts(grad="none", prior="kronecker", want_mode=False, want_marg_var=False, max_newton=50,
+              newton_tol=1e-8, fd_eps=1e-3):
+    o = C.inla_eval_opts()
+    o.grad = _GRAD[grad]
+    o.prior_mode = _PRIOR[prior]
+    o.precision = C.INLA_FP64
+    o.want_mode = int(bool(want_mode))
+    o.want_marg_var = int(bool(want_marg_var))
+    o.max_newton = int(max_newton)
+    o.newton_tol = float(newton_tol)
+    o.fd_eps = float(fd_eps)
+    return o
+
+
+class Model:
+    """A spatio-temporal latent Gaussian model resident on one GPU.
+
+    ``data`` provides n_t, n_s, n_b, m, lik ('gaussian' / 'poisson'), C_diag,
+    G (CSR: G_rowptr, G_col, G_val), A (CSR: A_rowptr int64, A_col, A_val),
+    y, E (Poisson), tau_b, prior_mean[4], prior_sd[4] (e.g. ``synth.GridModel``).
+    """
+
+    def __init__(self, data, device: int = 0):
+        self.lib = C.load()
+        arr = lambda x, dt: np.ascontiguousarray(np.asarray(x, dtype=dt))
+        keep = dict(C=arr(data.C_diag, np.float64), Gr=arr(data.G_rowptr, np.int32), Gc=arr(data.G_col, np.int32),
+                    Gv=arr(data.G_val, np.float64), Ar=arr(data.A_rowptr, np.int64), Ac=arr(data.A_col, np.int32),
+                    Av=arr(data.A_val, np.float64), y=arr(data.y, np.float64))
+        d = C.inla_model_desc()
+        d.n_t, d.n_s, d.n_b, d.m = int(data.n_t), int(data.n_s), int(data.n_b), int(data.m)
+        d.lik = C.INLA_LIK_GAUSSIAN if data.lik == "gaussian" else C.INLA_LIK_POISSON
+        d.C_diag = _ptr(keep["C"], c_double)
+        d.G_rowptr = _ptr(keep["Gr"], ctypes.c_int32)
+        d.G_col = _ptr(keep["Gc"], ctypes.c_int32)
+        d.G_val = _ptr(keep["Gv"], c_double)
+        d.A_rowptr = _ptr(keep["Ar"], ctypes.c_int64)
+        d.A_col = _ptr(keep["Ac"], ctypes.c_int32)
+        d.A_val = _ptr(keep["Av"], c_double)
+        d.y = _ptr(keep["y"], c_double)
+        if getattr(data, "E", None) is not None:
+            keep["E"] = arr(data.E, np.float64)
+            d.E = _ptr(keep["E"], c_double)
+        d.tau_b = float(data.tau_b)
+        for j in range(4):
+            d.prior_mean[j] = float(data.prior_mean[j])
+            d.prior_sd[j] = float(data.prior_sd[j])
+        h = c_void_p()
+        C.check(self.lib.inla_model_create(byref(d), int(device), byref(h)))
+        self.handle = h
+        self.device = int(device)
+        self.n = int(self.lib.inla_model_latent_dim(h))
+        self.n_t, self.n_s, self.n_b, self.m = d.n_t, d.n_s, d.n_b, d.m
+        self.lik = data.lik
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.inla_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, B, **kw):
+        out = c_size_t()
+        o = make_opts(**kw)
+        C.check(self.lib.inla_workspace_bytes(self.handle, int(B), byref(o), byref(out)))
+        return out.value
+
+    def last_launch_count(self):
+        return int(self.lib.inla_last_launch_count(self.handle))
+
+    def profile_enable(self, on=True):
+        C.check(self.lib.inla_profile_enable(self.handle, int(bool(on))))
+
+    def profile_read(self, kernel):
+        """(total_ms, launches, units) of one kernel since profiling was enabled."""
+        ms, n, u = c_double(), ctypes.c_int64(), c_double()
+        C.check(self.lib.inla_profile_read(self.handle, int(kernel), byref(ms), byref(n), byref(u)))
+        return ms.value, n.value, u.value
+
+    def eval(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False, max_newton=50,
+             newton_tol=1e-8, fd_eps=1e-3, stream=None, out=None):
+        """Evaluate a batch on the GPU.  theta: CUDA float64 tensor [B, 4].
+
+        Returns a dict of CUDA tensors: f [B], grad [B, 4] (if requested),
+        x_mode [B, n], marg_var [B, n], status [B] (int32), newton_iters [B].
+        Work is enqueued on ``stream`` (default: torch's current stream).
+        """
+        import torch
+        if not (isinstance(theta, torch.Tensor) and theta.is_cuda and theta.dtype == torch.float64):
+            raise TypeError("theta must be a CUDA float64 tensor")
+        theta = theta.contiguous()
+        B = theta.shape[0]
+        if theta.dim() != 2 or theta.shape[1] != 4:
+            raise ValueError("theta must have shape [B, 4]")
+        dev = theta.device
+        if out is None:
+            out = dict(f=torch.empty(B, dtype=torch.float64, device=dev),
+                       status=torch.empty(B, dtype=torch.int32, device=dev),
+                       newton_iters=torch.empty(B, dtype=torch.int32, device=dev))
+            if grad != "none":
+                out["grad"] = torch.empty(B, 4, dtype=torch.float64, device=dev)
+            if want_mode:
+                out["x_mode"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
+            if want_marg_var:
+                out["marg_var"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps)
+        so = C.inla_eval_out()
+        so.f_dev = out["f"].data_ptr()
+        so.status_dev = out["status"].data_ptr()
+        so.newton_iters_dev = out["newton_iters"].data_ptr()
+        so.grad_dev = out["grad"].data_ptr() if "grad" in out else None
+        so.x_mode_dev = out["x_mode"].data_ptr() if "x_mode" in out else None
+        so.marg_var_dev = out["marg_var"].data_ptr() if "marg_var" in out else None
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        C.check(self.lib.inla_eval_batch(self.handle, int(B), c_void_p(theta.data_ptr()), byref(o), byref(so),
+                                         c_void_p(stream.cuda_stream)))
+        return out
+
+    def eval_host(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False,
+                  max_newton=50, newton_tol=1e-8, fd_eps=1e-3):
+        """Evaluate with HOST numpy buffers (copies in and out inside the call)."""
+        theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 4))
+        B = theta.shape[0]
+        res = dict(f=np.empty(B), status=np.empty(B, np.int32), newton_iters=np.empty(B, np.int32))
+        if grad != "none":
+            res["grad"] = np.empty((B, 4))
+        if want_mode:
+            res["x_mode"] = np.empty((B, self.n))
+        if want_marg_var:
+            res["marg_var"] = np.empty((B, self.n))
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps)
+        so = C.inla_eval_out_host()
+        so.f = res["f"].ctypes.data
+        so.status = res["status"].ctypes.data
+        so.newton_iters = res["newton_iters"].ctypes.data
+        so.grad = res["grad"].ctypes.data if "grad" in res else None
+        so.x_mode = res["x_mode"].ctypes.data if "x_mode" in res else None
+        so.marg_var = res["marg_var"].ctypes.data if "marg_var" in res else None
+        C.check(self.lib.inla_eval_batch_host(self.handle, int(B), theta.ctypes.data, byref(o), byref(so)))
+        return res
+
+
+def measure_fp64_peak(device=0, tensor=False):
+    """Measured FP64 throughput (TFLOP/s) of scalar FMA or the DMMA instruction."""
+    lib = C.load()
+    v = c_double()
+    C.check(lib.inla_measure_fp64_peak(int(device), int(bool(tensor)), byref(v)))
+    return v.value
+
+
+def _make_function():
+    import torch
+
+    class LogPosterior(torch.autograd.Function):
+        """f(theta) = -log pi~(theta|y) for a batch; backward uses the adjoint gradient."""
+
+        @staticmethod
+        def forward(ctx, theta, model, prior="kronecker"):
+            need = ctx.needs_input_grad[0]
+            r = model.eval(theta.detach().contiguous(), grad="adjoint" if need else "none", prior=prior)
+            if need:
+                ctx.save_for_backward(r["grad"])
+            ctx.mark_non_differentiable(r["status"])
+            return r["f"]
+
+        @staticmethod
+        def backward(ctx, gf):
+            (g,) = ctx.saved_tensors
+            return gf[:, None] * g, None, None
+
+    return LogPosterior
+
+
+_LP = None
+
+
+def log_posterior(theta, model, prior="kronecker"):
+    """Differentiable f(theta) for a [B, 4] CUDA float64 tensor."""
+    global _LP
+    if _LP is None:
+        _LP = _make_function()
+    return _LP.apply(theta, model, prior)

@@ -1,0 +1,872 @@
+// C ABI (include/inla_gpu.h): model construction on the host (index
+// structures only; every value is computed by device kernels), workspace
+// management and the orchestration of one batched evaluation.
+//
+// One evaluation of a wave of P points runs, per point (all points of the
+// wave advance together, one kernel launch per step):
+//   1. theta -> model scalars; Q_s(theta) on the sparse pattern.
+//   2. log|Q|: Kronecker form n_s log|Q_t| + n_t log|Q_s| + n_b log tau_b with one
+//      dense inversion of Q_s, or the same block factorisation as Q_c.
+//   3. Block factorisation of Q_c along the time chain (Sec. 2.4): per t the
+//      Schur complement D_t is assembled from the sparse blocks and inverted
+//      (block sweep, log|D_t| from its pivots); the arrow is updated; the tip
+//      D_a is factored last (arrow last: no fill, Fig. arrowhead_matrices).
+//   4. Mode: block forward/backward substitution (Gaussian), or the Newton
+//      iteration of Sec. 2.2 (Poisson) with a factorisation per iteration and
+//      a refactorisation at the mode.
+//   5. f = -log pi~(theta|y) from the log-determinants and quadratic forms
+//      (Eq. post_theta_approx, Sec. 3.1).
+//   6. Selected inversion (block Takahashi recursion, Eq. takahashi_recursion
+//      in block form) for diag(Q_c^-1) and the traces of the adjoint gradient;
+//      Poisson adds one adjoint solve.  Central differences (Eq. central_diff)
+//      instead evaluate 2d+1 points per centre.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "inla_internal.cuh"
+
+using namespace inla;
+
+namespace inla {
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+const char *get_error() { return g_err.c_str(); }
+}  // namespace inla
+
+namespace {
+
+struct ApiError : std::runtime_error {
+  int code;
+  ApiError(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define CUDA_OK(call)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      throw ApiError(e_ == cudaErrorMemoryAllocation ? INLA_ERR_OOM : INLA_ERR_CUDA,                \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+__global__ void point_out_kernel(int P, int per, int *out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  out[p] = (per == 1) ? p : ((p % per == 0) ? p / per : -1);
+}
+
+__global__ void flags_kernel(Work W, int64_t w0, int per, int centre_flags) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= W.P) return;
+  const int64_t g = w0 + b;
+  W.flags[b] = (per == 1 || g % per == 0) ? centre_flags : 0;
+}
+
+__global__ void zero_slot_kernel(Work W, int slot) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < W.P) W.sc[b * SC_COUNT + slot] = 0.0;
+}
+
+}  // namespace
+
+struct inla_model {
+  int device = 0;
+  DevModel M{};
+  std::vector<void *> allocs;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  int ws_points = 0;
+  void *bb = nullptr;
+  size_t bb_bytes = 0;
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  Profiler prof;
+  // host-API staging buffers (device)
+  void *hb = nullptr;
+  size_t hb_bytes = 0;
+
+  template <class T>
+  T *dalloc(size_t count) {
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    CUDA_OK(cudaMalloc(&p, count * sizeof(T)));
+    allocs.push_back(p);
+    return static_cast<T *>(p);
+  }
+  template <class T>
+  T *upload(const std::vector<T> &v) {
+    T *p = dalloc<T>(v.size());
+    if (!v.empty()) CUDA_OK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  ~inla_model() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(device);
+    for (void *p : allocs) cudaFree(p);
+    if (ws) cudaFree(ws);
+    if (bb) cudaFree(bb);
+    if (hb) cudaFree(hb);
+    if (stream) cudaStreamDestroy(stream);
+    cudaSetDevice(cur);
+  }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ model construction
+
+void validate(const inla_model_desc *d) {
+  auto bad = [](const std::string &m) { throw ApiError(INLA_ERR_ARG, m); };
+  if (!d) bad("desc is NULL");
+  if (d->n_t < 1 || d->n_s < 1) bad("n_t and n_s must be >= 1");
+  if (d->n_b < 0 || d->n_b > MAX_NB) bad("n_b must be in [0, 16]");
+  if (d->m < 1 || d->m > (int64_t)INT32_MAX) bad("m must be in [1, 2^31)");
+  if (d->lik != INLA_LIK_GAUSSIAN && d->lik != INLA_LIK_POISSON) bad("unknown likelihood");
+  if (!d->C_diag || !d->G_rowptr || !d->G_col || !d->G_val || !d->A_rowptr || !d->A_col || !d->A_val || !d->y)
+    bad("a required array is NULL");
+  if (d->lik == INLA_LIK_POISSON && !d->E) bad("Poisson likelihood needs exposures E");
+  if (d->lik == INLA_LIK_GAUSSIAN && !(d->tau_b > 0.0)) bad("tau_b must be > 0");
+  for (int j = 0; j < 4; ++j)
+    if (!(d->prior_sd[j] > 0.0) || !std::isfinite(d->prior_mean[j])) bad("hyperprior sd must be > 0");
+  const int64_t n_s = d->n_s;
+  for (int64_t i = 0; i < n_s; ++i)
+    if (!(d->C_diag[i] > 0.0) || !std::isfinite(d->C_diag[i])) bad("C_diag must be positive and finite");
+  if (d->G_rowptr[0] != 0) bad("G_rowptr[0] must be 0");
+  for (int64_t i = 0; i < n_s; ++i) {
+    if (d->G_rowptr[i + 1] < d->G_rowptr[i]) bad("G_rowptr not monotone");
+    for (int p = d->G_rowptr[i]; p < d->G_rowptr[i + 1]; ++p) {
+      if (d->G_col[p] < 0 || d->G_col[p] >= n_s) bad("G column index out of range");
+      if (p > d->G_rowptr[i] && d->G_col[p] <= d->G_col[p - 1]) bad("G columns must be sorted and unique");
+      if (!std::isfinite(d->G_val[p])) bad("G value not finite");
+    }
+  }
+  if (d->A_rowptr[0] != 0) bad("A_rowptr[0] must be 0");
+  const int64_t N = (int64_t)d->n_t * n_s, n = N + d->n_b;
+  for (int64_t r = 0; r < d->m; ++r) {
+    if (d->A_rowptr[r + 1] < d->A_rowptr[r]) bad("A_rowptr not monotone");
+    int nsp = 0;
+    int64_t tb = -1;
+    for (int64_t p = d->A_rowptr[r]; p < d->A_rowptr[r + 1]; ++p) {
+      const int64_t c = d->A_col[p];
+      if (c < 0 || c >= n) bad("A column index out of range");
+      if (p > d->A_rowptr[r] && c <= d->A_col[p - 1]) bad("A columns must be sorted and unique within a row");
+      if (!std::isfinite(d->A_val[p])) bad("A value not finite");
+      if (c < N) {
+        if (tb >= 0 && c / n_s != tb) bad("spatial entries of an A row must lie in one time block");
+        tb = c / n_s;
+        ++nsp;
+      }
+    }
+    if (nsp < 1 || nsp > MAX_SPATIAL) bad("each A row needs 1 to 3 spatial entries");
+    if (!std::isfinite(d->y[r])) bad("y not finite");
+    if (d->lik == INLA_LIK_POISSON) {
+      if (!(d->E[r] > 0.0) || !std::isfinite(d->E[r])) bad("E must be positive");
+      if (d->y[r] < 0.0 || d->y[r] != std::floor(d->y[r])) bad("Poisson y must be non-negative integers");
+    }
+  }
+}
+
+inla_model *create_model(const inla_model_desc *d, int device) {
+  validate(d);
+  int ndev = 0;
+  CUDA_OK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) throw ApiError(INLA_ERR_ARG, "device index out of range");
+  CUDA_OK(cudaSetDevice(device));
+  auto *mdl = new inla_model();
+  mdl->device = device;
+  try {
+    const int n_t = d->n_t, n_s = d->n_s, n_b = d->n_b;
+    const int64_t m = d->m, N = (int64_t)n_t * n_s;
+    DevModel &M = mdl->M;
+    M.n_t = n_t; M.n_s = n_s; M.n_b = n_b; M.lik = d->lik; M.m = m;
+    M.n_p = (int)rup(n_s, TILE);
+    M.n = N + n_b;
+    M.nv = (int64_t)n_t * M.n_p + n_b;
+    for (int j = 0; j < 4; ++j) { M.prior_mean[j] = d->prior_mean[j]; M.prior_sd[j] = d->prior_sd[j]; }
+    M.tau_b_fixed = d->tau_b;
+
+    // observations: time block, vertices, weights, covariates; stable sort by time
+    std::vector<int> ot(m);
+    std::vector<int> ov(m * MAX_SPATIAL, 0);
+    std::vector<double> ow(m * MAX_SPATIAL, 0.0), oz(m * (int64_t)n_b, 0.0);
+    for (int64_t r = 0; r < m; ++r) {
+      int s = 0;
+      for (int64_t p = d->A_rowptr[r]; p < d->A_rowptr[r + 1]; ++p) {
+        const int64_t c = d->A_col[p];
+        if (c < N) {
+          ot[r] = (int)(c / n_s);
+          ov[r * MAX_SPATIAL + s] = (int)(c % n_s);
+          ow[r * MAX_SPATIAL + s] = d->A_val[p];
+          ++s;
+        } else {
+          oz[r * n_b + (c - N)] = d->A_val[p];
+        }
+      }
+      for (; s < MAX_SPATIAL; ++s) ov[r * MAX_SPATIAL + s] = ov[r * MAX_SPATIAL];
+    }
+    std::vector<int64_t> obs_ptr(n_t + 1, 0);
+    for (int64_t r = 0; r < m; ++r) obs_ptr[ot[r] + 1]++;
+    for (int t = 0; t < n_t; ++t) obs_ptr[t + 1] += obs_ptr[t];
+    std::vector<int64_t> perm(m), fill(obs_ptr.begin(), obs_ptr.end() - 1);
+    for (int64_t r = 0; r < m; ++r) perm[fill[ot[r]]++] = r;
+    std::vector<int> s_t(m), s_v(m * MAX_SPATIAL);
+    std::vector<double> s_w(m * MAX_SPATIAL), s_z(m * (int64_t)n_b), s_y(m), s_E;
+    if (d->lik == INLA_LIK_POISSON) s_E.resize(m);
+    for (int64_t k = 0; k < m; ++k) {
+      const int64_t r = perm[k];
+      s_t[k] = ot[r];
+      for (int s = 0; s < MAX_SPATIAL; ++s) {
+        s_v[k * MAX_SPATIAL + s] = ov[r * MAX_SPATIAL + s];
+        s_w[k * MAX_SPATIAL + s] = ow[r * MAX_SPATIAL + s];
+      }
+      for (int l = 0; l < n_b; ++l) s_z[k * n_b + l] = oz[r * n_b + l];
+      s_y[k] = d->y[r];
+      if (!s_E.empty()) s_E[k] = d->E[r];
+    }
+    int max_mt = 0;
+    for (int t = 0; t < n_t; ++t) max_mt = std::max<int>(max_mt, (int)(obs_ptr[t + 1] - obs_ptr[t]));
+    M.max_mt = max_mt;
+
+    // union pattern: struct(G) + diag, struct(G)^2, and observation vertex pairs
+    std::vector<std::vector<int>> gadj(n_s), pat(n_s);
+    for (int i = 0; i < n_s; ++i) {
+      gadj[i].push_back(i);
+      for (int p = d->G_rowptr[i]; p < d->G_rowptr[i + 1]; ++p) gadj[i].push_back(d->G_col[p]);
+      std::sort(gadj[i].begin(), gadj[i].end());
+      gadj[i].erase(std::unique(gadj[i].begin(), gadj[i].end()), gadj[i].end());
+    }
+    for (int i = 0; i < n_s; ++i)
+      for (int k : gadj[i])
+        for (int j : gadj[k]) pat[i].push_back(j);
+    for (int64_t k = 0; k < m; ++k)
+      for (int a = 0; a < MAX_SPATIAL; ++a)
+        for (int b = 0; b < MAX_SPATIAL; ++b) pat[s_v[k * MAX_SPATIAL + a]].push_back(s_v[k * MAX_SPATIAL + b]);
+    std::vector<int> prow(n_s + 1, 0), pcol, prow_of;
+    for (int i = 0; i < n_s; ++i) {
+      auto &r = pat[i];
+      std::sort(r.begin(), r.end());
+      r.erase(std::unique(r.begin(), r.end()), r.end());
+      prow[i + 1] = prow[i] + (int)r.size();
+      for (int j : r) { pcol.push_back(j); prow_of.push_back(i); }
+    }
+    const int nnz = prow[n_s];
+    M.nnz = nnz;
+    auto find = [&](int i, int j) -> int {
+      auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
+      auto it = std::lower_bound(b, e, j);
+      if (it == e || *it != j) throw ApiError(INLA_ERR_ARG, "internal: pattern lookup failed");
+      return (int)(it - pcol.begin());
+    };
+    // G must be structurally and numerically symmetric
+    for (int i = 0; i < n_s; ++i)
+      for (int p = d->G_rowptr[i]; p < d->G_rowptr[i + 1]; ++p) {
+        const int j = d->G_col[p];
+        const int *b = d->G_col + d->G_rowptr[j], *e = d->G_col + d->G_rowptr[j + 1];
+        const int *it = std::lower_bound(b, e, i);
+        if (it == e || *it != i) throw ApiError(INLA_ERR_ARG, "G pattern is not symmetric");
+        const double v1 = d->G_val[p], v2 = d->G_val[it - d->G_col];
+        if (std::fabs(v1 - v2) > 1e-12 * (std::fabs(v1) + std::fabs(v2)) + 1e-300)
+          throw ApiError(INLA_ERR_ARG, "G is not symmetric");
+      }
+    // contribution lists of H = G C^-1 G on the pattern
+    std::vector<int64_t> hcnt(nnz + 1, 0);
+    for (int i = 0; i < n_s; ++i)
+      for (int p1 = d->G_rowptr[i]; p1 < d->G_rowptr[i + 1]; ++p1) {
+        const int k = d->G_col[p1];
+        for (int p2 = d->G_rowptr[k]; p2 < d->G_rowptr[k + 1]; ++p2) hcnt[find(i, d->G_col[p2]) + 1]++;
+      }
+    for (int e = 0; e < nnz; ++e) hcnt[e + 1] += hcnt[e];
+    std::vector<int> hk(hcnt[nnz]), hik(hcnt[nnz]), hkj(hcnt[nnz]);
+    {
+      std::vector<int64_t> f(hcnt.begin(), hcnt.end() - 1);
+      for (int i = 0; i < n_s; ++i)
+        for (int p1 = d->G_rowptr[i]; p1 < d->G_rowptr[i + 1]; ++p1) {
+          const int k = d->G_col[p1];
+          for (int p2 = d->G_rowptr[k]; p2 < d->G_rowptr[k + 1]; ++p2) {
+            const int64_t c = f[find(i, d->G_col[p2])]++;
+            hk[c] = k; hik[c] = p1; hkj[c] = p2;
+          }
+        }
+    }
+    std::vector<int> gpos(nnz, -1);
+    for (int i = 0; i < n_s; ++i)
+      for (int p = d->G_rowptr[i]; p < d->G_rowptr[i + 1]; ++p) gpos[find(i, d->G_col[p])] = p;
+    // pair contributions (t, pattern entry) and vertex contributions (t, v)
+    std::vector<int64_t> sp_ptr((int64_t)n_t * nnz + 1, 0), vt_ptr((int64_t)n_t * n_s + 1, 0);
+    std::vector<int> pairpos(m * MAX_SPATIAL * MAX_SPATIAL);
+    for (int64_t k = 0; k < m; ++k) {
+      const int t = s_t[k];
+      for (int a = 0; a < MAX_SPATIAL; ++a) {
+        if (s_w[k * MAX_SPATIAL + a] == 0.0 && a > 0) continue;
+        vt_ptr[(int64_t)t * n_s + s_v[k * MAX_SPATIAL + a] + 1]++;
+        for (int b = 0; b < MAX_SPATIAL; ++b) {
+          if (s_w[k * MAX_SPATIAL + b] == 0.0 && b > 0) continue;
+          const int e = find(s_v[k * MAX_SPATIAL + a], s_v[k * MAX_SPATIAL + b]);
+          pairpos[(k * MAX_SPATIAL + a) * MAX_SPATIAL + b] = e;
+          sp_ptr[(int64_t)t * nnz + e + 1]++;
+        }
+      }
+    }
+    for (size_t e = 1; e < sp_ptr.size(); ++e) sp_ptr[e] += sp_ptr[e - 1];
+    for (size_t e = 1; e < vt_ptr.size(); ++e) vt_ptr[e] += vt_ptr[e - 1];
+    std::vector<int> sp_obs(sp_ptr.back()), vt_obs(vt_ptr.back());
+    std::vector<double> sp_w(sp_ptr.back()), vt_w(vt_ptr.back());
+    {
+      std::vector<int64_t> fs(sp_ptr.begin(), sp_ptr.end() - 1), fv(vt_ptr.begin(), vt_ptr.end() - 1);
+      for (int64_t k = 0; k < m; ++k) {
+        const int t = s_t[k];
+        for (int a = 0; a < MAX_SPATIAL; ++a) {
+          if (s_w[k * MAX_SPATIAL + a] == 0.0 && a > 0) continue;
+          const int64_t cv = fv[(int64_t)t * n_s + s_v[k * MAX_SPATIAL + a]]++;
+          vt_obs[cv] = (int)k;
+          vt_w[cv] = s_w[k * MAX_SPATIAL + a];
+          for (int b = 0; b < MAX_SPATIAL; ++b) {
+            if (s_w[k * MAX_SPATIAL + b] == 0.0 && b > 0) continue;
+            const int e = pairpos[(k * MAX_SPATIAL + a) * MAX_SPATIAL + b];
+            const int64_t c = fs[(int64_t)t * nnz + e]++;
+            sp_obs[c] = (int)k;
+            sp_w[c] = s_w[k * MAX_SPATIAL + a] * s_w[k * MAX_SPATIAL + b];
+          }
+        }
+      }
+    }
+    // upload
+    M.prow = mdl->upload(prow);
+    M.pcol = mdl->upload(pcol);
+    M.prow_of = mdl->upload(prow_of);
+    M.obs_ptr = mdl->upload(obs_ptr);
+    M.obs_t = mdl->upload(s_t);
+    M.obs_v = mdl->upload(s_v);
+    M.obs_w = mdl->upload(s_w);
+    M.obs_z = mdl->upload(s_z);
+    M.y = mdl->upload(s_y);
+    M.E = s_E.empty() ? nullptr : mdl->upload(s_E);
+    M.sp_ptr = mdl->upload(sp_ptr);
+    M.sp_obs = mdl->upload(sp_obs);
+    M.sp_w = mdl->upload(sp_w);
+    M.vt_ptr = mdl->upload(vt_ptr);
+    M.vt_obs = mdl->upload(vt_obs);
+    M.vt_w = mdl->upload(vt_w);
+    std::vector<double> Gval(d->G_val, d->G_val + d->G_rowptr[n_s]), Cd(d->C_diag, d->C_diag + n_s);
+    const double *dG = mdl->upload(Gval);
+    const double *dC = mdl->upload(Cd);
+    const int *dgpos = mdl->upload(gpos);
+    const int64_t *dhptr = mdl->upload(hcnt);
+    const int *dhk = mdl->upload(hk), *dhik = mdl->upload(hik), *dhkj = mdl->upload(hkj);
+    double *vC = mdl->dalloc<double>(nnz), *vG = mdl->dalloc<double>(nnz), *vH = mdl->dalloc<double>(nnz);
+    M.vC = vC; M.vG = vG; M.vH = vH;
+    double *consts = mdl->dalloc<double>(4);
+    M.consts = consts;
+    CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream, cudaStreamNonBlocking));
+    setup_theta_free(mdl->stream, M, dhptr, dhk, dhik, dhkj, dG, dC, dgpos, vC, vG, vH);
+    setup_consts(mdl->stream, M, consts);
+    if (d->lik == INLA_LIK_GAUSSIAN) {
+      double *AtA = mdl->dalloc<double>((size_t)n_t * nnz);
+      double *Arw = mdl->dalloc<double>((size_t)n_t * n_b * n_s);
+      double *Tip = mdl->dalloc<double>((size_t)n_b * n_b);
+      double *Aty = mdl->dalloc<double>((size_t)M.nv);
+      double *tippart = mdl->dalloc<double>((size_t)n_t * (n_b * n_b + n_b));
+      M.AtA = AtA; M.Arw = Arw; M.Tip = Tip; M.Aty = Aty;
+      setup_gaussian(mdl->stream, M, AtA, Arw, Tip, Aty, tippart);
+    }
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaStreamSynchronize(mdl->stream));
+    return mdl;
+  } catch (...) {
+    delete mdl;
+    throw;
+  }
+}
+
+// ------------------------------------------------------------------ workspace
+
+struct Layout {
+  int64_t per_point_bytes = 0;
+  std::vector<std::pair<int64_t *, int64_t>> fields;  // (stride slot, count)
+};
+
+// Per-point element counts (doubles unless stated); each padded to 256 bytes.
+struct Sizes {
+  int64_t theta, prm, qs, Dinv, Rt, Da, vec, wv, mat, nbnp, gjP, gjCO, sc, pt, part, tippart;
+  int64_t m, AtAp, Arwp, ints;
+};
+
+Sizes sizes_of(const DevModel &M) {
+  Sizes s{};
+  const int64_t np = M.n_p, nb = M.n_b;
+  s.theta = 32;
+  s.prm = rup((int64_t)sizeof(PointParams), 256) / 8;
+  s.qs = rup(M.nnz, 32);
+  s.Dinv = (int64_t)M.n_t * np * np;
+  s.Rt = rup((int64_t)M.n_t * nb * np, 32);
+  s.Da = rup(nb * nb, 32) + 32;
+  s.vec = rup(M.nv, 32);
+  s.wv = rup((1 + nb) * np, 32);
+  s.mat = np * np;
+  s.nbnp = rup(nb * np, 32) + 32;
+  s.gjP = TILE * TILE;
+  s.gjCO = np * TILE;
+  s.sc = 32;
+  s.pt = rup((int64_t)M.n_t * PT_COUNT, 32);
+  s.part = NPART * 4;
+  s.tippart = rup((int64_t)M.n_t * (nb * nb + nb), 32) + 32;
+  s.ints = 32;
+  if (M.lik == INLA_LIK_POISSON) {
+    s.m = rup(M.m, 32);
+    s.AtAp = rup((int64_t)M.n_t * M.nnz, 32);
+    s.Arwp = rup((int64_t)M.n_t * nb * M.n_s, 32) + 32;
+  }
+  return s;
+}
+
+int64_t point_bytes(const DevModel &M) {
+  const Sizes s = sizes_of(M);
+  int64_t d = s.theta + s.prm + s.qs + s.Dinv + s.Rt + 2 * s.Da + 5 * s.vec + s.wv + 4 * s.mat + 3 * s.nbnp + s.gjP +
+              2 * s.gjCO + s.sc + s.pt + s.part + s.tippart + 4 * s.ints + 1;
+  if (M.lik == INLA_LIK_POISSON) d += 4 * s.m + s.AtAp + s.Arwp;
+  return d * 8;
+}
+
+Work carve(const DevModel &M, void *base, int Pw) {
+  const Sizes s = sizes_of(M);
+  Work W{};
+  char *p = static_cast<char *>(base);
+  auto take = [&](int64_t per) {
+    char *r = p;
+    p += (size_t)per * Pw * 8;
+    return reinterpret_cast<double *>(r);
+  };
+  W.theta = take(s.theta);
+  W.prm = reinterpret_cast<PointParams *>(take(s.prm));
+  W.qs = take(s.qs); W.sNnz = s.qs;
+  W.Dinv = take(s.Dinv); W.sDinv = s.Dinv;
+  W.Rt = take(s.Rt); W.sRt = s.Rt;
+  W.Da = take(s.Da); W.sNb2 = s.Da;
+  W.Tipp = take(s.Da);
+  W.rhs = take(s.vec); W.zf = take(s.vec); W.x = take(s.vec); W.xprev = take(s.vec); W.tmpv = take(s.vec);
+  W.sVec = s.vec;
+  W.wv = take(s.wv); W.sWV = s.wv;
+  W.T1 = take(s.mat); W.S = take(s.mat); W.SigN = take(s.mat); W.SigC = take(s.mat); W.sMat = s.mat;
+  W.SigAn = take(s.nbnp); W.SigAc = take(s.nbnp); W.Y = take(s.nbnp); W.sNbNp = s.nbnp;
+  W.gjP = take(s.gjP); W.gjC = take(s.gjCO); W.gjO = take(s.gjCO);
+  W.sc = take(s.sc);
+  W.pt = take(s.pt); W.sPt = s.pt;
+  W.part = take(s.part);
+  W.tippart = take(s.tippart);
+  W.status = reinterpret_cast<int *>(take(s.ints));
+  W.active = reinterpret_cast<int *>(take(s.ints));
+  W.flags = reinterpret_cast<int *>(take(s.ints));
+  W.iters = reinterpret_cast<int *>(take(s.ints));
+  W.any_active = reinterpret_cast<int *>(take(1));
+  if (M.lik == INLA_LIK_POISSON) {
+    W.eta = take(s.m); W.mu = take(s.m); W.qobs = take(s.m); W.wobs = take(s.m); W.sM = s.m;
+    W.AtAp = take(s.AtAp); W.sAtAp = s.AtAp;
+    W.Arwp = take(s.Arwp); W.sArwp = s.Arwp;
+  }
+  W.P = Pw;
+  return W;
+}
+
+// The per-point layout above uses stride = count for each array, so that the
+// stride of point b is the count; sc, pt and Tipp use fixed strides.
+static_assert(SC_COUNT <= 32, "sc slots");
+
+int wave_points(inla_model *mdl, int64_t P_total) {
+  const int64_t per = point_bytes(mdl->M);
+  size_t free_b = 0, total_b = 0;
+  CUDA_OK(cudaMemGetInfo(&free_b, &total_b));
+  const int64_t avail = (int64_t)free_b + (int64_t)mdl->ws_bytes - (int64_t)(2ll << 30);
+  int64_t cap = avail / per;
+  if (cap < 1) throw ApiError(INLA_ERR_OOM, "not enough device memory for one evaluation point");
+  return (int)std::min<int64_t>(P_total, std::min<int64_t>(cap, 65535));
+}
+
+void ensure_workspace(inla_model *mdl, int Pw) {
+  const size_t need = (size_t)point_bytes(mdl->M) * Pw;
+  if (mdl->ws && mdl->ws_bytes >= need) return;
+  if (mdl->ws) {
+    CUDA_OK(cudaStreamSynchronize(mdl->stream));
+    CUDA_OK(cudaDeviceSynchronize());
+    cudaFree(mdl->ws);
+    mdl->ws = nullptr;
+    mdl->ws_bytes = 0;
+  }
+  CUDA_OK(cudaMalloc(&mdl->ws, need));
+  mdl->ws_bytes = need;
+  mdl->ws_points = Pw;
+}
+
+struct BatchBufs {
+  double *theta_all, *f_all, *grad_all;
+  int *point_out, *status_all, *iters_all;
+};
+
+BatchBufs batch_buffers(inla_model *mdl, int64_t P_total) {
+  const int64_t per = rup(4 * 8, 256) + rup(8, 256) + rup(32, 256) + 3 * rup(4, 256);
+  const size_t need = (size_t)per * P_total + 4096;
+  if (!mdl->bb || mdl->bb_bytes < need) {
+    if (mdl->bb) {
+      CUDA_OK(cudaDeviceSynchronize());
+      cudaFree(mdl->bb);
+      mdl->bb = nullptr;
+    }
+    CUDA_OK(cudaMalloc(&mdl->bb, need));
+    mdl->bb_bytes = need;
+  }
+  char *p = static_cast<char *>(mdl->bb);
+  auto take = [&](int64_t bytes) {
+    char *r = p;
+    p += rup(bytes * P_total, 256);
+    return r;
+  };
+  BatchBufs b;
+  b.theta_all = reinterpret_cast<double *>(take(32));
+  b.f_all = reinterpret_cast<double *>(take(8));
+  b.grad_all = reinterpret_cast<double *>(take(32));
+  b.point_out = reinterpret_cast<int *>(take(4));
+  b.status_all = reinterpret_cast<int *>(take(4));
+  b.iters_all = reinterpret_cast<int *>(take(4));
+  return b;
+}
+
+// ------------------------------------------------------------------ phases
+
+void zero_slot(Launch &L, const Work &W, int slot) {
+  zero_slot_kernel<<<(W.P + 63) / 64, 64, 0, L.st>>>(W, slot);
+  L.tick();
+}
+
+// Block LDL^T factorisation of Q_c (mode ASM_QC) or Q (ASM_Q) along the time chain.
+void factor(Launch &L, const DevModel &M, const Work &W, int mode, int ld_slot) {
+  const int64_t np2 = (int64_t)M.n_p * M.n_p;
+  const int64_t rtb = (int64_t)M.n_b * M.n_p;
+  zero_slot(L, W, ld_slot);
+  k_init_step0(L, M, W, mode);
+  for (int t = 0; t < M.n_t; ++t) {
+    double *Dt = W.Dinv + t * np2;
+    if (t > 0) {
+      const double *Dp = W.Dinv + (t - 1) * np2;
+      if (M.n_b > 0) {
+        k_dinv_apply(L, M, W, Dp, M.n_b, W.Rt + (t - 1) * rtb, W.sRt, W.wv, W.sWV, 1.0);
+        k_arrow_update(L, M, W, t, mode);
+        k_arrow_dots(L, M, W, t - 1);
+      }
+      k_sparse_right(L, M, W, Dp, W.sDinv, W.T1, W.sMat, false, nullptr, nullptr);
+    }
+    k_assemble_diag(L, M, W, t, mode, Dt, W.sDinv, t > 0);
+    gj_invert(L, M, W, Dt, W.sDinv, W.sc + ld_slot, SC_COUNT);
+  }
+  if (M.n_b > 0) {
+    const int t = M.n_t - 1;
+    k_dinv_apply(L, M, W, W.Dinv + t * np2, M.n_b, W.Rt + t * rtb, W.sRt, W.wv, W.sWV, 1.0);
+    k_arrow_dots(L, M, W, t);
+  }
+  k_tip(L, M, W, ld_slot);
+}
+
+// Forward and backward block substitution with the stored factorisation.
+void solve(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x) {
+  const int64_t np2 = (int64_t)M.n_p * M.n_p;
+  CUDA_OK(cudaMemcpyAsync(W.zf, rhs, sizeof(double) * W.sVec * W.P, cudaMemcpyDeviceToDevice, L.st));
+  for (int t = 0; t < M.n_t; ++t) {
+    k_dinv_apply(L, M, W, W.Dinv + t * np2, 1, W.zf + (int64_t)t * M.n_p, W.sVec, W.wv, W.sWV, 1.0);
+    k_fwd_update(L, M, W, t, W.zf);
+  }
+  k_tip_solve(L, M, W, W.zf, x);
+  for (int t = M.n_t - 1; t >= 0; --t) {
+    k_bwd_rhs(L, M, W, t, W.zf, x);
+    k_dinv_apply(L, M, W, W.Dinv + t * np2, 1, W.tmpv, W.sVec, x + (int64_t)t * M.n_p, W.sVec, 1.0);
+  }
+}
+
+// Block Takahashi recursion from the last time block to the first.
+void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contractions, double *marg_var,
+            const int *point_out, int64_t point_base, bool poisson_q) {
+  Work W = W0;
+  const int64_t np2 = (int64_t)M.n_p * M.n_p;
+  const int64_t rtb = (int64_t)M.n_b * M.n_p;
+  const int slotD = (mode == ASM_QC) ? PT_FD_C : PT_QD_C;
+  const int slotO = (mode == ASM_QC) ? PT_FO_C : PT_QO_C;
+  for (int t = M.n_t - 1; t >= 0; --t) {
+    const double *Dt = W.Dinv + t * np2;
+    const double *Rt_t = W.Rt + t * rtb;
+    const bool nxt = t < M.n_t - 1;
+    if (nxt) k_sparse_right(L, M, W, W.SigN, W.sMat, W.T1, W.sMat, true, M.n_b ? W.SigAn : nullptr, Rt_t);
+    k_selinv_Y(L, M, W, t, nxt);
+    k_sparse_left(L, M, W, W.T1, W.sMat, W.S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
+    if (contractions && nxt) k_contract_offdiag(L, M, W, t, slotO);
+    if (M.n_b > 0) k_dinv_apply(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
+    gemm_nn(L, W.P, M.n_p, W.S, W.sMat, Dt, W.sDinv, W.T1, W.sMat, 1.0, nullptr, 0, 0.0, false, W.active);
+    gemm_nn(L, W.P, M.n_p, Dt, W.sDinv, W.T1, W.sMat, W.SigC, W.sMat, 1.0, Dt, W.sDinv, 1.0, true, W.active);
+    mirror_lower(L, W.P, M.n_p, W.SigC, W.sMat, W.active);
+    k_contract_diag(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
+    if (poisson_q) k_poisson_qobs(L, M, W, t);
+    std::swap(W.SigN, W.SigC);
+    std::swap(W.SigAn, W.SigAc);
+  }
+  k_contract_tip(L, M, W, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base);
+}
+
+void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o, int64_t w0,
+              const BatchBufs &bb, double *x_out, double *mv_out, int centre_flags) {
+  const DevModel &M = mdl->M;
+  const bool adj = o.grad == INLA_GRAD_ADJOINT;
+  const bool need_sel = (centre_flags & 1) != 0;
+  CUDA_OK(cudaMemsetAsync(W.sc, 0, sizeof(double) * 32 * W.P, L.st));
+  CUDA_OK(cudaMemsetAsync(W.pt, 0, sizeof(double) * W.sPt * W.P, L.st));
+  CUDA_OK(cudaMemsetAsync(W.status, 0, sizeof(int) * W.P, L.st));
+  CUDA_OK(cudaMemsetAsync(W.iters, 0, sizeof(int) * W.P, L.st));
+  CUDA_OK(cudaMemsetAsync(W.rhs, 0, sizeof(double) * W.sVec * W.P, L.st));
+  flags_kernel<<<(W.P + 63) / 64, 64, 0, L.st>>>(W, w0, o.grad == INLA_GRAD_FD_CENTRAL ? 9 : 1, centre_flags);
+  L.tick();
+  k_set_active(L, W, 0);
+  k_params(L, M, W);
+  k_qs_values(L, M, W);
+  // prior log-determinant (and traces for the adjoint)
+  if (o.prior_mode == INLA_PRIOR_KRONECKER) {
+    k_assemble_diag(L, M, W, 0, ASM_QS, W.T1, W.sMat, false);
+    gj_invert(L, M, W, W.T1, W.sMat, W.sc + SC_LOGDET_QS, SC_COUNT);
+    if (adj) k_qs_traces(L, M, W);
+  } else {
+    factor(L, M, W, ASM_Q, SC_LOGDET_Q);
+    if (adj) {
+      k_set_active(L, W, 2);
+      selinv(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false);
+      k_set_active(L, W, 0);
+    }
+  }
+  if (M.lik == INLA_LIK_GAUSSIAN) {
+    factor(L, M, W, ASM_QC, SC_LOGDET_QC);
+    k_rhs_gaussian(L, M, W);
+    solve(L, M, W, W.rhs, W.x);
+    k_obs_reduce(L, M, W, 0);
+    k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
+    if (need_sel) {
+      k_set_active(L, W, 1);
+      selinv(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+      k_set_active(L, W, 0);
+    }
+  } else {
+    const int max_it = o.max_newton > 0 ? o.max_newton : 50;
+    const double tol = o.newton_tol > 0 ? o.newton_tol : 1e-8;
+    CUDA_OK(cudaMemsetAsync(W.x, 0, sizeof(double) * W.sVec * W.P, L.st));
+    CUDA_OK(cudaMemsetAsync(W.xprev, 0, sizeof(double) * W.sVec * W.P, L.st));
+    for (int it = 1; it <= max_it; ++it) {
+      k_poisson_eta(L, M, W, W.x);
+      k_obs_assemble(L, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp, W.sArwp,
+                     W.Tipp, W.sNb2, W.rhs, W.sVec, W.tippart);
+      factor(L, M, W, ASM_QC, SC_LOGDET_QC);
+      solve(L, M, W, W.rhs, W.x);
+      CUDA_OK(cudaMemsetAsync(W.any_active, 0, sizeof(int), L.st));
+      k_poisson_step(L, M, W, tol, it, max_it);
+      int any = 0;
+      CUDA_OK(cudaMemcpyAsync(&any, W.any_active, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+      CUDA_OK(cudaStreamSynchronize(L.st));
+      if (!any) break;
+    }
+    // refactorise at the mode
+    k_set_active(L, W, 0);
+    k_poisson_eta(L, M, W, W.x);
+    k_obs_assemble(L, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp, W.sArwp,
+                   W.Tipp, W.sNb2, nullptr, 0, W.tippart);
+    factor(L, M, W, ASM_QC, SC_LOGDET_QC);
+    k_obs_reduce(L, M, W, 1);
+    k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
+    if (need_sel) {
+      k_set_active(L, W, 1);
+      selinv(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+      if (adj) {
+        k_set_active(L, W, 2);
+        k_poisson_wobs(L, M, W);
+        CUDA_OK(cudaMemsetAsync(W.rhs, 0, sizeof(double) * W.sVec * W.P, L.st));
+        k_obs_assemble(L, M, W.P, W.active, nullptr, 0, W.wobs, W.sM, false, nullptr, nullptr, 0, nullptr, 0,
+                       nullptr, 0, W.rhs, W.sVec, W.tippart);
+        solve(L, M, W, W.rhs, W.xprev);
+        k_quadforms(L, M, W, W.xprev, W.x, PT_LD_C, SC_TIP_LX);
+      }
+      k_set_active(L, W, 0);
+    }
+  }
+  if (x_out) k_copy_mode(L, M, W, x_out, bb.point_out, w0);
+  k_finalize(L, M, W, o.grad, o.prior_mode, w0, bb.f_all, bb.grad_all, bb.status_all, bb.iters_all);
+}
+
+int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_eval_opts *opts,
+                  const inla_eval_out *out, cudaStream_t st) {
+  if (!mdl || !opts || !out || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
+  if (!out->f_dev || !out->status_dev) throw ApiError(INLA_ERR_ARG, "f_dev and status_dev are required");
+  if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_ADJOINT) throw ApiError(INLA_ERR_ARG, "bad grad mode");
+  if (opts->prior_mode != INLA_PRIOR_KRONECKER && opts->prior_mode != INLA_PRIOR_BTA)
+    throw ApiError(INLA_ERR_ARG, "bad prior mode");
+  if (opts->precision != INLA_FP64) throw ApiError(INLA_ERR_UNSUPPORTED, "only INLA_FP64 is available");
+  if (opts->grad != INLA_GRAD_NONE && !out->grad_dev) throw ApiError(INLA_ERR_ARG, "grad_dev required");
+  if (opts->want_mode && !out->x_mode_dev) throw ApiError(INLA_ERR_ARG, "x_mode_dev required");
+  if (opts->want_marg_var && !out->marg_var_dev) throw ApiError(INLA_ERR_ARG, "marg_var_dev required");
+  CUDA_OK(cudaSetDevice(mdl->device));
+  const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+  const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
+  const int64_t P_total = (int64_t)B * per;
+  mdl->launches = 0;
+  Launch L{st, &mdl->launches, &mdl->prof};
+  const int Pw = wave_points(mdl, P_total);
+  ensure_workspace(mdl, Pw);
+  BatchBufs bb = batch_buffers(mdl, P_total);
+  point_out_kernel<<<(unsigned)((P_total + 127) / 128), 128, 0, st>>>((int)P_total, per, bb.point_out);
+  L.tick();
+  if (per == 9) k_fd_points(L, B, theta_dev, eps, bb.theta_all);
+  else CUDA_OK(cudaMemcpyAsync(bb.theta_all, theta_dev, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
+  int centre_flags = 0;
+  if (opts->want_marg_var || opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 1;
+  if (opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 2;
+  for (int64_t w0 = 0; w0 < P_total; w0 += Pw) {
+    const int P = (int)std::min<int64_t>(Pw, P_total - w0);
+    Work W = carve(mdl->M, mdl->ws, mdl->ws_points);
+    W.P = P;
+    CUDA_OK(cudaMemcpyAsync(W.theta, bb.theta_all + 4 * w0, sizeof(double) * 4 * P, cudaMemcpyDeviceToDevice, st));
+    // theta rows are read with stride 4 by the parameter kernel
+    run_wave(mdl, L, W, *opts, w0, bb, opts->want_mode ? out->x_mode_dev : nullptr,
+             opts->want_marg_var ? out->marg_var_dev : nullptr, centre_flags);
+  }
+  k_outputs(L, B, per, eps, 4, bb.f_all, opts->grad == INLA_GRAD_ADJOINT ? bb.grad_all : nullptr, bb.status_all,
+            bb.iters_all, out->f_dev, opts->grad != INLA_GRAD_NONE ? out->grad_dev : nullptr, out->status_dev,
+            out->newton_iters_dev);
+  CUDA_OK(cudaGetLastError());
+  return mdl->launches;
+}
+
+template <class F>
+int guarded(F &&f) {
+  try {
+    f();
+    set_error("");
+    return INLA_OK;
+  } catch (const ApiError &e) {
+    set_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    return INLA_ERR_OOM;
+  } catch (const std::exception &e) {
+    set_error(e.what());
+    return INLA_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int inla_model_create(const inla_model_desc *desc, int device, inla_model **out) {
+  return guarded([&] {
+    if (!out) throw ApiError(INLA_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    *out = create_model(desc, device);
+  });
+}
+
+int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *opts, size_t *bytes) {
+  return guarded([&] {
+    if (!model || !opts || !bytes || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
+    const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+    *bytes = (size_t)point_bytes(model->M) * (size_t)B * per;
+  });
+}
+
+int inla_eval_batch(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
+                    const inla_eval_out *out, void *stream) {
+  return guarded([&] { eval_impl(model, B, theta_dev, opts, out, static_cast<cudaStream_t>(stream)); });
+}
+
+int inla_eval_batch_host(inla_model *model, int B, const double *theta, const inla_eval_opts *opts,
+                         const inla_eval_out_host *out) {
+  return guarded([&] {
+    if (!model || !opts || !out || !theta || B < 1 || !out->f || !out->status)
+      throw ApiError(INLA_ERR_ARG, "invalid arguments");
+    CUDA_OK(cudaSetDevice(model->device));
+    const int64_t n = model->M.n;
+    const size_t need = rup(32 * B, 256) + rup(8 * B, 256) + rup(32 * B, 256) + 2 * rup(4 * B, 256) +
+                        2 * rup(8 * n * B, 256);
+    if (!model->hb || model->hb_bytes < need) {
+      if (model->hb) {
+        CUDA_OK(cudaStreamSynchronize(model->stream));
+        cudaFree(model->hb);
+        model->hb = nullptr;
+      }
+      CUDA_OK(cudaMalloc(&model->hb, need));
+      model->hb_bytes = need;
+    }
+    char *p = static_cast<char *>(model->hb);
+    auto take = [&](size_t b) { char *r = p; p += rup(b, 256); return r; };
+    double *th = reinterpret_cast<double *>(take(32 * B));
+    inla_eval_out d{};
+    d.f_dev = reinterpret_cast<double *>(take(8 * B));
+    d.grad_dev = reinterpret_cast<double *>(take(32 * B));
+    d.status_dev = reinterpret_cast<int *>(take(4 * B));
+    d.newton_iters_dev = reinterpret_cast<int *>(take(4 * B));
+    d.x_mode_dev = reinterpret_cast<double *>(take(8 * n * B));
+    d.marg_var_dev = reinterpret_cast<double *>(take(8 * n * B));
+    cudaStream_t st = model->stream;
+    CUDA_OK(cudaMemcpyAsync(th, theta, sizeof(double) * 4 * B, cudaMemcpyHostToDevice, st));
+    eval_impl(model, B, th, opts, &d, st);
+    CUDA_OK(cudaMemcpyAsync(out->f, d.f_dev, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(out->status, d.status_dev, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    if (out->grad && opts->grad != INLA_GRAD_NONE)
+      CUDA_OK(cudaMemcpyAsync(out->grad, d.grad_dev, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
+    if (out->newton_iters)
+      CUDA_OK(cudaMemcpyAsync(out->newton_iters, d.newton_iters_dev, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    if (out->x_mode && opts->want_mode)
+      CUDA_OK(cudaMemcpyAsync(out->x_mode, d.x_mode_dev, sizeof(double) * n * B, cudaMemcpyDeviceToHost, st));
+    if (out->marg_var && opts->want_marg_var)
+      CUDA_OK(cudaMemcpyAsync(out->marg_var, d.marg_var_dev, sizeof(double) * n * B, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+  });
+}
+
+int inla_profile_enable(inla_model *model, int enable) {
+  return guarded([&] {
+    if (!model) throw ApiError(INLA_ERR_ARG, "model is NULL");
+    CUDA_OK(cudaSetDevice(model->device));
+    CUDA_OK(cudaDeviceSynchronize());
+    model->prof.reset();
+    model->prof.enabled = enable ? 1 : 0;
+  });
+}
+
+int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *launches, double *units) {
+  return guarded([&] {
+    if (!model || !total_ms || !launches || !units || kernel < 0 || kernel >= KID_COUNT)
+      throw ApiError(INLA_ERR_ARG, "invalid arguments");
+    CUDA_OK(cudaSetDevice(model->device));
+    double ms = 0.0, u = 0.0;
+    int64_t n = 0;
+    for (auto &r : model->prof.recs) {
+      if (r.id != kernel) continue;
+      CUDA_OK(cudaEventSynchronize(r.b));
+      float e = 0.f;
+      CUDA_OK(cudaEventElapsedTime(&e, r.a, r.b));
+      ms += e;
+      u += r.units;
+      ++n;
+    }
+    *total_ms = ms;
+    *launches = n;
+    *units = u;
+  });
+}
+
+int64_t inla_model_latent_dim(const inla_model *model) { return model ? model->M.n : -1; }
+
+int64_t inla_last_launch_count(const inla_model *model) { return model ? model->launches : -1; }
+
+void inla_model_destroy(inla_model *model) { delete model; }
+
+const char *inla_last_error(void) { return inla::get_error(); }
+
+}  // extern "C"

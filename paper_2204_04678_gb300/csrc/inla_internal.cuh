@@ -1,0 +1,236 @@
+// Internal declarations shared by the library's translation units.
+//
+// Layout in HBM (per evaluation point b of a wave of P points):
+//   Dinv   [P][n_t][n_p][n_p]  inverses of the Schur-complement diagonal blocks
+//                              D_t of the block LDL^T factorisation of Q_c,
+//                              padded to n_p = roundup(n_s, 64) with an identity
+//                              in the padding, full symmetric row-major storage
+//   Rt     [P][n_t][n_b][n_p]  arrow blocks after the Schur updates (R~_t)
+//   vectors in "padded latent" layout [n_t][n_p] followed by the n_b tail
+//   scratch [P][n_p][n_p] matrices for the assembly and the selected inversion
+// Sparse theta-free matrices live on one union pattern (CSR over n_s rows):
+//   vC, vG, vH (C, G, H = G C^-1 G) and per time block the spatial part of
+//   A^T D A.  Q_s(theta) on the pattern is aC*vC + aG*vG + aH*vH.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/inla_gpu.h"
+
+namespace inla {
+
+constexpr int TILE = 64;        // dense tile edge (pivot blocks, GEMM tiles)
+constexpr int MAX_NB = 16;      // fixed effects supported by the small kernels
+constexpr int MAX_SPATIAL = 3;  // spatial entries per observation row
+constexpr int NPART = 256;      // partial sums per point for long reductions
+
+// Scalars of one evaluation point, computed on the device from theta.
+struct PointParams {
+  double tau_y;                     // Gaussian noise precision (0 for Poisson)
+  double tau_b;                     // fixed-effect prior precision
+  double aC, aG, aH;                // Q_s = aC C + aG G + aH H
+  double rho;
+  double qd_end, qd_mid, q_off;     // AR(1) precision entries
+  double dqd_end, dqd_mid, dq_off;  // their derivatives wrt theta_4
+  double logprior;
+  double dlogprior[4];
+  double theta[4];
+};
+
+// Index structures and theta-free values of a model (device pointers).
+struct DevModel {
+  int n_t, n_s, n_b, n_p, lik, nnz;
+  int max_mt;                    // largest number of observations in one time block
+  int64_t m, n, nv;              // nv = n_t*n_p + n_b (padded latent length)
+  const int *prow, *pcol;        // union pattern, CSR [n_s+1], [nnz]
+  const int *prow_of;            // [nnz] row of each pattern entry
+  const double *vC, *vG, *vH;    // [nnz]
+  const int64_t *obs_ptr;        // [n_t+1] observations of block t (sorted by time)
+  const int *obs_t;              // [m] time block of each observation
+  const int *obs_v;              // [m][3] local vertex of each spatial entry
+  const double *obs_w;           // [m][3] weights (0 for unused entries)
+  const double *obs_z;           // [m][n_b] covariates
+  const double *y, *E;           // [m]
+  const int64_t *sp_ptr;         // [n_t*nnz+1] pair contributions of each pattern entry
+  const int *sp_obs;             //   observation index
+  const double *sp_w;            //   product of the two weights
+  const int64_t *vt_ptr;         // [n_t*n_s+1] contributions of each (t, vertex)
+  const int *vt_obs;
+  const double *vt_w;
+  const double *AtA;             // Gaussian: [n_t][nnz] spatial A_t^T A_t
+  const double *Arw;             // Gaussian: [n_t][n_b][n_s] Z^T A_t
+  const double *Tip;             // Gaussian: [n_b][n_b] Z^T Z
+  const double *Aty;             // Gaussian: [nv] A^T y (padded latent layout)
+  const double *consts;          // [4]: y^T y, sum lgamma(y+1), sum y log E
+  double prior_mean[4], prior_sd[4];
+  double tau_b_fixed;
+};
+
+// Per-wave workspace (device) with per-point strides (in doubles / ints).
+struct Work {
+  int P;
+  int64_t sDinv, sMat, sRt, sVec, sNb2, sWV, sNbNp, sNnz, sPt, sM, sAtAp, sArwp;
+  double *theta;         // [P][4]
+  PointParams *prm;      // [P]
+  double *qs;            // [P][nnz]     Q_s values on the pattern
+  double *Dinv;          // [P][n_t][n_p][n_p]
+  double *Rt;            // [P][n_t][n_b][n_p]
+  double *Da;            // [P][n_b][n_b]  tip Schur complement, then its inverse
+  double *rhs, *zf, *x, *xprev, *tmpv;  // [P][nv]
+  double *wv;            // [P][1+n_b][n_p]  Dinv_t times vectors
+  double *T1, *S, *SigN, *SigC;          // [P][n_p][n_p]
+  double *SigAn, *SigAc, *Y;             // [P][n_b][n_p]
+  double *gjP, *gjC, *gjO;               // [P][64*64], [P][n_p*64], [P][n_p*64]
+  double *sc;            // [P][SC_COUNT] per-point scalars
+  double *pt;            // [P][n_t][PT_COUNT] per-time-block contractions
+  double *part;          // [P][NPART][4] partial sums
+  double *tippart;       // [P][n_t][n_b*n_b + n_b] per-time-block partial sums
+  int *status;           // [P]
+  int *active;           // [P]  1 = this point takes part in the current pass
+  int *flags;            // [P]  bit 0: selected inversion, bit 1: adjoint gradient
+  int *iters;            // [P]
+  int *any_active;       // [1]
+  // Poisson
+  double *eta, *mu, *qobs, *wobs;        // [P][m]
+  double *AtAp;          // [P][n_t][nnz]
+  double *Arwp;          // [P][n_t][n_b][n_s]
+  double *Tipp;          // [P][n_b][n_b]
+};
+
+enum {
+  SC_LOGDET_QC = 0, SC_LOGDET_Q, SC_LOGDET_QS, SC_TR_QSI_C, SC_TR_QSI_G, SC_TR_QSI_H,
+  SC_RES2, SC_LOGLIK, SC_TIP_XX, SC_TIP_LX, SC_TIP_TRSIG, SC_TIP_ATA, SC_STEP2,
+  SC_COUNT = 16
+};
+enum {
+  PT_FD_C = 0, PT_FD_G, PT_FD_H, PT_FD_ATA,   // <Sigma_tt, X>
+  PT_FO_C, PT_FO_G, PT_FO_H,                  // <Sigma_{t+1,t}, X>
+  PT_FA_ATA,                                  // <Sigma_{a,t}, Z^T A_t>
+  PT_XD_C, PT_XD_G, PT_XD_H,                  // x_t^T X x_t
+  PT_XO_C, PT_XO_G, PT_XO_H,                  // x_{t+1}^T X x_t + x_t^T X x_{t+1}
+  PT_LD_C, PT_LD_G, PT_LD_H,                  // lambda_t^T X x_t
+  PT_LO_C, PT_LO_G, PT_LO_H,                  // lambda_{t+1}^T X x_t + lambda_t^T X x_{t+1}
+  PT_QD_C, PT_QD_G, PT_QD_H,                  // prior (BTA mode): <Sigma_Q,tt, X>
+  PT_QO_C, PT_QO_G, PT_QO_H,                  //                   <Sigma_Q,{t+1,t}, X>
+  PT_COUNT = 32
+};
+
+// Which matrix an assembly builds.
+enum { ASM_QC = 0, ASM_Q = 1, ASM_QS = 2 };
+
+// Optional CUDA-event timing of selected kernels (inla_profile_*).
+enum { KID_GJ_UPDATE = 0, KID_GEMM = 1, KID_GJ_PIVOT = 2, KID_GJ_PANEL = 3, KID_COUNT = 4 };
+struct Profiler {
+  int enabled = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Rec { int id; double units; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  cudaEvent_t get() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[next++];
+  }
+  void reset() { next = 0; recs.clear(); }
+  ~Profiler() { for (auto e : pool) cudaEventDestroy(e); }
+};
+
+struct Launch {
+  cudaStream_t st;
+  int64_t *counter;
+  Profiler *prof = nullptr;
+  int cur_id = -1;
+  double cur_units = 0.0;
+  cudaEvent_t cur_a = nullptr;
+  void tick() { if (counter) ++*counter; }
+  // bracket one launch of kernel `id` processing `units` algorithmic units
+  void start(int id, double units) {
+    if (!prof || !prof->enabled) return;
+    cur_id = id;
+    cur_units = units;
+    cur_a = prof->get();
+    cudaEventRecord(cur_a, st);
+  }
+  void stop() {
+    if (!prof || !prof->enabled || cur_id < 0) return;
+    cudaEvent_t b = prof->get();
+    cudaEventRecord(b, st);
+    prof->recs.push_back({cur_id, cur_units, cur_a, b});
+    cur_id = -1;
+  }
+};
+
+// dense_fp64.cu
+void gj_invert(Launch &L, const DevModel &M, const Work &W, double *A, int64_t strideA, double *logdet,
+               int ld_stride);
+void gemm_nn(Launch &L, int P, int n, const double *A, int64_t sA, const double *B, int64_t sB, double *C,
+             int64_t sC, double alpha, const double *C0, int64_t sC0, double beta, bool lower_only,
+             const int *active);
+void mirror_lower(Launch &L, int P, int n, double *A, int64_t sA, const int *active);
+
+// bta_kernels.cu
+void k_params(Launch &L, const DevModel &M, const Work &W);
+void k_qs_values(Launch &L, const DevModel &M, const Work &W);
+void k_set_active(Launch &L, const Work &W, int mask);
+void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode);
+void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *dst, int64_t sdst,
+                     bool schur);
+void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
+                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t);
+void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
+                   int64_t sOut, bool with_X, const double *Rt_t, const double *Ymat);
+void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const double *Dinv_t, int nvec,
+                  const double *vecs, int64_t sVecs, double *out, int64_t sOut, double scale);
+void k_arrow_update(Launch &L, const DevModel &M, const Work &W, int t, int mode);
+void k_arrow_dots(Launch &L, const DevModel &M, const Work &W, int tprev);
+void k_tip(Launch &L, const DevModel &M, const Work &W, int ld_slot);
+void k_fwd_update(Launch &L, const DevModel &M, const Work &W, int t, double *z);
+void k_tip_solve(Launch &L, const DevModel &M, const Work &W, const double *z, double *x);
+void k_bwd_rhs(Launch &L, const DevModel &M, const Work &W, int t, const double *z, const double *x);
+void k_selinv_Y(Launch &L, const DevModel &M, const Work &W, int t, bool has_next);
+void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int slot0);
+void k_contract_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *marg_var,
+                     const int *point_out, int64_t point_base, int slot0);
+void k_contract_tip(Launch &L, const DevModel &M, const Work &W, int mode, double *marg_var,
+                    const int *point_out, int64_t point_base);
+void k_quadforms(Launch &L, const DevModel &M, const Work &W, const double *u, const double *v, int slot0,
+                 int tip_slot);
+void k_rhs_gaussian(Launch &L, const DevModel &M, const Work &W);
+void k_obs_reduce(Launch &L, const DevModel &M, const Work &W, int kind);
+void k_qs_traces(Launch &L, const DevModel &M, const Work &W);
+void k_finalize(Launch &L, const DevModel &M, const Work &W, int grad_mode, int prior_mode, int64_t point_base,
+                double *f_all, double *grad_all, int *status_all, int *iters_all);
+void k_copy_mode(Launch &L, const DevModel &M, const Work &W, double *x_out, const int *point_out,
+                 int64_t point_base);
+void k_fd_points(Launch &L, int B, const double *theta, double eps, double *pts);
+void k_outputs(Launch &L, int B, int per, double eps, int d, const double *f_all, const double *grad_all,
+               const int *status_all, const int *iters_all, double *f, double *grad, int *status, int *iters);
+void k_poisson_eta(Launch &L, const DevModel &M, const Work &W, const double *x);
+// A^T diag(mu) A pieces and A^T r.  mu == nullptr means mu = 1; r_newton
+// uses r = y - mu + mu*eta from the workspace.  Any output may be nullptr.
+void k_obs_assemble(Launch &L, const DevModel &M, int P, const int *active, const double *mu, int64_t sMu,
+                    const double *r, int64_t sR, bool r_newton, const double *eta, double *AtA, int64_t sAtA,
+                    double *Arw, int64_t sArw, double *Tip, int64_t sTip, double *rhs, int64_t sRhs,
+                    double *tippart);
+void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter);
+void k_poisson_qobs(Launch &L, const DevModel &M, const Work &W, int t);
+void k_poisson_wobs(Launch &L, const DevModel &M, const Work &W);
+void k_zero(Launch &L, double *p, int64_t n);
+
+// setup_kernels.cu
+void setup_theta_free(cudaStream_t st, DevModel &M, const int64_t *d_hptr, const int *d_hk, const int *d_hik,
+                      const int *d_hkj, const double *d_Gval, const double *d_Cdiag, const int *d_gpos,
+                      double *vC, double *vG, double *vH);
+void setup_gaussian(cudaStream_t st, DevModel &M, double *AtA, double *Arw, double *Tip, double *Aty,
+                    double *tippart);
+void setup_consts(cudaStream_t st, DevModel &M, double *consts);
+
+void set_error(const std::string &msg);
+
+}  // namespace inla

@@ -1,0 +1,97 @@
+// FP64 throughput probe (measurement utility; no counterpart in the paper).
+// Every SM runs register-resident chains of independent FP64 fused
+// multiply-adds (scalar FMA, or the warp-level m8n8k4 double-precision MMA
+// instruction) for a fixed number of iterations; the rate is
+// flops / CUDA-event time.  The loops are bounded and touch no memory except
+// one store per thread at the end (so the compiler cannot drop them).
+#include <cuda_runtime.h>
+
+#include "inla_internal.cuh"
+
+namespace {
+
+constexpr int CHAINS = 8;
+
+__global__ void __launch_bounds__(256) dfma_probe(int iters, double *sink) {
+  double a[CHAINS];
+  const double x = 1.0 + 1e-9 * threadIdx.x, y = 1.0 - 1e-9 * blockIdx.x;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) a[c] = 0.5 * c;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) a[c] = fma(a[c], x, y);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) s += a[c];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(256) dmma_probe(int iters, double *sink) {
+  double acc[CHAINS][2];
+  const double av = 1.0 + 1e-9 * threadIdx.x, bv = 1.0 - 1e-9 * blockIdx.x;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) acc[c][0] = acc[c][1] = 0.25 * c;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) {
+      asm volatile(
+          "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+          : "+d"(acc[c][0]), "+d"(acc[c][1])
+          : "d"(av), "d"(bv));
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) s += acc[c][0] + acc[c][1];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops) {
+  if (!tflops) {
+    inla::set_error("tflops is NULL");
+    return INLA_ERR_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    inla::set_error("cudaSetDevice failed");
+    return INLA_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, device);
+  const int blocks = prop.multiProcessorCount * 4, threads = 256;
+  const int iters = use_tensor ? (1 << 14) : (1 << 16);
+  double *sink = nullptr;
+  if (cudaMalloc(&sink, sizeof(double) * blocks * threads) != cudaSuccess) {
+    inla::set_error("cudaMalloc failed");
+    return INLA_ERR_OOM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    if (use_tensor) dmma_probe<<<blocks, threads>>>(iters, sink);
+    else dfma_probe<<<blocks, threads>>>(iters, sink);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (err != cudaSuccess) {
+    inla::set_error(cudaGetErrorString(err));
+    return INLA_ERR_CUDA;
+  }
+  // scalar: 2 flops per FMA per thread; MMA m8n8k4: 8*8*4 FMAs per warp instruction
+  const double per_iter = use_tensor ? (double)blocks * (threads / 32) * CHAINS * 8 * 8 * 4 * 2
+                                     : (double)blocks * threads * CHAINS * 2;
+  *tflops = per_iter * iters / (best * 1e-3) / 1e12;
+  return INLA_OK;
+}
