@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=2, choices=[1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grad", default="fd", choices=["fd", "adjoint"],
+                    help="fd: one f+grad from the 9-point stencil per step (the workload's definition); "
+                         "adjoint: the 9 stencil points each get f and an adjoint gradient")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--evals", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -207,12 +211,19 @@ def main():
     centre = theta_batch(cfg, mdl)[0] + 0.01 * rank
     model = pkg.Model(mdl, device=local)
     stream = torch.cuda.current_stream()
-    theta = torch.tensor(centre[None, :], dtype=torch.float64, device="cuda")
-    out = model.eval(theta, grad="fd")
+    if args.grad == "fd":
+        theta = torch.tensor(centre[None, :], dtype=torch.float64, device="cuda")
+        per_step = 1
+    else:
+        from synth import fd_stencil
+        theta = torch.tensor(fd_stencil(centre), dtype=torch.float64, device="cuda")
+        per_step = theta.shape[0]
+    grad = args.grad
+    out = model.eval(theta, grad=grad)
     for w in range(max(args.warmup, 1)):
         if w == args.warmup - 1:
             model.profile_enable(True)      # creates the event pool outside the timed region
-        model.eval(theta, grad="fd", out=out)
+        model.eval(theta, grad=grad, out=out)
     torch.cuda.synchronize()
     assert int(out["status"][0]) == 0, "evaluation failed"
     model.profile_enable(True)
@@ -225,7 +236,7 @@ def main():
     launches = 0
     e0.record(stream)
     for _ in range(args.steps):
-        model.eval(theta, grad="fd", out=out)
+        model.eval(theta, grad=grad, out=out)
         launches += model.last_launch_count()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -237,7 +248,7 @@ def main():
         t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t[0])
-    value = world * args.steps / elapsed
+    value = world * args.steps * per_step / elapsed
 
     # dominant kernel: rank-64 tile update of the block sweep inversion
     ms, nl, units = model.profile_read(capi.KERNEL_GJ_UPDATE)
@@ -260,18 +271,21 @@ def main():
                 "launches_timed": nl, "share_of_step": ms / 1e3 / elapsed if elapsed else None}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
-    th_host = centre[None, :].copy()
-    model.eval_host(th_host, grad="fd")
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        model.eval_host(th_host, grad="fd")
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
-    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * 8,
-           "d2h_bytes_per_step": 8 + 4 * 8 + 4 + 4}
+    e2e = None
+    if not args.no_e2e:
+        th_host = theta.cpu().numpy().copy()
+        model.eval_host(th_host, grad=grad)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            model.eval_host(th_host, grad=grad)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t[0])
+        nb = th_host.shape[0]
+        e2e = {"value": world * per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * nb,
+               "d2h_bytes_per_step": nb * (8 + 4 * 8 + 4 + 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -286,7 +300,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_dict(cfg, world), "clocks": clk, "gpu_launches": launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "f_evals_per_s": 9 * value,
+                "f_evals_per_s": 9 * value if grad == "fd" else value,
+                "grad_mode": grad,
                 "fp64_peaks_tflops": {"fma": peak_fp64, "dmma": peak_dmma},
                 "gemm_kernel": {"ms": gms, "launches": gnl,
                                 "tflops": gunits * flop_per_unit / (gms / 1e3) / 1e12 if gms else None}}

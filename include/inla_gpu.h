@@ -38,8 +38,10 @@
  *   - Pointers named *_dev are device pointers, all others host pointers.
  *     All floating point is IEEE binary64 ("double"), arrays are dense and
  *     contiguous (row-major where two-dimensional).
- *   - A model is not re-entrant: calls on one model must not overlap
- *     (one stream at a time).  Distinct models are independent.
+ *   - Calls on one model share its device workspace.  The library orders
+ *     each evaluation after the previous one on the same model, whatever
+ *     the streams, so results are never mixed; a model must still not be
+ *     used from two host threads at once.  Distinct models are independent.
  */
 #ifndef INLA_GPU_H
 #define INLA_GPU_H

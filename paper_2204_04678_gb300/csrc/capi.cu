@@ -85,6 +85,8 @@ struct inla_model {
   void *bb = nullptr;
   size_t bb_bytes = 0;
   cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;   // end of the last evaluation (orders calls across streams)
+  bool done_valid = false;
   int64_t launches = 0;
   Profiler prof;
   // host-API staging buffers (device)
@@ -114,6 +116,7 @@ struct inla_model {
     if (bb) cudaFree(bb);
     if (hb) cudaFree(hb);
     if (stream) cudaStreamDestroy(stream);
+    if (done) cudaEventDestroy(done);
     cudaSetDevice(cur);
   }
 };
@@ -365,6 +368,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     double *consts = mdl->dalloc<double>(4);
     M.consts = consts;
     CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream, cudaStreamNonBlocking));
+    CUDA_OK(cudaEventCreateWithFlags(&mdl->done, cudaEventDisableTiming));
     setup_theta_free(mdl->stream, M, dhptr, dhk, dhik, dhkj, dG, dC, dgpos, vC, vG, vH);
     setup_consts(mdl->stream, M, consts);
     if (d->lik == INLA_LIK_GAUSSIAN) {
@@ -411,7 +415,7 @@ Sizes sizes_of(const DevModel &M) {
   s.wv = rup((1 + nb) * np, 32);
   s.mat = np * np;
   s.nbnp = rup(nb * np, 32) + 32;
-  s.gjP = TILE * TILE;
+  s.gjP = 2 * TILE * TILE;
   s.gjCO = np * TILE;
   s.sc = 32;
   s.pt = rup((int64_t)M.n_t * PT_COUNT, 32);
@@ -715,6 +719,8 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   const int64_t P_total = (int64_t)B * per;
   mdl->launches = 0;
   Launch L{st, &mdl->launches, &mdl->prof};
+  // the workspace is shared by all calls on this model: order this call after the previous one
+  if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
   const int Pw = wave_points(mdl, P_total);
   ensure_workspace(mdl, Pw);
   BatchBufs bb = batch_buffers(mdl, P_total);
@@ -737,6 +743,8 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   k_outputs(L, B, per, eps, 4, bb.f_all, opts->grad == INLA_GRAD_ADJOINT ? bb.grad_all : nullptr, bb.status_all,
             bb.iters_all, out->f_dev, opts->grad != INLA_GRAD_NONE ? out->grad_dev : nullptr, out->status_dev,
             out->newton_iters_dev);
+  CUDA_OK(cudaEventRecord(mdl->done, st));
+  mdl->done_valid = true;
   CUDA_OK(cudaGetLastError());
   return mdl->launches;
 }

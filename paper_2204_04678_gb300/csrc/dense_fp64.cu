@@ -36,55 +36,95 @@ __device__ __forceinline__ void tri_index(int x, int &I, int &J) {
   J = x - i * (i + 1) / 2;
 }
 
-// Invert the current pivot block A_KK (64 x 64) in shared memory by 64 scalar
-// sweep steps; write P = A_KK^-1 and add log|A_KK| to *logdet.
+// Scalar sweep of a 64 x 64 SPD block held (lower triangle) in shared memory `a`:
+// after 64 steps `a` holds -A^-1.  Writes P = A^-1 (full symmetric tile) to Pout and
+// adds log|A| = sum_p log(pivot_p) to *logdet; a non-positive pivot sets *status.
+// One FMA per lower entry and step; the reciprocal of each pivot is formed once
+// and the logarithms once at the end.  Called by all threads of the block.
+constexpr int TRI = T * (T + 1) / 2;             // 2080 lower entries
+constexpr int PIV_PER_THREAD = (TRI + 255) / 256;
+constexpr int SWEEP_SMEM_DOUBLES = T * LDS + 3 * T;
+
+__device__ void sweep_tile(double *sm, double *Pout, double *logdet, int *status) {
+  double *a = sm;                 // [64][65]
+  double *colp = sm + T * LDS;    // [64]  column p of the current state
+  double *cinv = colp + T;        // [64]  column p divided by the pivot
+  double *pivs = cinv + T;        // [64]  pivots, for the log-determinant
+  __shared__ double s_inv;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  int ei[PIV_PER_THREAD], ej[PIV_PER_THREAD];
+  int ne = 0;
+  for (int e = tid; e < TRI; e += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    ei[ne] = i;
+    ej[ne] = e - i * (i + 1) / 2;
+    ++ne;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int p = 0; p < T; ++p) {
+    if (tid == 0) {
+      const double piv = a[p * LDS + p];
+      const bool ok = (piv > 0.0) && (piv < INFINITY);
+      pivs[p] = ok ? piv : 1.0;
+      s_inv = ok ? 1.0 / piv : 0.0;
+      if (!ok) s_bad = 1;
+    }
+    __syncthreads();
+    if (tid < T) {
+      const double c = (tid >= p) ? a[tid * LDS + p] : a[p * LDS + tid];
+      colp[tid] = c;
+      cinv[tid] = c * s_inv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PIV_PER_THREAD; ++k) {
+      if (k >= ne) break;
+      const int i = ei[k], j = ej[k];
+      double *ap = &a[i * LDS + j];
+      if (i == p) *ap = (j == p) ? -s_inv : cinv[j];
+      else if (j == p) *ap = cinv[i];
+      else *ap = fma(-cinv[i], colp[j], *ap);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    int i = e >> 6, j = e & 63;
+    Pout[e] = -((j <= i) ? a[i * LDS + j] : a[j * LDS + i]);
+  }
+  if (tid < 64) {
+    double l = log(pivs[tid]);
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((tid & 31) == 0) colp[tid >> 5] = l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    *logdet += colp[0] + colp[1];
+    if (s_bad) *status = INLA_ERR_NOT_SPD;
+  }
+}
+
+__device__ __forceinline__ void load_lower_tile(double *a, const double *src, int n_p) {
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    int i = e >> 6, j = e & 63;
+    if (j <= i) a[i * LDS + j] = src[(int64_t)i * n_p + j];
+  }
+}
+
+// Pivot block K (used for K = 0 only: later pivots are inverted by the update
+// kernel of the previous step).  Pbuf holds two 64 x 64 slots per point.
 __global__ void __launch_bounds__(256) gj_pivot_kernel(double *A, int64_t sA, int n_p, int K, double *Pbuf,
                                                       double *logdet, int ld_stride, int *status,
                                                       const int *active) {
   const int b = blockIdx.x;
   if (active && !active[b]) return;
   extern __shared__ double sm[];
-  double *a = sm;                 // [64][65]
-  double *colp = sm + T * LDS;    // [64]
-  double *rowp = colp + T;        // [64]
-  const double *src = A + b * sA + (int64_t)(K * T) * n_p + K * T;
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    int i = e >> 6, j = e & 63;
-    a[i * LDS + j] = src[(int64_t)i * n_p + j];
-  }
+  load_lower_tile(sm, A + b * sA + (int64_t)(K * T) * n_p + K * T, n_p);
   __syncthreads();
-  double ld = 0.0;
-  int bad = 0;
-  for (int p = 0; p < T; ++p) {
-    if (threadIdx.x < T) {
-      colp[threadIdx.x] = a[threadIdx.x * LDS + p];
-      rowp[threadIdx.x] = a[p * LDS + threadIdx.x];
-    }
-    __syncthreads();
-    const double piv = colp[p];
-    const bool ok = (piv > 0.0) && (piv < INFINITY);
-    const double inv = ok ? 1.0 / piv : 0.0;
-    if (!ok) bad = 1;
-    else ld += log(piv);
-    for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-      int i = e >> 6, j = e & 63;
-      double v;
-      if (i == p) v = (j == p) ? -inv : rowp[j] * inv;
-      else if (j == p) v = colp[i] * inv;
-      else v = a[i * LDS + j] - colp[i] * rowp[j] * inv;
-      a[i * LDS + j] = v;
-    }
-    __syncthreads();
-  }
-  double *dst = Pbuf + (int64_t)b * T * T;
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    int i = e >> 6, j = e & 63;
-    dst[e] = -a[i * LDS + j];
-  }
-  if (threadIdx.x == 0) {
-    logdet[(int64_t)b * ld_stride] += ld;
-    if (bad) status[b] = INLA_ERR_NOT_SPD;
-  }
+  sweep_tile(sm, Pbuf + ((int64_t)b * 2 + (K & 1)) * T * T, logdet + (int64_t)b * ld_stride, status + b);
 }
 
 // C_I = A_IK P for every row tile I != K; also keep the old A_IK in Obuf.
@@ -110,7 +150,7 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const double *A, int64_t 
       Os[r * LDS + c] = src[(int64_t)c * n_p + r];
     }
   }
-  const double *Pb = Pbuf + (int64_t)b * T * T;
+  const double *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * T * T;
   for (int e = threadIdx.x; e < T * T; e += blockDim.x) Ps[(e >> 6) * LDS + (e & 63)] = Pb[e];
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -137,19 +177,32 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(const double *A, int64_t 
 }
 
 // Rank-64 update of every lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K;
-// the pivot row/column become C (resp. C^T) and the pivot block -P.
-__global__ void __launch_bounds__(256) gj_update_kernel(double *A, int64_t sA, int n_p, int K, const double *Pbuf,
-                                                       const double *Cbuf, const double *Obuf, int64_t sCO,
+// the pivot row/column become C (resp. C^T) and the pivot block -P.  With
+// lookahead (K + 1 < nt) block 0 takes tile (K+1, K+1) and, once updated,
+// inverts it as the next pivot (slot (K+1)&1 of Pbuf), so no separate pivot
+// launch sits on the critical path.
+__global__ void __launch_bounds__(256) gj_update_kernel(double *A, int64_t sA, int n_p, int K, int nt,
+                                                       double *Pbuf, const double *Cbuf, const double *Obuf,
+                                                       int64_t sCO, double *logdet, int ld_stride, int *status,
                                                        const int *active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
+  const bool look = K + 1 < nt;
   int I, J;
-  tri_index(blockIdx.x, I, J);
+  if (look) {
+    const int nxt = (K + 1) * (K + 2) / 2 + (K + 1);   // linear index of tile (K+1, K+1)
+    int x = blockIdx.x;
+    if (x == 0) x = nxt;
+    else if (x <= nxt) x = x - 1;
+    tri_index(x, I, J);
+  } else {
+    tri_index(blockIdx.x, I, J);
+  }
   double *Ab = A + b * sA;
   double *dst = Ab + (int64_t)(I * T) * n_p + J * T;
   const double *Cb = Cbuf + b * sCO;
   if (I == K && J == K) {
-    const double *Pb = Pbuf + (int64_t)b * T * T;
+    const double *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * T * T;
     for (int e = threadIdx.x; e < T * T; e += blockDim.x) dst[(int64_t)(e >> 6) * n_p + (e & 63)] = -Pb[e];
     return;
   }
@@ -190,13 +243,21 @@ __global__ void __launch_bounds__(256) gj_update_kernel(double *A, int64_t sA, i
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
+  const bool next_pivot = look && I == K + 1 && J == K + 1;
+  if (next_pivot) __syncthreads();   // Cs/Os are reused as the sweep's workspace
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       double *p = dst + (int64_t)(ty + 16 * i) * n_p + tx + 16 * j;
-      *p -= acc[i][j];
+      const double v = *p - acc[i][j];
+      *p = v;
+      if (next_pivot && tx + 16 * j <= ty + 16 * i) sm[(ty + 16 * i) * LDS + tx + 16 * j] = v;
     }
+  if (next_pivot) {
+    __syncthreads();
+    sweep_tile(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * T * T, logdet + (int64_t)b * ld_stride, status + b);
+  }
 }
 
 // A <- -A on the lower triangle, mirrored into the upper triangle.
@@ -283,7 +344,7 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(int n, const double *A, in
 }
 
 constexpr size_t SMEM2 = 2 * T * LDS * sizeof(double);
-constexpr size_t SMEM_PIV = (T * LDS + 2 * T) * sizeof(double);
+constexpr size_t SMEM_PIV = SWEEP_SMEM_DOUBLES * sizeof(double);
 
 bool g_attr_done = false;
 void ensure_attrs() {
@@ -304,11 +365,13 @@ void gj_invert(Launch &L, const DevModel &M, const Work &W, double *A, int64_t s
   const int ntri = nt * (nt + 1) / 2;
   const int64_t sCO = (int64_t)n_p * T;
   for (int K = 0; K < nt; ++K) {
-    L.start(KID_GJ_PIVOT, (double)P);
-    gj_pivot_kernel<<<P, 256, SMEM_PIV, L.st>>>(A, strideA, n_p, K, W.gjP, logdet_out, logdet_slot_stride,
-                                                 W.status, W.active);
-    L.stop();
-    L.tick();
+    if (K == 0) {
+      L.start(KID_GJ_PIVOT, (double)P);
+      gj_pivot_kernel<<<P, 256, SMEM_PIV, L.st>>>(A, strideA, n_p, K, W.gjP, logdet_out, logdet_slot_stride,
+                                                   W.status, W.active);
+      L.stop();
+      L.tick();
+    }
     if (nt > 1) {
       L.start(KID_GJ_PANEL, (double)P * (nt - 1));
       gj_panel_kernel<<<dim3(nt, P), 256, SMEM2, L.st>>>(A, strideA, n_p, K, W.gjP, W.gjC, W.gjO, sCO, W.active);
@@ -317,8 +380,8 @@ void gj_invert(Launch &L, const DevModel &M, const Work &W, double *A, int64_t s
     }
     // units: rank-64 updates of one 64 x 64 tile (2 * 64^3 flops each)
     L.start(KID_GJ_UPDATE, (double)P * (ntri - nt));
-    gj_update_kernel<<<dim3(ntri, P), 256, SMEM2, L.st>>>(A, strideA, n_p, K, W.gjP, W.gjC, W.gjO, sCO,
-                                                           W.active);
+    gj_update_kernel<<<dim3(ntri, P), 256, SMEM2, L.st>>>(A, strideA, n_p, K, nt, W.gjP, W.gjC, W.gjO, sCO,
+                                                           logdet_out, logdet_slot_stride, W.status, W.active);
     L.stop();
     L.tick();
   }

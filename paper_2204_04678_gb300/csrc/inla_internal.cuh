@@ -83,7 +83,7 @@ struct Work {
   double *wv;            // [P][1+n_b][n_p]  Dinv_t times vectors
   double *T1, *S, *SigN, *SigC;          // [P][n_p][n_p]
   double *SigAn, *SigAc, *Y;             // [P][n_b][n_p]
-  double *gjP, *gjC, *gjO;               // [P][64*64], [P][n_p*64], [P][n_p*64]
+  double *gjP, *gjC, *gjO;               // [P][2][64*64], [P][n_p*64], [P][n_p*64]
   double *sc;            // [P][SC_COUNT] per-point scalars
   double *pt;            // [P][n_t][PT_COUNT] per-time-block contractions
   double *part;          // [P][NPART][4] partial sums
