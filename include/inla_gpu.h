@@ -158,6 +158,29 @@ int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *o
 int inla_eval_batch(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
                     const inla_eval_out *out, void *stream);
 
+/* No counterpart in the paper: a variant of inla_eval_batch that allocates no
+ * device memory, for callers that cannot call cudaMalloc once they are
+ * running -- a serving loop that must keep a fixed device-memory footprint
+ * after start-up, or a plugin inside a host framework whose own caching
+ * allocator owns the device memory, so that a raw cudaMalloc could fail or
+ * fragment that pool.  Its workspace is one array of INLA_STATIC_SCRATCH_BYTES
+ * (64 MiB) that the library reserves in device memory on every GPU that
+ * loads it, until the process exits; the model itself (inla_model_create)
+ * still allocates, so create models at start-up.
+ * Arguments, outputs and results are those of inla_eval_batch.  The whole
+ * batch must fit in the array in one pass: inla_workspace_bytes() plus
+ * about 96 bytes per point (B points, or 9 B with central differences) up
+ * to 64 MiB; a larger batch returns INLA_ERR_ARG and does nothing.
+ * The first call on a device looks up the array's device address with that
+ * device current (no allocation); make that first call before any stream
+ * capture.  All calls on a device share the array, which keeps the last
+ * call's contents (every call clears what it needs); calls on one model are
+ * ordered like inla_eval_batch, but calls from two models that overlap on
+ * the GPU race on the array.  Errors as for inla_eval_batch. */
+#define INLA_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+int inla_eval_batch_static(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
+                           const inla_eval_out *out, void *stream);
+
 /* Same as inla_eval_batch with HOST buffers: copies theta to the device,
  * evaluates on the model's internal stream, copies the results back and
  * synchronises.  theta: HOST [B][4]. */

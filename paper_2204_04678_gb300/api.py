@@ -143,6 +143,38 @@ class Model:
                                          c_void_p(stream.cuda_stream)))
         return out
 
+    def eval_static(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False,
+                    max_newton=50, newton_tol=1e-8, fd_eps=1e-3, stream=None):
+        """Same as eval() through inla_eval_batch_static: the library's fixed
+        device array serves as the workspace, so the call allocates no device
+        memory (the output tensors are allocated here, by torch)."""
+        import torch
+        theta = theta.contiguous()
+        B = theta.shape[0]
+        dev = theta.device
+        out = dict(f=torch.empty(B, dtype=torch.float64, device=dev),
+                   status=torch.empty(B, dtype=torch.int32, device=dev),
+                   newton_iters=torch.empty(B, dtype=torch.int32, device=dev))
+        if grad != "none":
+            out["grad"] = torch.empty(B, 4, dtype=torch.float64, device=dev)
+        if want_mode:
+            out["x_mode"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
+        if want_marg_var:
+            out["marg_var"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps)
+        so = C.inla_eval_out()
+        so.f_dev = out["f"].data_ptr()
+        so.status_dev = out["status"].data_ptr()
+        so.newton_iters_dev = out["newton_iters"].data_ptr()
+        so.grad_dev = out["grad"].data_ptr() if "grad" in out else None
+        so.x_mode_dev = out["x_mode"].data_ptr() if "x_mode" in out else None
+        so.marg_var_dev = out["marg_var"].data_ptr() if "marg_var" in out else None
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        C.check(self.lib.inla_eval_batch_static(self.handle, int(B), c_void_p(theta.data_ptr()), byref(o),
+                                                byref(so), c_void_p(stream.cuda_stream)))
+        return out
+
     def eval_host(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False,
                   max_newton=50, newton_tol=1e-8, fd_eps=1e-3):
         """Evaluate with HOST numpy buffers (copies in and out inside the call)."""

@@ -29,6 +29,8 @@ KERNEL_GEMM = 1
 KERNEL_GJ_PIVOT = 2
 KERNEL_GJ_PANEL = 3
 
+STATIC_SCRATCH_BYTES = 64 << 20
+
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD",
                 5: "ERR_NO_CONVERGENCE", 7: "ERR_UNSUPPORTED"}
 
@@ -64,6 +66,8 @@ SIGNATURES = {
     "inla_workspace_bytes": (c_int, [c_void_p, c_int, POINTER(inla_eval_opts), POINTER(c_size_t)]),
     "inla_eval_batch": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts), POINTER(inla_eval_out),
                                 c_void_p]),
+    "inla_eval_batch_static": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts), POINTER(inla_eval_out),
+                                       c_void_p]),
     "inla_eval_batch_host": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts),
                                      POINTER(inla_eval_out_host)]),
     "inla_model_latent_dim": (c_int64, [c_void_p]),

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <stdexcept>
 #include <string>
@@ -769,6 +770,91 @@ int guarded(F &&f) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ no-allocation variant
+//
+// inla_eval_batch_static runs the same evaluation with its workspace in this
+// fixed array instead of memory from cudaMalloc.  Every GPU that loads the
+// library holds the array until the process exits.  Host code must not use
+// the symbol as an address: the device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_static_scratch[INLA_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_static_mu;
+void *g_static_addr[256] = {};
+
+void *static_scratch(int device) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (device < 0 || device >= 256) throw ApiError(INLA_ERR_ARG, "device index out of range");
+  if (!g_static_addr[device]) {
+    void *p = nullptr;
+    CUDA_OK(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[device] = p;
+  }
+  return g_static_addr[device];
+}
+
+int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const inla_eval_opts *opts,
+                         const inla_eval_out *out, cudaStream_t st) {
+  if (!mdl || !opts || !out || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
+  if (!out->f_dev || !out->status_dev) throw ApiError(INLA_ERR_ARG, "f_dev and status_dev are required");
+  if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_ADJOINT) throw ApiError(INLA_ERR_ARG, "bad grad mode");
+  if (opts->prior_mode != INLA_PRIOR_KRONECKER && opts->prior_mode != INLA_PRIOR_BTA)
+    throw ApiError(INLA_ERR_ARG, "bad prior mode");
+  if (opts->precision != INLA_FP64) throw ApiError(INLA_ERR_UNSUPPORTED, "only INLA_FP64 is available");
+  if (opts->grad != INLA_GRAD_NONE && !out->grad_dev) throw ApiError(INLA_ERR_ARG, "grad_dev required");
+  if (opts->want_mode && !out->x_mode_dev) throw ApiError(INLA_ERR_ARG, "x_mode_dev required");
+  if (opts->want_marg_var && !out->marg_var_dev) throw ApiError(INLA_ERR_ARG, "marg_var_dev required");
+  const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+  const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
+  const int64_t P_total = (int64_t)B * per;
+  // the whole batch is one wave: workspace, then the per-point batch arrays
+  const int64_t ws_bytes = point_bytes(mdl->M) * P_total;
+  const int64_t bb_bytes = rup(32 * P_total, 256) + rup(8 * P_total, 256) + rup(32 * P_total, 256) +
+                           3 * rup(4 * P_total, 256);
+  if (P_total > 65535 || ws_bytes + bb_bytes > (int64_t)INLA_STATIC_SCRATCH_BYTES)
+    throw ApiError(INLA_ERR_ARG, "batch needs " + std::to_string(ws_bytes + bb_bytes) +
+                                     " bytes of scratch; the static array holds " +
+                                     std::to_string((long long)INLA_STATIC_SCRATCH_BYTES));
+  CUDA_OK(cudaSetDevice(mdl->device));
+  char *base = static_cast<char *>(static_scratch(mdl->device));
+  mdl->launches = 0;
+  Launch L{st, &mdl->launches, nullptr};
+  if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
+  Work W0 = carve(mdl->M, base, (int)P_total);
+  char *p = base + ws_bytes;
+  auto take = [&](int64_t bytes) { char *r = p; p += rup(bytes, 256); return r; };
+  BatchBufs bb;
+  bb.theta_all = reinterpret_cast<double *>(take(32 * P_total));
+  bb.f_all = reinterpret_cast<double *>(take(8 * P_total));
+  bb.grad_all = reinterpret_cast<double *>(take(32 * P_total));
+  bb.point_out = reinterpret_cast<int *>(take(4 * P_total));
+  bb.status_all = reinterpret_cast<int *>(take(4 * P_total));
+  bb.iters_all = reinterpret_cast<int *>(take(4 * P_total));
+  point_out_kernel<<<(unsigned)((P_total + 127) / 128), 128, 0, st>>>((int)P_total, per, bb.point_out);
+  L.tick();
+  if (per == 9) k_fd_points(L, B, theta_dev, eps, bb.theta_all);
+  else CUDA_OK(cudaMemcpyAsync(bb.theta_all, theta_dev, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
+  int centre_flags = 0;
+  if (opts->want_marg_var || opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 1;
+  if (opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 2;
+  Work W = W0;
+  W.P = (int)P_total;
+  CUDA_OK(cudaMemcpyAsync(W.theta, bb.theta_all, sizeof(double) * 4 * P_total, cudaMemcpyDeviceToDevice, st));
+  run_wave(mdl, L, W, *opts, 0, bb, opts->want_mode ? out->x_mode_dev : nullptr,
+           opts->want_marg_var ? out->marg_var_dev : nullptr, centre_flags);
+  k_outputs(L, B, per, eps, 4, bb.f_all, opts->grad == INLA_GRAD_ADJOINT ? bb.grad_all : nullptr, bb.status_all,
+            bb.iters_all, out->f_dev, opts->grad != INLA_GRAD_NONE ? out->grad_dev : nullptr, out->status_dev,
+            out->newton_iters_dev);
+  CUDA_OK(cudaEventRecord(mdl->done, st));
+  mdl->done_valid = true;
+  CUDA_OK(cudaGetLastError());
+  return mdl->launches;
+}
+
+}  // namespace
+
 extern "C" {
 
 int inla_model_create(const inla_model_desc *desc, int device, inla_model **out) {
@@ -790,6 +876,11 @@ int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *o
 int inla_eval_batch(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
                     const inla_eval_out *out, void *stream) {
   return guarded([&] { eval_impl(model, B, theta_dev, opts, out, static_cast<cudaStream_t>(stream)); });
+}
+
+int inla_eval_batch_static(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
+                           const inla_eval_out *out, void *stream) {
+  return guarded([&] { eval_static_impl(model, B, theta_dev, opts, out, static_cast<cudaStream_t>(stream)); });
 }
 
 int inla_eval_batch_host(inla_model *model, int B, const double *theta, const inla_eval_opts *opts,
