@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--grad", default="fd", choices=["fd", "adjoint"],
                     help="fd: one f+grad from the 9-point stencil per step (the workload's definition); "
                          "adjoint: the 9 stencil points each get f and an adjoint gradient")
+    ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
+    ap.add_argument("--centres", type=int, default=1, help="stencil centres per step (FD mode)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--evals", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -207,13 +209,18 @@ def main():
     cfg = args.config
     peak_fp64 = pkg.measure_fp64_peak(local, tensor=False)
     peak_dmma = pkg.measure_fp64_peak(local, tensor=True)
-    mdl = config_model(cfg)
+    if args.nt:
+        from synth import CONFIGS, build
+        mdl = build(**dict(CONFIGS[cfg], n_t=args.nt, name="profiling case"))
+    else:
+        mdl = config_model(cfg)
     centre = theta_batch(cfg, mdl)[0] + 0.01 * rank
     model = pkg.Model(mdl, device=local)
     stream = torch.cuda.current_stream()
     if args.grad == "fd":
-        theta = torch.tensor(centre[None, :], dtype=torch.float64, device="cuda")
-        per_step = 1
+        cen = centre[None, :] + 0.01 * np.arange(args.centres)[:, None]
+        theta = torch.tensor(cen, dtype=torch.float64, device="cuda")
+        per_step = args.centres
     else:
         from synth import fd_stencil
         theta = torch.tensor(fd_stencil(centre), dtype=torch.float64, device="cuda")
@@ -294,6 +301,7 @@ def main():
         except Exception as e:  # reported, not fatal
             cpu = {"value": None, "error": str(e)[:200]}
 
+    line = {}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -305,7 +313,11 @@ def main():
                 "fp64_peaks_tflops": {"fma": peak_fp64, "dmma": peak_dmma},
                 "gemm_kernel": {"ms": gms, "launches": gnl,
                                 "tflops": gunits * flop_per_unit / (gms / 1e3) / 1e12 if gms else None}}
-        print(json.dumps(line))
+        if not (args.nt or args.centres != 1):
+            print(json.dumps(line))
+    if args.nt or args.centres != 1:
+        line["config"]["workload"] = f"profiling case: n_t={mdl.n_t}, {args.centres} stencil centres per step"
+        print(json.dumps(line)) if rank == 0 else None
     model.close()
     if dist:
         dist.destroy_process_group()

@@ -143,13 +143,15 @@ __global__ void init_step0_kernel(DevModel M, Work W, int mode) {
 
 // Dense diagonal block: D_t = c_t Q_s + (likelihood block) - [schur] q_off^2 Q_s T1,
 // with T1 = Dinv_{t-1} Q_s; identity in the padding.  mode ASM_QS builds Q_s alone.
+// Only the lower 32-wide tiles are written: the block sweep reads nothing else.
+constexpr int SWEEP_TILE = 32;
 __global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, double *dst, int64_t sdst, int schur) {
   const int b = blockIdx.z;
   if (!W.active[b]) return;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_p = M.n_p, n_s = M.n_s;
-  if (j >= n_p) return;
+  if (j >= n_p || j >= (i / SWEEP_TILE + 1) * SWEEP_TILE) return;
   double *out = dst + b * sdst + (int64_t)i * n_p + j;
   if (i >= n_s || j >= n_s) {
     *out = (i == j) ? 1.0 : 0.0;
@@ -178,14 +180,17 @@ __global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, double
 }
 
 // out[i][j] = coef * sum_k X[i][k] Q_s[k][j] + sum_l SigA[l][i] Rt[l][j]   (i, j < n_s; 0 elsewhere)
+// lower_band: only columns j < (floor((i + pbw) / 32) + 1) * 32, the ones the
+// lower-tile assembly of rows within the pattern bandwidth of i reads.
 __global__ void sparse_right_kernel(DevModel M, Work W, const double *X, int64_t sX, double *outp, int64_t sOut,
-                                    int coef_qoff, const double *SigA, const double *Rt_t) {
+                                    int coef_qoff, const double *SigA, const double *Rt_t, int lower_band) {
   const int b = blockIdx.z;
   if (!W.active[b]) return;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_p = M.n_p, n_s = M.n_s;
   if (j >= n_p) return;
+  if (lower_band && j >= ((i + M.pbw) / SWEEP_TILE + 1) * SWEEP_TILE) return;
   double *out = outp + b * sOut + (int64_t)i * n_p + j;
   if (i >= n_s || j >= n_s) { *out = 0.0; return; }
   const double *Xi = X + b * sX + (int64_t)i * n_p;
@@ -1005,9 +1010,10 @@ void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mod
   L.tick();
 }
 void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
-                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t) {
+                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band) {
   sparse_right_kernel<<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
-                                                                               coef_qoff ? 1 : 0, SigA, Rt_t);
+                                                                               coef_qoff ? 1 : 0, SigA, Rt_t,
+                                                                               lower_band ? 1 : 0);
   L.tick();
 }
 void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,

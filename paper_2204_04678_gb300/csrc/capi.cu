@@ -262,6 +262,10 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     }
     const int nnz = prow[n_s];
     M.nnz = nnz;
+    int pbw = 0;
+    for (int i = 0; i < n_s; ++i)
+      for (int e = prow[i]; e < prow[i + 1]; ++e) pbw = std::max(pbw, std::abs(pcol[e] - i));
+    M.pbw = pbw;
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);
@@ -563,7 +567,7 @@ void factor(Launch &L, const DevModel &M, const Work &W, int mode, int ld_slot) 
         k_arrow_update(L, M, W, t, mode);
         k_arrow_dots(L, M, W, t - 1);
       }
-      k_sparse_right(L, M, W, Dp, W.sDinv, W.T1, W.sMat, false, nullptr, nullptr);
+      k_sparse_right(L, M, W, Dp, W.sDinv, W.T1, W.sMat, false, nullptr, nullptr, true);
     }
     k_assemble_diag(L, M, W, t, mode, Dt, W.sDinv, t > 0);
     gj_invert(L, M, W, Dt, W.sDinv, W.sc + ld_slot, SC_COUNT);

@@ -10,9 +10,9 @@
 //    and after all pivot blocks A holds -A^-1; the pivots are the successive
 //    Schur complements, so log|A| = sum_K log|pivot_K| and a non-positive
 //    pivot means A is not positive definite.  Each sweep step is one small
-//    pivot inversion followed by a rank-64 update of the whole lower
-//    triangle, which spreads over every SM (no triangular solves on the
-//    critical path).  Work: n^3 flops, the same as Cholesky + inverse.
+//    (32 x 32) pivot inversion followed by a rank-32 update of the whole
+//    lower triangle, which spreads over every SM (no triangular solves on
+//    the critical path).  Work: n^3 flops, the same as Cholesky + inverse.
 // 2. C = alpha A B + beta C0 for the selected-inversion products.
 //
 // The kernels are bound by the FP64 pipe; all operand traffic is staged
@@ -28,34 +28,44 @@ namespace {
 constexpr int T = TILE;     // 64
 constexpr int LDS = T + 1;  // padded shared-memory row
 
+// Row and column of the x-th lower tile.  Single-precision square root plus an
+// integer correction: no instruction of this lands on the FP64 pipe, which
+// the tile products saturate.
 __device__ __forceinline__ void tri_index(int x, int &I, int &J) {
-  int i = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+  int i = (int)((sqrtf(8.0f * (float)x + 1.0f) - 1.0f) * 0.5f);
   while ((i + 1) * (i + 2) / 2 <= x) ++i;
   while (i * (i + 1) / 2 > x) --i;
   I = i;
   J = x - i * (i + 1) / 2;
 }
 
-// Scalar sweep of a 64 x 64 SPD block held (lower triangle) in shared memory `a`:
-// after 64 steps `a` holds -A^-1.  Writes P = A^-1 (full symmetric tile) to Pout and
-// adds log|A| = sum_p log(pivot_p) to *logdet; a non-positive pivot sets *status.
-// One FMA per lower entry and step; the reciprocal of each pivot is formed once
-// and the logarithms once at the end.  Called by all threads of the block.
-constexpr int TRI = T * (T + 1) / 2;             // 2080 lower entries
-constexpr int PIV_PER_THREAD = (TRI + 255) / 256;
-constexpr int SWEEP_SMEM_DOUBLES = T * LDS + 3 * T;
+// ---------------------------------------------------------------- block sweep
+// Pivot blocks and update tiles are 32 x 32 (GT); a block of 128 threads
+// owns one tile, so one update launch has P * nt(nt+1)/2 small blocks that
+// balance well over 152 SMs (up to 16 resident blocks per SM).
+constexpr int GT = 32;
+constexpr int GLD = GT + 1;
+constexpr int GTHREADS = 128;
+constexpr int GTRI = GT * (GT + 1) / 2;                    // 528 lower entries
+constexpr int GPER = (GTRI + GTHREADS - 1) / GTHREADS;     // entries per thread
+constexpr int SWEEP_SMEM_DOUBLES = GT * GLD + 3 * GT;
 
+// Scalar sweep of a 32 x 32 SPD block held (lower triangle) in shared memory:
+// after 32 steps it holds -A^-1.  Writes P = A^-1 (full symmetric tile) to
+// Pout and adds log|A| = sum_p log(pivot_p) to *logdet; a non-positive pivot
+// sets *status.  One FMA per lower entry and step; one reciprocal per step;
+// the logarithms once at the end.  Called by all GTHREADS threads.
 __device__ void sweep_tile(double *sm, double *Pout, double *logdet, int *status) {
-  double *a = sm;                 // [64][65]
-  double *colp = sm + T * LDS;    // [64]  column p of the current state
-  double *cinv = colp + T;        // [64]  column p divided by the pivot
-  double *pivs = cinv + T;        // [64]  pivots, for the log-determinant
+  double *a = sm;                  // [32][33]
+  double *colp = sm + GT * GLD;    // [32]  column p of the current state
+  double *cinv = colp + GT;        // [32]  column p divided by the pivot
+  double *pivs = cinv + GT;        // [32]  pivots
   __shared__ double s_inv;
   __shared__ int s_bad;
   const int tid = threadIdx.x;
-  int ei[PIV_PER_THREAD], ej[PIV_PER_THREAD];
+  int ei[GPER], ej[GPER];
   int ne = 0;
-  for (int e = tid; e < TRI; e += blockDim.x) {
+  for (int e = tid; e < GTRI; e += GTHREADS) {
     int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
     while ((i + 1) * (i + 2) / 2 <= e) ++i;
     while (i * (i + 1) / 2 > e) --i;
@@ -65,126 +75,121 @@ __device__ void sweep_tile(double *sm, double *Pout, double *logdet, int *status
   }
   if (tid == 0) s_bad = 0;
   __syncthreads();
-  for (int p = 0; p < T; ++p) {
+  for (int p = 0; p < GT; ++p) {
     if (tid == 0) {
-      const double piv = a[p * LDS + p];
+      const double piv = a[p * GLD + p];
       const bool ok = (piv > 0.0) && (piv < INFINITY);
       pivs[p] = ok ? piv : 1.0;
       s_inv = ok ? 1.0 / piv : 0.0;
       if (!ok) s_bad = 1;
     }
     __syncthreads();
-    if (tid < T) {
-      const double c = (tid >= p) ? a[tid * LDS + p] : a[p * LDS + tid];
+    if (tid < GT) {
+      const double c = (tid >= p) ? a[tid * GLD + p] : a[p * GLD + tid];
       colp[tid] = c;
       cinv[tid] = c * s_inv;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < PIV_PER_THREAD; ++k) {
+    for (int k = 0; k < GPER; ++k) {
       if (k >= ne) break;
       const int i = ei[k], j = ej[k];
-      double *ap = &a[i * LDS + j];
+      double *ap = &a[i * GLD + j];
       if (i == p) *ap = (j == p) ? -s_inv : cinv[j];
       else if (j == p) *ap = cinv[i];
       else *ap = fma(-cinv[i], colp[j], *ap);
     }
     __syncthreads();
   }
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    int i = e >> 6, j = e & 63;
-    Pout[e] = -((j <= i) ? a[i * LDS + j] : a[j * LDS + i]);
+  for (int e = tid; e < GT * GT; e += GTHREADS) {
+    const int i = e >> 5, j = e & 31;
+    Pout[e] = -((j <= i) ? a[i * GLD + j] : a[j * GLD + i]);
   }
-  if (tid < 64) {
+  if (tid < 32) {
     double l = log(pivs[tid]);
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((tid & 31) == 0) colp[tid >> 5] = l;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    *logdet += colp[0] + colp[1];
-    if (s_bad) *status = INLA_ERR_NOT_SPD;
+    if (tid == 0) {
+      *logdet += l;
+      if (s_bad) *status = INLA_ERR_NOT_SPD;
+    }
   }
 }
 
-__device__ __forceinline__ void load_lower_tile(double *a, const double *src, int n_p) {
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    int i = e >> 6, j = e & 63;
-    if (j <= i) a[i * LDS + j] = src[(int64_t)i * n_p + j];
-  }
-}
-
-// Pivot block K (used for K = 0 only: later pivots are inverted by the update
-// kernel of the previous step).  Pbuf holds two 64 x 64 slots per point.
-__global__ void __launch_bounds__(256) gj_pivot_kernel(double *A, int64_t sA, int n_p, int K, double *Pbuf,
-                                                      double *logdet, int ld_stride, int *status,
-                                                      const int *active) {
+// Pivot block 0 of an inversion (later pivots are inverted by the update
+// kernel of the previous step).  Pbuf holds two 32 x 32 slots per point.
+__global__ void __launch_bounds__(GTHREADS) gj_pivot_kernel(double *A, int64_t sA, int n_p, int K, double *Pbuf,
+                                                           double *logdet, int ld_stride, int *status,
+                                                           const int *active) {
   const int b = blockIdx.x;
   if (active && !active[b]) return;
   extern __shared__ double sm[];
-  load_lower_tile(sm, A + b * sA + (int64_t)(K * T) * n_p + K * T, n_p);
+  const double *src = A + b * sA + (int64_t)(K * GT) * n_p + K * GT;
+  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
+    const int i = e >> 5, j = e & 31;
+    if (j <= i) sm[i * GLD + j] = src[(int64_t)i * n_p + j];
+  }
   __syncthreads();
-  sweep_tile(sm, Pbuf + ((int64_t)b * 2 + (K & 1)) * T * T, logdet + (int64_t)b * ld_stride, status + b);
+  sweep_tile(sm, Pbuf + ((int64_t)b * 2 + (K & 1)) * GT * GT, logdet + (int64_t)b * ld_stride, status + b);
 }
 
-// C_I = A_IK P for every row tile I != K; also keep the old A_IK in Obuf.
-__global__ void __launch_bounds__(256) gj_panel_kernel(const double *A, int64_t sA, int n_p, int K,
-                                                      const double *Pbuf, double *Cbuf, double *Obuf,
-                                                      int64_t sCO, const int *active) {
+// C_I = A_IK P for every row tile I != K; the old A_IK is kept in Obuf.
+__global__ void __launch_bounds__(GTHREADS) gj_panel_kernel(const double *A, int64_t sA, int n_p, int K,
+                                                           const double *Pbuf, double *Cbuf, double *Obuf,
+                                                           int64_t sCO, const int *active) {
   const int I = blockIdx.x, b = blockIdx.y;
   if (I == K || (active && !active[b])) return;
   extern __shared__ double sm[];
-  double *Os = sm;              // [64][65]  O[r][k]
-  double *Ps = sm + T * LDS;    // [64][65]  P[k][c]
+  double *Os = sm;               // [32][33]  O[r][k]
+  double *Ps = sm + GT * GLD;    // [32][33]  P[k][c]
   const double *Ab = A + b * sA;
   if (I > K) {
-    const double *src = Ab + (int64_t)(I * T) * n_p + K * T;
-    for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-      int r = e >> 6, c = e & 63;
-      Os[r * LDS + c] = src[(int64_t)r * n_p + c];
+    const double *src = Ab + (int64_t)(I * GT) * n_p + K * GT;
+    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
+      const int r = e >> 5, c = e & 31;
+      Os[r * GLD + c] = src[(int64_t)r * n_p + c];
     }
   } else {  // upper tile (I, K) = transpose of the stored lower tile (K, I)
-    const double *src = Ab + (int64_t)(K * T) * n_p + I * T;
-    for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-      int c = e >> 6, r = e & 63;
-      Os[r * LDS + c] = src[(int64_t)c * n_p + r];
+    const double *src = Ab + (int64_t)(K * GT) * n_p + I * GT;
+    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
+      const int c = e >> 5, r = e & 31;
+      Os[r * GLD + c] = src[(int64_t)c * n_p + r];
     }
   }
-  const double *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * T * T;
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) Ps[(e >> 6) * LDS + (e & 63)] = Pb[e];
+  const double *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * GT * GT;
+  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) Ps[(e >> 5) * GLD + (e & 31)] = Pb[e];
   __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
-#pragma unroll 4
-  for (int k = 0; k < T; ++k) {
-    double av[4], bv[4];
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // rows ty + 16 i, cols tx + 8 j
+  double acc[2][4] = {};
+#pragma unroll 8
+  for (int k = 0; k < GT; ++k) {
+    double av[2], bv[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) av[i] = Os[(ty + 16 * i) * LDS + k];
+    for (int i = 0; i < 2; ++i) av[i] = Os[(ty + 16 * i) * GLD + k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bv[j] = Ps[k * LDS + tx + 16 * j];
+    for (int j = 0; j < 4; ++j) bv[j] = Ps[k * GLD + tx + 8 * j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
-  double *Cb = Cbuf + b * sCO + (int64_t)(I * T) * T;
-  double *Ob = Obuf + b * sCO + (int64_t)(I * T) * T;
+  double *Cb = Cbuf + b * sCO + (int64_t)(I * GT) * GT;
+  double *Ob = Obuf + b * sCO + (int64_t)(I * GT) * GT;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Cb[(ty + 16 * i) * T + tx + 16 * j] = acc[i][j];
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) Ob[e] = Os[(e >> 6) * LDS + (e & 63)];
+    for (int j = 0; j < 4; ++j) Cb[(ty + 16 * i) * GT + tx + 8 * j] = acc[i][j];
+  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) Ob[e] = Os[(e >> 5) * GLD + (e & 31)];
 }
 
-// Rank-64 update of every lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K;
+// Rank-32 update of every lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K;
 // the pivot row/column become C (resp. C^T) and the pivot block -P.  With
 // lookahead (K + 1 < nt) block 0 takes tile (K+1, K+1) and, once updated,
 // inverts it as the next pivot (slot (K+1)&1 of Pbuf), so no separate pivot
 // launch sits on the critical path.
-__global__ void __launch_bounds__(256) gj_update_kernel(double *A, int64_t sA, int n_p, int K, int nt,
-                                                       double *Pbuf, const double *Cbuf, const double *Obuf,
-                                                       int64_t sCO, double *logdet, int ld_stride, int *status,
-                                                       const int *active) {
+__global__ void __launch_bounds__(GTHREADS) gj_update_kernel(double *A, int64_t sA, int n_p, int K, int nt,
+                                                            double *Pbuf, const double *Cbuf, const double *Obuf,
+                                                            int64_t sCO, double *logdet, int ld_stride, int *status,
+                                                            const int *active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const bool look = K + 1 < nt;
@@ -198,65 +203,68 @@ __global__ void __launch_bounds__(256) gj_update_kernel(double *A, int64_t sA, i
   } else {
     tri_index(blockIdx.x, I, J);
   }
-  double *Ab = A + b * sA;
-  double *dst = Ab + (int64_t)(I * T) * n_p + J * T;
+  double *dst = A + b * sA + (int64_t)(I * GT) * n_p + J * GT;
   const double *Cb = Cbuf + b * sCO;
   if (I == K && J == K) {
-    const double *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * T * T;
-    for (int e = threadIdx.x; e < T * T; e += blockDim.x) dst[(int64_t)(e >> 6) * n_p + (e & 63)] = -Pb[e];
+    const double *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * GT * GT;
+    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) dst[(int64_t)(e >> 5) * n_p + (e & 31)] = -Pb[e];
     return;
   }
   if (J == K) {  // tile (I, K), I > K
-    const double *src = Cb + (int64_t)(I * T) * T;
-    for (int e = threadIdx.x; e < T * T; e += blockDim.x) dst[(int64_t)(e >> 6) * n_p + (e & 63)] = src[e];
+    const double *src = Cb + (int64_t)(I * GT) * GT;
+    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) dst[(int64_t)(e >> 5) * n_p + (e & 31)] = src[e];
     return;
   }
   if (I == K) {  // tile (K, J), J < K: transpose of C_J
-    const double *src = Cb + (int64_t)(J * T) * T;
-    for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-      int c = e >> 6, r = e & 63;  // read C_J[c][r] coalesced, write dst[r][c]
-      dst[(int64_t)r * n_p + c] = src[c * T + r];
+    const double *src = Cb + (int64_t)(J * GT) * GT;
+    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
+      const int c = e >> 5, r = e & 31;
+      dst[(int64_t)r * n_p + c] = src[c * GT + r];
     }
     return;
   }
   extern __shared__ double sm[];
-  double *Cs = sm;            // [64][65]  C_I[r][k]
-  double *Os = sm + T * LDS;  // [64][65]  O_J[c][k]
-  const double *ci = Cb + (int64_t)(I * T) * T;
-  const double *oj = Obuf + b * sCO + (int64_t)(J * T) * T;
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    Cs[(e >> 6) * LDS + (e & 63)] = ci[e];
-    Os[(e >> 6) * LDS + (e & 63)] = oj[e];
+  double *Cs = sm;               // [32][33]  C_I[r][k]
+  double *Os = sm + GT * GLD;    // [32][33]  O_J[c][k]
+  const double *ci = Cb + (int64_t)(I * GT) * GT;
+  const double *oj = Obuf + b * sCO + (int64_t)(J * GT) * GT;
+  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
+    Cs[(e >> 5) * GLD + (e & 31)] = ci[e];
+    Os[(e >> 5) * GLD + (e & 31)] = oj[e];
   }
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  double acc[2][4];   // starts at A_IJ; each step subtracts with one FMA
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = dst[(int64_t)(ty + 16 * i) * n_p + tx + 8 * j];
   __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
-#pragma unroll 4
-  for (int k = 0; k < T; ++k) {
-    double av[4], bv[4];
+#pragma unroll 8
+  for (int k = 0; k < GT; ++k) {
+    double av[2], bv[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) av[i] = Cs[(ty + 16 * i) * LDS + k];
+    for (int i = 0; i < 2; ++i) av[i] = -Cs[(ty + 16 * i) * GLD + k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bv[j] = Os[(tx + 16 * j) * LDS + k];
+    for (int j = 0; j < 4; ++j) bv[j] = Os[(tx + 8 * j) * GLD + k];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
   const bool next_pivot = look && I == K + 1 && J == K + 1;
   if (next_pivot) __syncthreads();   // Cs/Os are reused as the sweep's workspace
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      double *p = dst + (int64_t)(ty + 16 * i) * n_p + tx + 16 * j;
-      const double v = *p - acc[i][j];
-      *p = v;
-      if (next_pivot && tx + 16 * j <= ty + 16 * i) sm[(ty + 16 * i) * LDS + tx + 16 * j] = v;
+      const int r = ty + 16 * i, c = tx + 8 * j;
+      dst[(int64_t)r * n_p + c] = acc[i][j];
+      if (next_pivot && c <= r) sm[r * GLD + c] = acc[i][j];
     }
   if (next_pivot) {
     __syncthreads();
-    sweep_tile(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * T * T, logdet + (int64_t)b * ld_stride, status + b);
+    sweep_tile(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * GT * GT, logdet + (int64_t)b * ld_stride,
+               status + b);
   }
 }
 
@@ -344,13 +352,12 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(int n, const double *A, in
 }
 
 constexpr size_t SMEM2 = 2 * T * LDS * sizeof(double);
+constexpr size_t GSMEM2 = 2 * GT * GLD * sizeof(double);
 constexpr size_t SMEM_PIV = SWEEP_SMEM_DOUBLES * sizeof(double);
 
 bool g_attr_done = false;
 void ensure_attrs() {
   if (g_attr_done) return;
-  cudaFuncSetAttribute(gj_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM2);
-  cudaFuncSetAttribute(gj_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM2);
   cudaFuncSetAttribute(gemm_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM2);
   cudaFuncSetAttribute(gj_pivot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_PIV);
   g_attr_done = true;
@@ -361,31 +368,33 @@ void ensure_attrs() {
 void gj_invert(Launch &L, const DevModel &M, const Work &W, double *A, int64_t strideA, double *logdet_out,
                int logdet_slot_stride) {
   ensure_attrs();
-  const int n_p = M.n_p, nt = n_p / T, P = W.P;
+  const int n_p = M.n_p, nt = n_p / GT, P = W.P;
   const int ntri = nt * (nt + 1) / 2;
-  const int64_t sCO = (int64_t)n_p * T;
+  const int64_t sCO = (int64_t)n_p * GT;
+  const int tnt = n_p / T, tntri = tnt * (tnt + 1) / 2;
   for (int K = 0; K < nt; ++K) {
     if (K == 0) {
       L.start(KID_GJ_PIVOT, (double)P);
-      gj_pivot_kernel<<<P, 256, SMEM_PIV, L.st>>>(A, strideA, n_p, K, W.gjP, logdet_out, logdet_slot_stride,
-                                                   W.status, W.active);
+      gj_pivot_kernel<<<P, GTHREADS, SMEM_PIV, L.st>>>(A, strideA, n_p, K, W.gjP, logdet_out, logdet_slot_stride,
+                                                        W.status, W.active);
       L.stop();
       L.tick();
     }
     if (nt > 1) {
-      L.start(KID_GJ_PANEL, (double)P * (nt - 1));
-      gj_panel_kernel<<<dim3(nt, P), 256, SMEM2, L.st>>>(A, strideA, n_p, K, W.gjP, W.gjC, W.gjO, sCO, W.active);
+      L.start(KID_GJ_PANEL, (double)P * (nt - 1) / 8.0);
+      gj_panel_kernel<<<dim3(nt, P), GTHREADS, GSMEM2, L.st>>>(A, strideA, n_p, K, W.gjP, W.gjC, W.gjO, sCO,
+                                                               W.active);
       L.stop();
       L.tick();
     }
-    // units: rank-64 updates of one 64 x 64 tile (2 * 64^3 flops each)
-    L.start(KID_GJ_UPDATE, (double)P * (ntri - nt));
-    gj_update_kernel<<<dim3(ntri, P), 256, SMEM2, L.st>>>(A, strideA, n_p, K, nt, W.gjP, W.gjC, W.gjO, sCO,
-                                                           logdet_out, logdet_slot_stride, W.status, W.active);
+    // units: 64 x 64 x 64 tile products (2 * 64^3 flops); a 32-tile update is 1/8 of one
+    L.start(KID_GJ_UPDATE, (double)P * (ntri - nt) / 8.0);
+    gj_update_kernel<<<dim3(ntri, P), GTHREADS, GSMEM2, L.st>>>(A, strideA, n_p, K, nt, W.gjP, W.gjC, W.gjO, sCO,
+                                                                logdet_out, logdet_slot_stride, W.status, W.active);
     L.stop();
     L.tick();
   }
-  gj_finalize_kernel<<<dim3(ntri, P), 256, 0, L.st>>>(A, strideA, n_p, W.active);
+  gj_finalize_kernel<<<dim3(tntri, P), 256, 0, L.st>>>(A, strideA, n_p, W.active);
   L.tick();
 }
 

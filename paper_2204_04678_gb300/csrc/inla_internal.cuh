@@ -44,6 +44,7 @@ struct PointParams {
 struct DevModel {
   int n_t, n_s, n_b, n_p, lik, nnz;
   int max_mt;                    // largest number of observations in one time block
+  int pbw;                       // bandwidth of the pattern: max |column - row|
   int64_t m, n, nv;              // nv = n_t*n_p + n_b (padded latent length)
   const int *prow, *pcol;        // union pattern, CSR [n_s+1], [nnz]
   const int *prow_of;            // [nnz] row of each pattern entry
@@ -181,8 +182,10 @@ void k_set_active(Launch &L, const Work &W, int mask);
 void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode);
 void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *dst, int64_t sdst,
                      bool schur);
+// lower_band: compute only the columns that the lower-tile assembly of the
+// next diagonal block reads (the factorisation); false = the full matrix.
 void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
-                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t);
+                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band = false);
 void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
                    int64_t sOut, bool with_X, const double *Rt_t, const double *Ymat);
 void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const double *Dinv_t, int nvec,
