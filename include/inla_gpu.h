@@ -193,13 +193,13 @@ int64_t inla_model_latent_dim(const inla_model *model);
 /* Number of kernel launches the last inla_eval_batch issued (diagnostics). */
 int64_t inla_last_launch_count(const inla_model *model);
 
-/* Live kernel timing (diagnostics, off by default).  While enabled, the
- * launches of the kernels below are bracketed by CUDA events on the launch
- * stream; inla_profile_read synchronises those events and returns, for one
+/* Live kernel timing (diagnostics, off by default).  While enabled
+ * (enable = k >= 1), every k-th launch of each kernel below is bracketed by
+ * CUDA events on the launch stream; inla_profile_read synchronises those events and returns, for one
  * kernel, the summed event time in ms, the number of launches and the
  * number of algorithmic units processed (a unit is one 64 x 64 x 64 tile
  * product, 2 * 64^3 flops).  Enabling resets the records.
- *   kernel 0: rank-64 tile update of the block sweep inversion
+ *   kernel 0: rank-32 tile update of the block sweep inversion
  *   kernel 1: 64 x 64 tile GEMM of the selected inversion
  *   kernel 2: pivot-block inversion        kernel 3: pivot-panel product */
 int inla_profile_enable(inla_model *model, int enable);

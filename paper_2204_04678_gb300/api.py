@@ -94,8 +94,9 @@ class Model:
     def last_launch_count(self):
         return int(self.lib.inla_last_launch_count(self.handle))
 
-    def profile_enable(self, on=True):
-        C.check(self.lib.inla_profile_enable(self.handle, int(bool(on))))
+    def profile_enable(self, every=1):
+        """Time every `every`-th launch of the instrumented kernels (0 = off)."""
+        C.check(self.lib.inla_profile_enable(self.handle, int(every)))
 
     def profile_read(self, kernel):
         """(total_ms, launches, units) of one kernel since profiling was enabled."""

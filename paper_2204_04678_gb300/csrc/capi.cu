@@ -938,7 +938,7 @@ int inla_profile_enable(inla_model *model, int enable) {
     CUDA_OK(cudaSetDevice(model->device));
     CUDA_OK(cudaDeviceSynchronize());
     model->prof.reset();
-    model->prof.enabled = enable ? 1 : 0;
+    model->prof.enabled = enable > 0 ? enable : 0;
   });
 }
 

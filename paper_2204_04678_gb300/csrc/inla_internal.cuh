@@ -125,7 +125,8 @@ enum { ASM_QC = 0, ASM_Q = 1, ASM_QS = 2 };
 // Optional CUDA-event timing of selected kernels (inla_profile_*).
 enum { KID_GJ_UPDATE = 0, KID_GEMM = 1, KID_GJ_PIVOT = 2, KID_GJ_PANEL = 3, KID_COUNT = 4 };
 struct Profiler {
-  int enabled = 0;
+  int enabled = 0;      // 0 = off, k >= 1: time every k-th launch of each kernel
+  int64_t seen[KID_COUNT] = {};
   std::vector<cudaEvent_t> pool;
   size_t next = 0;
   struct Rec { int id; double units; cudaEvent_t a, b; };
@@ -138,7 +139,11 @@ struct Profiler {
     }
     return pool[next++];
   }
-  void reset() { next = 0; recs.clear(); }
+  void reset() {
+    next = 0;
+    recs.clear();
+    for (auto &c : seen) c = 0;
+  }
   ~Profiler() { for (auto e : pool) cudaEventDestroy(e); }
 };
 
@@ -153,6 +158,7 @@ struct Launch {
   // bracket one launch of kernel `id` processing `units` algorithmic units
   void start(int id, double units) {
     if (!prof || !prof->enabled) return;
+    if (prof->seen[id]++ % prof->enabled != 0) return;
     cur_id = id;
     cur_units = units;
     cur_a = prof->get();
