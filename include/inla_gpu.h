@@ -70,7 +70,13 @@ enum { INLA_GRAD_NONE = 0, INLA_GRAD_FD_CENTRAL = 1, INLA_GRAD_ADJOINT = 2 };
  * inversion of Q_s; BTA runs the same block factorisation (and selected
  * inversion, for the gradient) on Q as on Q_c.  Both are exact. */
 enum { INLA_PRIOR_KRONECKER = 0, INLA_PRIOR_BTA = 1 };
-enum { INLA_FP64 = 0 };
+/* Arithmetic of the dense n_s x n_s blocks (the Schur-complement inverses,
+ * their sweep updates and the selected-inversion products).  INLA_FP64: all
+ * FP64.  INLA_MIXED: those blocks are stored and multiplied in FP32, while
+ * the pivot-block inversions, every log-determinant, the sparse assembly
+ * inputs, all vectors, reductions and traces stay FP64, and the mode is
+ * refined with FP64 residuals r = b - Q_c x (three refinement steps). */
+enum { INLA_FP64 = 0, INLA_MIXED = 1 };
 
 /* Model description.  Every pointer is a HOST pointer; the arrays are read
  * (and copied to the device) by inla_model_create and may be freed after it
@@ -100,7 +106,7 @@ typedef struct {
 typedef struct {
   int32_t grad;           /* INLA_GRAD_NONE / _FD_CENTRAL / _ADJOINT               */
   int32_t prior_mode;     /* INLA_PRIOR_KRONECKER or INLA_PRIOR_BTA                */
-  int32_t precision;      /* INLA_FP64                                             */
+  int32_t precision;      /* INLA_FP64 or INLA_MIXED                               */
   int32_t want_mode;      /* nonzero: write x*(theta) to out->x_mode               */
   int32_t want_marg_var;  /* nonzero: write diag(Q_c^-1) to out->marg_var          */
   int32_t max_newton;     /* Poisson: iteration limit (<= 0: 50)                   */

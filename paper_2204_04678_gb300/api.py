@@ -20,12 +20,15 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
 
 
+_PREC = {"fp64": C.INLA_FP64, "mixed": C.INLA_MIXED}
+
+
 def make_opts(grad="none", prior="kronecker", want_mode=False, want_marg_var=False, max_newton=50,
-              newton_tol=1e-8, fd_eps=1e-3):
+              newton_tol=1e-8, fd_eps=1e-3, precision="fp64"):
     o = C.inla_eval_opts()
     o.grad = _GRAD[grad]
     o.prior_mode = _PRIOR[prior]
-    o.precision = C.INLA_FP64
+    o.precision = _PREC[precision]
     o.want_mode = int(bool(want_mode))
     o.want_marg_var = int(bool(want_marg_var))
     o.max_newton = int(max_newton)
@@ -105,7 +108,7 @@ class Model:
         return ms.value, n.value, u.value
 
     def eval(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False, max_newton=50,
-             newton_tol=1e-8, fd_eps=1e-3, stream=None, out=None):
+             newton_tol=1e-8, fd_eps=1e-3, stream=None, out=None, precision="fp64"):
         """Evaluate a batch on the GPU.  theta: CUDA float64 tensor [B, 4].
 
         Returns a dict of CUDA tensors: f [B], grad [B, 4] (if requested),
@@ -130,7 +133,7 @@ class Model:
                 out["x_mode"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
             if want_marg_var:
                 out["marg_var"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
-        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision)
         so = C.inla_eval_out()
         so.f_dev = out["f"].data_ptr()
         so.status_dev = out["status"].data_ptr()
@@ -177,7 +180,7 @@ class Model:
         return out
 
     def eval_host(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False,
-                  max_newton=50, newton_tol=1e-8, fd_eps=1e-3):
+                  max_newton=50, newton_tol=1e-8, fd_eps=1e-3, precision="fp64"):
         """Evaluate with HOST numpy buffers (copies in and out inside the call)."""
         theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 4))
         B = theta.shape[0]
@@ -188,7 +191,7 @@ class Model:
             res["x_mode"] = np.empty((B, self.n))
         if want_marg_var:
             res["marg_var"] = np.empty((B, self.n))
-        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision)
         so = C.inla_eval_out_host()
         so.f = res["f"].ctypes.data
         so.status = res["status"].ctypes.data

@@ -24,6 +24,7 @@ INLA_GRAD_ADJOINT = 2
 INLA_PRIOR_KRONECKER = 0
 INLA_PRIOR_BTA = 1
 INLA_FP64 = 0
+INLA_MIXED = 1
 KERNEL_GJ_UPDATE = 0
 KERNEL_GEMM = 1
 KERNEL_GJ_PIVOT = 2

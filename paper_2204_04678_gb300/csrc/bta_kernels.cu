@@ -44,7 +44,8 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
@@ -145,44 +146,47 @@ __global__ void init_step0_kernel(DevModel M, Work W, int mode) {
 // with T1 = Dinv_{t-1} Q_s; identity in the padding.  mode ASM_QS builds Q_s alone.
 // Only the lower 32-wide tiles are written: the block sweep reads nothing else.
 constexpr int SWEEP_TILE = 32;
-__global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, double *dst, int64_t sdst, int schur) {
+template <typename R>
+__global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, R *dst, int64_t sdst, int schur) {
   const int b = blockIdx.z;
   if (!W.active[b]) return;
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_p = M.n_p, n_s = M.n_s;
   if (j >= n_p || j >= (i / SWEEP_TILE + 1) * SWEEP_TILE) return;
-  double *out = dst + b * sdst + (int64_t)i * n_p + j;
+  R *out = dst + b * sdst + (int64_t)i * n_p + j;
   if (i >= n_s || j >= n_s) {
-    *out = (i == j) ? 1.0 : 0.0;
+    *out = (i == j) ? R(1) : R(0);
     return;
   }
   const PointParams &p = W.prm[b];
   const double c = (mode == ASM_QS) ? 1.0 : q_tt(p, t, M.n_t);
   const double *qs = W.qs + b * W.sNnz;
-  const double *T1 = W.T1 + b * W.sMat;
+  const R *T1 = static_cast<const R *>(W.T1) + b * W.sMat;
   const double *lik = nullptr;
   double lik_scale = 0.0;
   if (mode == ASM_QC) {
     if (M.lik == INLA_LIK_GAUSSIAN) { lik = M.AtA + (int64_t)t * M.nnz; lik_scale = p.tau_y; }
     else { lik = W.AtAp + b * W.sAtAp + (int64_t)t * M.nnz; lik_scale = 1.0; }
   }
-  double acc = 0.0, sparse = 0.0;
+  R acc = 0;
+  double sparse = 0.0;
   for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) {
     const int k = M.pcol[e];
-    if (schur) acc = fma(qs[e], T1[(int64_t)k * n_p + j], acc);
+    if (schur) acc = fma((R)qs[e], T1[(int64_t)k * n_p + j], acc);
     if (k == j) {
       sparse = c * qs[e];
       if (lik) sparse += lik_scale * lik[e];
     }
   }
-  *out = sparse - (schur ? p.q_off * p.q_off * acc : 0.0);
+  *out = (R)(sparse - (schur ? p.q_off * p.q_off * (double)acc : 0.0));
 }
 
 // out[i][j] = coef * sum_k X[i][k] Q_s[k][j] + sum_l SigA[l][i] Rt[l][j]   (i, j < n_s; 0 elsewhere)
 // lower_band: only columns j < (floor((i + pbw) / 32) + 1) * 32, the ones the
 // lower-tile assembly of rows within the pattern bandwidth of i reads.
-__global__ void sparse_right_kernel(DevModel M, Work W, const double *X, int64_t sX, double *outp, int64_t sOut,
+template <typename R>
+__global__ void sparse_right_kernel(DevModel M, Work W, const R *X, int64_t sX, R *outp, int64_t sOut,
                                     int coef_qoff, const double *SigA, const double *Rt_t, int lower_band) {
   const int b = blockIdx.z;
   if (!W.active[b]) return;
@@ -191,23 +195,24 @@ __global__ void sparse_right_kernel(DevModel M, Work W, const double *X, int64_t
   const int n_p = M.n_p, n_s = M.n_s;
   if (j >= n_p) return;
   if (lower_band && j >= ((i + M.pbw) / SWEEP_TILE + 1) * SWEEP_TILE) return;
-  double *out = outp + b * sOut + (int64_t)i * n_p + j;
-  if (i >= n_s || j >= n_s) { *out = 0.0; return; }
-  const double *Xi = X + b * sX + (int64_t)i * n_p;
+  R *out = outp + b * sOut + (int64_t)i * n_p + j;
+  if (i >= n_s || j >= n_s) { *out = R(0); return; }
+  const R *Xi = X + b * sX + (int64_t)i * n_p;
   const double *qs = W.qs + b * W.sNnz;
-  double acc = 0.0;
-  for (int e = M.prow[j]; e < M.prow[j + 1]; ++e) acc = fma(Xi[M.pcol[e]], qs[e], acc);
-  if (coef_qoff) acc *= W.prm[b].q_off;
+  R acc = 0;
+  for (int e = M.prow[j]; e < M.prow[j + 1]; ++e) acc = fma(Xi[M.pcol[e]], (R)qs[e], acc);
+  if (coef_qoff) acc *= (R)W.prm[b].q_off;
   if (SigA) {
     const double *sa = SigA + b * W.sNbNp;
     const double *rt = Rt_t + b * W.sRt;
-    for (int l = 0; l < M.n_b; ++l) acc = fma(sa[(int64_t)l * n_p + i], rt[(int64_t)l * n_p + j], acc);
+    for (int l = 0; l < M.n_b; ++l) acc = fma((R)sa[(int64_t)l * n_p + i], (R)rt[(int64_t)l * n_p + j], acc);
   }
   *out = acc;
 }
 
 // out[i][j] = [with_X] q_off * sum_k Q_s[i][k] X[k][j] + sum_l Rt[l][i] Y[l][j]
-__global__ void sparse_left_kernel(DevModel M, Work W, const double *X, int64_t sX, double *outp, int64_t sOut,
+template <typename R>
+__global__ void sparse_left_kernel(DevModel M, Work W, const R *X, int64_t sX, R *outp, int64_t sOut,
                                    int with_X, const double *Rt_t, const double *Ymat) {
   const int b = blockIdx.z;
   if (!W.active[b]) return;
@@ -215,19 +220,19 @@ __global__ void sparse_left_kernel(DevModel M, Work W, const double *X, int64_t 
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_p = M.n_p, n_s = M.n_s;
   if (j >= n_p) return;
-  double *out = outp + b * sOut + (int64_t)i * n_p + j;
-  if (i >= n_s || j >= n_s) { *out = 0.0; return; }
-  double acc = 0.0;
+  R *out = outp + b * sOut + (int64_t)i * n_p + j;
+  if (i >= n_s || j >= n_s) { *out = R(0); return; }
+  R acc = 0;
   if (with_X) {
-    const double *Xb = X + b * sX;
+    const R *Xb = X + b * sX;
     const double *qs = W.qs + b * W.sNnz;
-    for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) acc = fma(qs[e], Xb[(int64_t)M.pcol[e] * n_p + j], acc);
-    acc *= W.prm[b].q_off;
+    for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) acc = fma((R)qs[e], Xb[(int64_t)M.pcol[e] * n_p + j], acc);
+    acc *= (R)W.prm[b].q_off;
   }
   if (Ymat) {
     const double *rt = Rt_t + b * W.sRt;
     const double *y = Ymat + b * W.sNbNp;
-    for (int l = 0; l < M.n_b; ++l) acc = fma(rt[(int64_t)l * n_p + i], y[(int64_t)l * n_p + j], acc);
+    for (int l = 0; l < M.n_b; ++l) acc = fma((R)rt[(int64_t)l * n_p + i], (R)y[(int64_t)l * n_p + j], acc);
   }
   *out = acc;
 }
@@ -237,36 +242,37 @@ constexpr int DA_ROWS_PER_WARP = 2;
 constexpr int DA_ROWS = 8 * DA_ROWS_PER_WARP;
 constexpr int DA_CHUNK = 256;
 constexpr int DA_MAXV = 1 + MAX_NB;
-__global__ void __launch_bounds__(256) dinv_apply_kernel(DevModel M, Work W, const double *Dinv_t, int nvec,
+template <typename R>
+__global__ void __launch_bounds__(256) dinv_apply_kernel(DevModel M, Work W, const R *Dinv_t, int nvec,
                                                         const double *vecs, int64_t sVecs, double *outp,
                                                         int64_t sOut, double scale) {
   const int b = blockIdx.y;
   if (!W.active[b]) return;
-  __shared__ double vs[DA_MAXV * DA_CHUNK];
+  __shared__ R vs[DA_MAXV * DA_CHUNK];
   const int n_p = M.n_p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * DA_ROWS + warp * DA_ROWS_PER_WARP;
-  const double *D = Dinv_t + b * W.sDinv;
+  const R *D = Dinv_t + b * W.sDinv;
   const double *V = vecs + b * sVecs;
-  double acc[DA_ROWS_PER_WARP][DA_MAXV];
+  R acc[DA_ROWS_PER_WARP][DA_MAXV];
 #pragma unroll
   for (int r = 0; r < DA_ROWS_PER_WARP; ++r)
 #pragma unroll
-    for (int c = 0; c < DA_MAXV; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < DA_MAXV; ++c) acc[r][c] = 0;
   for (int k0 = 0; k0 < n_p; k0 += DA_CHUNK) {
     __syncthreads();
     for (int e = threadIdx.x; e < nvec * DA_CHUNK; e += blockDim.x) {
       const int c = e / DA_CHUNK, k = e % DA_CHUNK;
-      vs[e] = (k0 + k < n_p) ? V[(int64_t)c * n_p + k0 + k] : 0.0;
+      vs[e] = (k0 + k < n_p) ? (R)V[(int64_t)c * n_p + k0 + k] : R(0);
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < DA_ROWS_PER_WARP; ++r) {
       const int row = row0 + r;
       if (row >= n_p) continue;
-      const double *Dr = D + (int64_t)row * n_p + k0;
+      const R *Dr = D + (int64_t)row * n_p + k0;
       for (int q = lane; q < DA_CHUNK && k0 + q < n_p; q += 32) {
-        const double d = Dr[q];
+        const R d = Dr[q];
 #pragma unroll
         for (int c = 0; c < DA_MAXV; ++c)
           if (c < nvec) acc[r][c] = fma(d, vs[c * DA_CHUNK + q], acc[r][c]);
@@ -280,8 +286,8 @@ __global__ void __launch_bounds__(256) dinv_apply_kernel(DevModel M, Work W, con
 #pragma unroll
     for (int c = 0; c < DA_MAXV; ++c) {
       if (c >= nvec) break;
-      const double s = warp_sum(acc[r][c]);
-      if (lane == 0 && row < n_p) O[(int64_t)c * n_p + row] = scale * s;
+      const R s = warp_sum(acc[r][c]);
+      if (lane == 0 && row < n_p) O[(int64_t)c * n_p + row] = scale * (double)s;
     }
   }
 }
@@ -457,25 +463,26 @@ __global__ void selinv_Y_kernel(DevModel M, Work W, int t, int has_next) {
 
 // <Sigma_{t+1,t}, X> for X in {C, G, H} with Sigma_{t+1,t} = -N Dinv_t on the pattern.
 constexpr int OFF_ENTRIES_PER_WARP = 4;
+template <typename R>
 __global__ void __launch_bounds__(256) contract_offdiag_kernel(DevModel M, Work W, int t) {
   const int b = blockIdx.y;
   if (!W.active[b]) return;
   __shared__ double red[32];
   const int n_p = M.n_p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double *N = W.T1 + b * W.sMat;
-  const double *D = W.Dinv + b * W.sDinv + (int64_t)t * n_p * n_p;
+  const R *N = static_cast<const R *>(W.T1) + b * W.sMat;
+  const R *D = static_cast<const R *>(W.Dinv) + b * W.sDinv + (int64_t)t * n_p * n_p;
   double sC = 0.0, sG = 0.0, sH = 0.0;
   const int per_block = 8 * OFF_ENTRIES_PER_WARP;
   for (int e0 = blockIdx.x * per_block; e0 < M.nnz; e0 += gridDim.x * per_block) {
     for (int q = 0; q < OFF_ENTRIES_PER_WARP; ++q) {
       const int e = e0 + warp * OFF_ENTRIES_PER_WARP + q;
       if (e >= M.nnz) break;
-      const double *Ni = N + (int64_t)M.prow_of[e] * n_p;
-      const double *Dj = D + (int64_t)M.pcol[e] * n_p;
-      double d = 0.0;
-      for (int k = lane; k < n_p; k += 32) d = fma(Ni[k], Dj[k], d);
-      d = -warp_sum(d);
+      const R *Ni = N + (int64_t)M.prow_of[e] * n_p;
+      const R *Dj = D + (int64_t)M.pcol[e] * n_p;
+      R dd = 0;
+      for (int k = lane; k < n_p; k += 32) dd = fma(Ni[k], Dj[k], dd);
+      const double d = -(double)warp_sum(dd);
       if (lane == 0) {
         sC = fma(d, M.vC[e], sC);
         sG = fma(d, M.vG[e], sG);
@@ -506,19 +513,20 @@ __global__ void reduce_parts_kernel(Work W, int nparts, int ncomp, double *dst, 
 }
 
 // <Sigma_tt, X> on the pattern, <Sigma_{a,t}, Z^T D A_t>, and diag(Sigma_tt) output.
+template <typename R>
 __global__ void __launch_bounds__(256) contract_diag_kernel(DevModel M, Work W, int t, int mode, double *mv,
                                                            const int *point_out, int64_t point_base, int slot0) {
   const int b = blockIdx.x;
   if (!W.active[b]) return;
   __shared__ double red[32];
   const int n_p = M.n_p;
-  const double *S = W.SigC + b * W.sMat;
+  const R *S = static_cast<const R *>(W.SigC) + b * W.sMat;
   const double *lik = nullptr;
   if (mode == ASM_QC)
     lik = (M.lik == INLA_LIK_GAUSSIAN) ? M.AtA + (int64_t)t * M.nnz : W.AtAp + b * W.sAtAp + (int64_t)t * M.nnz;
   double sC = 0.0, sG = 0.0, sH = 0.0, sA = 0.0;
   for (int e = threadIdx.x; e < M.nnz; e += blockDim.x) {
-    const double s = S[(int64_t)M.prow_of[e] * n_p + M.pcol[e]];
+    const double s = (double)S[(int64_t)M.prow_of[e] * n_p + M.pcol[e]];
     sC = fma(s, M.vC[e], sC);
     sG = fma(s, M.vG[e], sG);
     sH = fma(s, M.vH[e], sH);
@@ -550,7 +558,7 @@ __global__ void __launch_bounds__(256) contract_diag_kernel(DevModel M, Work W, 
       const int o = point_out[point_base + b];
       if (o >= 0) {
         double *dst = mv + (int64_t)o * M.n + (int64_t)t * M.n_s;
-        for (int i = threadIdx.x; i < M.n_s; i += blockDim.x) dst[i] = S[(int64_t)i * n_p + i];
+        for (int i = threadIdx.x; i < M.n_s; i += blockDim.x) dst[i] = (double)S[(int64_t)i * n_p + i];
       }
     }
   }
@@ -654,7 +662,7 @@ __global__ void qs_traces_kernel(DevModel M, Work W) {
   const int b = blockIdx.x;
   if (!W.active[b]) return;
   __shared__ double red[32];
-  const double *S = W.T1 + b * W.sMat;
+  const double *S = W.QsI + b * W.sMat;
   double sC = 0.0, sG = 0.0, sH = 0.0;
   for (int e = threadIdx.x; e < M.nnz; e += blockDim.x) {
     const double s = S[(int64_t)M.prow_of[e] * M.n_p + M.pcol[e]];
@@ -732,18 +740,39 @@ __global__ void finalize_kernel(DevModel M, Work W, int grad_mode, int prior_mod
   status_all[g] = st;
   iters_all[g] = W.iters[b];
   if (grad_mode != INLA_GRAD_ADJOINT || !grad_all) return;
+  // tr(Sigma_c (Q - tau_b I_tip)) = n - tr(Sigma_c A^T D A) - tau_b tr(Sigma_a)  (Sigma_c Q_c = I).
+  // With dQ/dlog(sigma) = -2 (Q - tau_b I_tip) and dQ_s/dlog(range) = 2 Q_s - 4 aC C - 2 aG G this
+  // removes the large, nearly cancelling Q_s and H parts of the prior and posterior traces.
+  double liktr = sc[SC_TIP_ATA];
+  for (int t = 0; t < n_t; ++t) liktr += pt[(int64_t)t * PT_COUNT + PT_FD_ATA] + 2.0 * pt[(int64_t)t * PT_COUNT + PT_FA_ATA];
+  liktr *= gauss ? p.tau_y : 1.0;
+  const double trQcQ = (double)M.n - liktr - p.tau_b * sc[SC_TIP_TRSIG];
+  auto cg_part = [&](int sd, int so) {   // sum_t of q (4 aC <S, C> + 2 aG <S, G>) over diagonal and 2x off blocks
+    double v = 0.0;
+    for (int t = 0; t < n_t; ++t) {
+      const double *q = pt + (int64_t)t * PT_COUNT;
+      v += q_tt(p, t, n_t) * (4.0 * p.aC * q[sd + 0] + 2.0 * p.aG * q[sd + 1]);
+      if (t < n_t - 1) v += 2.0 * p.q_off * (4.0 * p.aC * q[so + 0] + 2.0 * p.aG * q[so + 1]);
+    }
+    return v;
+  };
   double gr[4];
   for (int j = 0; j < 4; ++j) {
     double trQ;
     if (prior_mode == INLA_PRIOR_KRONECKER) {
       if (j == 0) trQ = gauss ? 0.0 : (double)n_b;
-      else if (j == 1) trQ = n_t * (-2.0 * p.aC * sc[SC_TR_QSI_C] + 2.0 * p.aH * sc[SC_TR_QSI_H]);
+      else if (j == 1) trQ = n_t * (2.0 * n_s - 4.0 * p.aC * sc[SC_TR_QSI_C] - 2.0 * p.aG * sc[SC_TR_QSI_G]);
       else if (j == 2) trQ = -2.0 * n_t * n_s;
       else trQ = n_s * rho * (1.0 - rho) * 2.0 * (n_t - 1) * rho / (1.0 - rho * rho);
     } else {
-      trQ = dsum(M, p, pt, j, PT_QD_C, PT_QO_C, 2.0) + ((j == 0 && !gauss) ? (double)n_b : 0.0);
+      if (j == 1) trQ = 2.0 * n_t * n_s - cg_part(PT_QD_C, PT_QO_C);
+      else if (j == 2) trQ = -2.0 * n_t * n_s;
+      else trQ = dsum(M, p, pt, j, PT_QD_C, PT_QO_C, 2.0) + ((j == 0 && !gauss) ? (double)n_b : 0.0);
     }
-    double trQc = dsum(M, p, pt, j, PT_FD_C, PT_FO_C, 2.0);
+    double trQc;
+    if (j == 1) trQc = 2.0 * trQcQ - cg_part(PT_FD_C, PT_FO_C);
+    else if (j == 2) trQc = -2.0 * trQcQ;
+    else trQc = dsum(M, p, pt, j, PT_FD_C, PT_FO_C, 2.0);
     double xdx = dsum(M, p, pt, j, PT_XD_C, PT_XO_C, 1.0);
     double v = -p.dlogprior[j] - 0.5 * trQ + 0.5 * xdx + 0.5 * trQc;
     if (gauss) {
@@ -946,13 +975,14 @@ __global__ void poisson_step_kernel(DevModel M, Work W, double tol, int iter, in
 }
 
 // a_i^T Sigma_c a_i for the observations of time block t (pattern entries only).
+template <typename R>
 __global__ void poisson_qobs_kernel(DevModel M, Work W, int t) {
   const int b = blockIdx.y;
   if (!W.active[b]) return;
   const int64_t i = M.obs_ptr[t] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M.obs_ptr[t + 1]) return;
   const int n_p = M.n_p, nb = M.n_b;
-  const double *S = W.SigC + b * W.sMat;
+  const R *S = static_cast<const R *>(W.SigC) + b * W.sMat;
   const double *Sa = W.SigAc + b * W.sNbNp;
   const double *St = W.Da + b * W.sNb2;
   const double *w = M.obs_w + i * MAX_SPATIAL;
@@ -960,7 +990,7 @@ __global__ void poisson_qobs_kernel(DevModel M, Work W, int t) {
   const double *z = M.obs_z + i * nb;
   double q = 0.0;
   for (int s1 = 0; s1 < MAX_SPATIAL; ++s1)
-    for (int s2 = 0; s2 < MAX_SPATIAL; ++s2) q += w[s1] * w[s2] * S[(int64_t)v[s1] * n_p + v[s2]];
+    for (int s2 = 0; s2 < MAX_SPATIAL; ++s2) q += w[s1] * w[s2] * (double)S[(int64_t)v[s1] * n_p + v[s2]];
   for (int s1 = 0; s1 < MAX_SPATIAL; ++s1)
     for (int l = 0; l < nb; ++l) q += 2.0 * w[s1] * z[l] * Sa[(int64_t)l * n_p + v[s1]];
   for (int l = 0; l < nb; ++l)
@@ -974,6 +1004,81 @@ __global__ void poisson_wobs_kernel(DevModel M, Work W) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M.m) return;
   W.wobs[b * W.sM + i] = 0.5 * W.qobs[b * W.sM + i] * W.mu[b * W.sM + i];
+}
+
+// r = b - Q_c x in FP64 from the sparse blocks (iterative refinement of the
+// mode in the mixed-precision path): per time block
+//   (Q_c x)_t = q_tt Q_s x_t + q_off Q_s (x_{t-1} + x_{t+1}) + L_t x_t + Arw_t^T x_a,
+//   (Q_c x)_a = (tau_b I + L_a) x_a + sum_t Arw_t x_t.
+__global__ void qc_residual_kernel(DevModel M, Work W, const double *x, const double *bvec, double *r) {
+  const int b = blockIdx.z;
+  if (!W.active[b]) return;
+  const int t = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_p = M.n_p, n_s = M.n_s, n_b = M.n_b, n_t = M.n_t;
+  if (i >= n_p) return;
+  const int64_t o = b * W.sVec + (int64_t)t * n_p + i;
+  if (i >= n_s) { r[o] = 0.0; return; }
+  const PointParams &p = W.prm[b];
+  const double *xb = x + b * W.sVec;
+  const double *qs = W.qs + b * W.sNnz;
+  const double *lik = (M.lik == INLA_LIK_GAUSSIAN) ? M.AtA + (int64_t)t * M.nnz
+                                                   : W.AtAp + b * W.sAtAp + (int64_t)t * M.nnz;
+  const double ls = (M.lik == INLA_LIK_GAUSSIAN) ? p.tau_y : 1.0;
+  const double c = q_tt(p, t, n_t);
+  const double *xt = xb + (int64_t)t * n_p;
+  double y = 0.0;
+  for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) {
+    const int k = M.pcol[e];
+    double xn = 0.0;
+    if (t > 0) xn += xt[k - n_p];
+    if (t < n_t - 1) xn += xt[k + n_p];
+    y += (c * qs[e] + ls * lik[e]) * xt[k] + p.q_off * qs[e] * xn;
+  }
+  const double *xa = xb + (int64_t)n_t * n_p;
+  for (int l = 0; l < n_b; ++l) {
+    const int64_t ka = ((int64_t)t * n_b + l) * n_s + i;
+    const double a = (M.lik == INLA_LIK_GAUSSIAN) ? p.tau_y * M.Arw[ka] : W.Arwp[b * W.sArwp + ka];
+    y += a * xa[l];
+  }
+  r[o] = (bvec ? bvec[o] : 0.0) - y;
+}
+
+// Tail rows of the residual: one block per point.
+__global__ void qc_residual_tail_kernel(DevModel M, Work W, const double *x, const double *bvec, double *r) {
+  const int b = blockIdx.x;
+  if (!W.active[b]) return;
+  __shared__ double red[32];
+  const int n_p = M.n_p, n_s = M.n_s, n_b = M.n_b, n_t = M.n_t;
+  const PointParams &p = W.prm[b];
+  const double *xb = x + b * W.sVec;
+  const double *xa = xb + (int64_t)n_t * n_p;
+  const bool gauss = M.lik == INLA_LIK_GAUSSIAN;
+  for (int l = 0; l < n_b; ++l) {
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < (int64_t)n_t * n_s; k += blockDim.x) {
+      const int t = (int)(k / n_s), i = (int)(k % n_s);
+      const int64_t ka = ((int64_t)t * n_b + l) * n_s + i;
+      const double a = gauss ? p.tau_y * M.Arw[ka] : W.Arwp[b * W.sArwp + ka];
+      s = fma(a, xb[(int64_t)t * n_p + i], s);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+      for (int l2 = 0; l2 < n_b; ++l2) {
+        const double tip = gauss ? p.tau_y * M.Tip[l * n_b + l2] : W.Tipp[b * W.sNb2 + l * n_b + l2];
+        s += ((l == l2) ? p.tau_b : 0.0) * xa[l2] + tip * xa[l2];
+      }
+      const int64_t o = b * W.sVec + (int64_t)n_t * n_p + l;
+      r[o] = (bvec ? bvec[o] : 0.0) - s;
+    }
+  }
+}
+
+__global__ void axpy_kernel(DevModel M, Work W, double *x, const double *d) {
+  const int b = blockIdx.y;
+  if (!W.active[b]) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < M.nv) x[b * W.sVec + k] += d[b * W.sVec + k];
 }
 
 __global__ void zero_kernel(double *p, int64_t n) {
@@ -1003,29 +1108,33 @@ void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode) {
   init_step0_kernel<<<dim3(blocks(M.n_p, 128), M.n_b + 1, W.P), 128, 0, L.st>>>(M, W, mode);
   L.tick();
 }
-void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *dst, int64_t sdst,
+template <typename R>
+void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, R *dst, int64_t sdst,
                      bool schur) {
-  assemble_diag_kernel<<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, t, mode, dst, sdst,
+  assemble_diag_kernel<R><<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, t, mode, dst, sdst,
                                                                                 schur ? 1 : 0);
   L.tick();
 }
-void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
-                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band) {
-  sparse_right_kernel<<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
+template <typename R>
+void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const R *X, int64_t sX, R *out, int64_t sOut,
+                    bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band) {
+  sparse_right_kernel<R><<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
                                                                                coef_qoff ? 1 : 0, SigA, Rt_t,
                                                                                lower_band ? 1 : 0);
   L.tick();
 }
-void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
-                   int64_t sOut, bool with_X, const double *Rt_t, const double *Ymat) {
-  sparse_left_kernel<<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
+template <typename R>
+void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const R *X, int64_t sX, R *out, int64_t sOut,
+                   bool with_X, const double *Rt_t, const double *Ymat) {
+  sparse_left_kernel<R><<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
                                                                               with_X ? 1 : 0, Rt_t, Ymat);
   L.tick();
 }
-void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const double *Dinv_t, int nvec, const double *vecs,
+template <typename R>
+void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const R *Dinv_t, int nvec, const double *vecs,
                   int64_t sVecs, double *out, int64_t sOut, double scale) {
   if (nvec <= 0) return;
-  dinv_apply_kernel<<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs, sVecs, out,
+  dinv_apply_kernel<R><<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs, sVecs, out,
                                                                          sOut, scale);
   L.tick();
 }
@@ -1063,18 +1172,20 @@ void k_selinv_Y(Launch &L, const DevModel &M, const Work &W, int t, bool has_nex
   selinv_Y_kernel<<<dim3(blocks(M.n_p, 128), M.n_b, W.P), 128, 0, L.st>>>(M, W, t, has_next ? 1 : 0);
   L.tick();
 }
+template <typename R>
 void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int slot0) {
   int nparts = (int)blocks(M.nnz, 8 * OFF_ENTRIES_PER_WARP);
   if (nparts > NPART) nparts = NPART;
-  contract_offdiag_kernel<<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W, t);
+  contract_offdiag_kernel<R><<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W, t);
   L.tick();
   reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, 3, W.pt + (int64_t)t * PT_COUNT + slot0,
                                             (int64_t)M.n_t * PT_COUNT);
   L.tick();
 }
+template <typename R>
 void k_contract_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *marg_var,
                      const int *point_out, int64_t point_base, int slot0) {
-  contract_diag_kernel<<<W.P, 256, 0, L.st>>>(M, W, t, mode, marg_var, point_out, point_base, slot0);
+  contract_diag_kernel<R><<<W.P, 256, 0, L.st>>>(M, W, t, mode, marg_var, point_out, point_base, slot0);
   L.tick();
 }
 void k_contract_tip(Launch &L, const DevModel &M, const Work &W, int mode, double *marg_var, const int *point_out,
@@ -1155,15 +1266,45 @@ void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int
   poisson_step_kernel<<<W.P, 256, 0, L.st>>>(M, W, tol, iter, max_iter);
   L.tick();
 }
+template <typename R>
 void k_poisson_qobs(Launch &L, const DevModel &M, const Work &W, int t) {
   if (M.max_mt == 0) return;
-  poisson_qobs_kernel<<<dim3(blocks(M.max_mt, 128), W.P), 128, 0, L.st>>>(M, W, t);
+  poisson_qobs_kernel<R><<<dim3(blocks(M.max_mt, 128), W.P), 128, 0, L.st>>>(M, W, t);
   L.tick();
 }
 void k_poisson_wobs(Launch &L, const DevModel &M, const Work &W) {
   poisson_wobs_kernel<<<dim3(blocks(M.m, 256), W.P), 256, 0, L.st>>>(M, W);
   L.tick();
 }
+void k_qc_residual(Launch &L, const DevModel &M, const Work &W, const double *x, const double *b, double *r) {
+  qc_residual_kernel<<<dim3(blocks(M.n_p, 128), M.n_t, W.P), 128, 0, L.st>>>(M, W, x, b, r);
+  L.tick();
+  if (M.n_b > 0) {
+    qc_residual_tail_kernel<<<W.P, 256, 0, L.st>>>(M, W, x, b, r);
+    L.tick();
+  }
+}
+void k_axpy(Launch &L, const DevModel &M, const Work &W, double *x, const double *d) {
+  axpy_kernel<<<dim3(blocks(M.nv, 256), W.P), 256, 0, L.st>>>(M, W, x, d);
+  L.tick();
+}
+
+#define INLA_INSTANTIATE(R)                                                                                     \
+  template void k_assemble_diag<R>(Launch &, const DevModel &, const Work &, int, int, R *, int64_t, bool);     \
+  template void k_sparse_right<R>(Launch &, const DevModel &, const Work &, const R *, int64_t, R *, int64_t,  \
+                                  bool, const double *, const double *, bool);                                \
+  template void k_sparse_left<R>(Launch &, const DevModel &, const Work &, const R *, int64_t, R *, int64_t,   \
+                                 bool, const double *, const double *);                                       \
+  template void k_dinv_apply<R>(Launch &, const DevModel &, const Work &, const R *, int, const double *,      \
+                                int64_t, double *, int64_t, double);                                          \
+  template void k_contract_offdiag<R>(Launch &, const DevModel &, const Work &, int, int);                    \
+  template void k_contract_diag<R>(Launch &, const DevModel &, const Work &, int, int, double *, const int *,  \
+                                   int64_t, int);                                                             \
+  template void k_poisson_qobs<R>(Launch &, const DevModel &, const Work &, int);
+INLA_INSTANTIATE(double)
+INLA_INSTANTIATE(float)
+#undef INLA_INSTANTIATE
+
 void k_zero(Launch &L, double *p, int64_t n) {
   if (n <= 0) return;
   zero_kernel<<<blocks(n, 256), 256, 0, L.st>>>(p, n);

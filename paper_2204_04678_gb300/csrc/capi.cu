@@ -407,7 +407,7 @@ struct Sizes {
   int64_t m, AtAp, Arwp, ints;
 };
 
-Sizes sizes_of(const DevModel &M) {
+Sizes sizes_of(const DevModel &M) {  // element counts per point
   Sizes s{};
   const int64_t np = M.n_p, nb = M.n_b;
   s.theta = 32;
@@ -435,36 +435,47 @@ Sizes sizes_of(const DevModel &M) {
   return s;
 }
 
-int64_t point_bytes(const DevModel &M) {
+// rb: bytes per element of the dense blocks (8 = FP64, 4 = mixed precision)
+int64_t point_bytes(const DevModel &M, int rb) {
   const Sizes s = sizes_of(M);
-  int64_t d = s.theta + s.prm + s.qs + s.Dinv + s.Rt + 2 * s.Da + 5 * s.vec + s.wv + 4 * s.mat + 3 * s.nbnp + s.gjP +
-              2 * s.gjCO + s.sc + s.pt + s.part + s.tippart + 4 * s.ints + 1;
+  int64_t d = s.theta + s.prm + s.qs + s.Rt + 2 * s.Da + 7 * s.vec + s.wv + 3 * s.nbnp + s.sc + s.pt + s.part +
+              s.tippart + 4 * s.ints + 1;
   if (M.lik == INLA_LIK_POISSON) d += 4 * s.m + s.AtAp + s.Arwp;
-  return d * 8;
+  d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
+  const int64_t dense = s.Dinv + 4 * s.mat;
+  return d * 8 + rup(dense * rb, 256) + 64 * 256;   // slack: each array starts on 256 bytes
 }
 
-Work carve(const DevModel &M, void *base, int Pw) {
+Work carve(const DevModel &M, void *base, int Pw, int rb) {
   const Sizes s = sizes_of(M);
   Work W{};
+  W.rb = rb;
   char *p = static_cast<char *>(base);
   auto take = [&](int64_t per) {
     char *r = p;
-    p += (size_t)per * Pw * 8;
+    p += rup((int64_t)per * Pw * 8, 256);
     return reinterpret_cast<double *>(r);
+  };
+  auto take_r = [&](int64_t per) {   // dense block storage, element size rb
+    char *r = p;
+    p += rup((int64_t)per * Pw * rb, 256);
+    return static_cast<void *>(r);
   };
   W.theta = take(s.theta);
   W.prm = reinterpret_cast<PointParams *>(take(s.prm));
   W.qs = take(s.qs); W.sNnz = s.qs;
-  W.Dinv = take(s.Dinv); W.sDinv = s.Dinv;
+  W.Dinv = take_r(s.Dinv); W.sDinv = s.Dinv;
   W.Rt = take(s.Rt); W.sRt = s.Rt;
   W.Da = take(s.Da); W.sNb2 = s.Da;
   W.Tipp = take(s.Da);
   W.rhs = take(s.vec); W.zf = take(s.vec); W.x = take(s.vec); W.xprev = take(s.vec); W.tmpv = take(s.vec);
+  W.rvec = take(s.vec); W.dvec = take(s.vec);
   W.sVec = s.vec;
   W.wv = take(s.wv); W.sWV = s.wv;
-  W.T1 = take(s.mat); W.S = take(s.mat); W.SigN = take(s.mat); W.SigC = take(s.mat); W.sMat = s.mat;
+  W.T1 = take_r(s.mat); W.S = take_r(s.mat); W.SigN = take_r(s.mat); W.SigC = take_r(s.mat); W.sMat = s.mat;
   W.SigAn = take(s.nbnp); W.SigAc = take(s.nbnp); W.Y = take(s.nbnp); W.sNbNp = s.nbnp;
   W.gjP = take(s.gjP); W.gjC = take(s.gjCO); W.gjO = take(s.gjCO);
+  W.QsI = take(s.mat);
   W.sc = take(s.sc);
   W.pt = take(s.pt); W.sPt = s.pt;
   W.part = take(s.part);
@@ -487,8 +498,8 @@ Work carve(const DevModel &M, void *base, int Pw) {
 // stride of point b is the count; sc, pt and Tipp use fixed strides.
 static_assert(SC_COUNT <= 32, "sc slots");
 
-int wave_points(inla_model *mdl, int64_t P_total) {
-  const int64_t per = point_bytes(mdl->M);
+int wave_points(inla_model *mdl, int64_t P_total, int rb) {
+  const int64_t per = point_bytes(mdl->M, rb);
   size_t free_b = 0, total_b = 0;
   CUDA_OK(cudaMemGetInfo(&free_b, &total_b));
   const int64_t avail = (int64_t)free_b + (int64_t)mdl->ws_bytes - (int64_t)(2ll << 30);
@@ -497,8 +508,8 @@ int wave_points(inla_model *mdl, int64_t P_total) {
   return (int)std::min<int64_t>(P_total, std::min<int64_t>(cap, 65535));
 }
 
-void ensure_workspace(inla_model *mdl, int Pw) {
-  const size_t need = (size_t)point_bytes(mdl->M) * Pw;
+void ensure_workspace(inla_model *mdl, int Pw, int rb) {
+  const size_t need = (size_t)point_bytes(mdl->M, rb) * Pw;
   if (mdl->ws && mdl->ws_bytes >= need) return;
   if (mdl->ws) {
     CUDA_OK(cudaStreamSynchronize(mdl->stream));
@@ -553,49 +564,69 @@ void zero_slot(Launch &L, const Work &W, int slot) {
 }
 
 // Block LDL^T factorisation of Q_c (mode ASM_QC) or Q (ASM_Q) along the time chain.
+template <typename R>
 void factor(Launch &L, const DevModel &M, const Work &W, int mode, int ld_slot) {
   const int64_t np2 = (int64_t)M.n_p * M.n_p;
   const int64_t rtb = (int64_t)M.n_b * M.n_p;
+  R *Dinv = static_cast<R *>(W.Dinv);
+  R *T1 = static_cast<R *>(W.T1);
   zero_slot(L, W, ld_slot);
   k_init_step0(L, M, W, mode);
   for (int t = 0; t < M.n_t; ++t) {
-    double *Dt = W.Dinv + t * np2;
+    R *Dt = Dinv + t * np2;
     if (t > 0) {
-      const double *Dp = W.Dinv + (t - 1) * np2;
+      const R *Dp = Dinv + (t - 1) * np2;
       if (M.n_b > 0) {
         k_dinv_apply(L, M, W, Dp, M.n_b, W.Rt + (t - 1) * rtb, W.sRt, W.wv, W.sWV, 1.0);
         k_arrow_update(L, M, W, t, mode);
         k_arrow_dots(L, M, W, t - 1);
       }
-      k_sparse_right(L, M, W, Dp, W.sDinv, W.T1, W.sMat, false, nullptr, nullptr, true);
+      k_sparse_right<R>(L, M, W, Dp, W.sDinv, T1, W.sMat, false, nullptr, nullptr, true);
     }
-    k_assemble_diag(L, M, W, t, mode, Dt, W.sDinv, t > 0);
-    gj_invert(L, M, W, Dt, W.sDinv, W.sc + ld_slot, SC_COUNT);
+    k_assemble_diag<R>(L, M, W, t, mode, Dt, W.sDinv, t > 0);
+    gj_invert<R>(L, M, W, Dt, W.sDinv, W.sc + ld_slot, SC_COUNT);
   }
   if (M.n_b > 0) {
     const int t = M.n_t - 1;
-    k_dinv_apply(L, M, W, W.Dinv + t * np2, M.n_b, W.Rt + t * rtb, W.sRt, W.wv, W.sWV, 1.0);
+    k_dinv_apply<R>(L, M, W, Dinv + t * np2, M.n_b, W.Rt + t * rtb, W.sRt, W.wv, W.sWV, 1.0);
     k_arrow_dots(L, M, W, t);
   }
   k_tip(L, M, W, ld_slot);
 }
 
 // Forward and backward block substitution with the stored factorisation.
-void solve(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x) {
+template <typename R>
+void solve_once(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x) {
   const int64_t np2 = (int64_t)M.n_p * M.n_p;
+  const R *Dinv = static_cast<const R *>(W.Dinv);
   CUDA_OK(cudaMemcpyAsync(W.zf, rhs, sizeof(double) * W.sVec * W.P, cudaMemcpyDeviceToDevice, L.st));
   for (int t = 0; t < M.n_t; ++t) {
-    k_dinv_apply(L, M, W, W.Dinv + t * np2, 1, W.zf + (int64_t)t * M.n_p, W.sVec, W.wv, W.sWV, 1.0);
+    k_dinv_apply<R>(L, M, W, Dinv + t * np2, 1, W.zf + (int64_t)t * M.n_p, W.sVec, W.wv, W.sWV, 1.0);
     k_fwd_update(L, M, W, t, W.zf);
   }
   k_tip_solve(L, M, W, W.zf, x);
   for (int t = M.n_t - 1; t >= 0; --t) {
     k_bwd_rhs(L, M, W, t, W.zf, x);
-    k_dinv_apply(L, M, W, W.Dinv + t * np2, 1, W.tmpv, W.sVec, x + (int64_t)t * M.n_p, W.sVec, 1.0);
+    k_dinv_apply<R>(L, M, W, Dinv + t * np2, 1, W.tmpv, W.sVec, x + (int64_t)t * M.n_p, W.sVec, 1.0);
+  }
+}
+
+// Q_c x = rhs.  With single-precision blocks the solution is refined with FP64
+// residuals r = rhs - Q_c x computed from the sparse blocks (x += Q_c^-1 r).
+constexpr int REFINE_STEPS = 3;
+template <typename R>
+void solve(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x) {
+  solve_once<R>(L, M, W, rhs, x);
+  if (sizeof(R) == sizeof(double)) return;
+  for (int it = 0; it < REFINE_STEPS; ++it) {
+    k_qc_residual(L, M, W, x, rhs, W.rvec);
+    solve_once<R>(L, M, W, W.rvec, W.dvec);
+    k_axpy(L, M, W, x, W.dvec);
   }
 }
 
 // Block Takahashi recursion from the last time block to the first.
+template <typename R>
 void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contractions, double *marg_var,
             const int *point_out, int64_t point_base, bool poisson_q) {
   Work W = W0;
@@ -603,28 +634,33 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
   const int64_t rtb = (int64_t)M.n_b * M.n_p;
   const int slotD = (mode == ASM_QC) ? PT_FD_C : PT_QD_C;
   const int slotO = (mode == ASM_QC) ? PT_FO_C : PT_QO_C;
+  const R *Dinv = static_cast<const R *>(W.Dinv);
+  R *T1 = static_cast<R *>(W.T1);
+  R *S = static_cast<R *>(W.S);
   for (int t = M.n_t - 1; t >= 0; --t) {
-    const double *Dt = W.Dinv + t * np2;
+    const R *Dt = Dinv + t * np2;
     const double *Rt_t = W.Rt + t * rtb;
     const bool nxt = t < M.n_t - 1;
-    if (nxt) k_sparse_right(L, M, W, W.SigN, W.sMat, W.T1, W.sMat, true, M.n_b ? W.SigAn : nullptr, Rt_t);
+    R *SigN = static_cast<R *>(W.SigN), *SigC = static_cast<R *>(W.SigC);
+    if (nxt) k_sparse_right<R>(L, M, W, SigN, W.sMat, T1, W.sMat, true, M.n_b ? W.SigAn : nullptr, Rt_t);
     k_selinv_Y(L, M, W, t, nxt);
-    k_sparse_left(L, M, W, W.T1, W.sMat, W.S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
-    if (contractions && nxt) k_contract_offdiag(L, M, W, t, slotO);
-    if (M.n_b > 0) k_dinv_apply(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
-    gemm_nn(L, W.P, M.n_p, W.S, W.sMat, Dt, W.sDinv, W.T1, W.sMat, 1.0, nullptr, 0, 0.0, false, W.active);
-    gemm_nn(L, W.P, M.n_p, Dt, W.sDinv, W.T1, W.sMat, W.SigC, W.sMat, 1.0, Dt, W.sDinv, 1.0, true, W.active);
-    mirror_lower(L, W.P, M.n_p, W.SigC, W.sMat, W.active);
-    k_contract_diag(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
-    if (poisson_q) k_poisson_qobs(L, M, W, t);
+    k_sparse_left<R>(L, M, W, T1, W.sMat, S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
+    if (contractions && nxt) k_contract_offdiag<R>(L, M, W, t, slotO);
+    if (M.n_b > 0) k_dinv_apply<R>(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
+    gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active);
+    gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active);
+    mirror_lower<R>(L, W.P, M.n_p, SigC, W.sMat, W.active);
+    k_contract_diag<R>(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
+    if (poisson_q) k_poisson_qobs<R>(L, M, W, t);
     std::swap(W.SigN, W.SigC);
     std::swap(W.SigAn, W.SigAc);
   }
   k_contract_tip(L, M, W, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base);
 }
 
-void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o, int64_t w0,
-              const BatchBufs &bb, double *x_out, double *mv_out, int centre_flags) {
+template <typename R>
+void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o, int64_t w0,
+                const BatchBufs &bb, double *x_out, double *mv_out, int centre_flags) {
   const DevModel &M = mdl->M;
   const bool adj = o.grad == INLA_GRAD_ADJOINT;
   const bool need_sel = (centre_flags & 1) != 0;
@@ -640,26 +676,27 @@ void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o
   k_qs_values(L, M, W);
   // prior log-determinant (and traces for the adjoint)
   if (o.prior_mode == INLA_PRIOR_KRONECKER) {
-    k_assemble_diag(L, M, W, 0, ASM_QS, W.T1, W.sMat, false);
-    gj_invert(L, M, W, W.T1, W.sMat, W.sc + SC_LOGDET_QS, SC_COUNT);
+    // one n_s x n_s inversion per point: always in FP64
+    k_assemble_diag<double>(L, M, W, 0, ASM_QS, W.QsI, W.sMat, false);
+    gj_invert<double>(L, M, W, W.QsI, W.sMat, W.sc + SC_LOGDET_QS, SC_COUNT);
     if (adj) k_qs_traces(L, M, W);
   } else {
-    factor(L, M, W, ASM_Q, SC_LOGDET_Q);
+    factor<R>(L, M, W, ASM_Q, SC_LOGDET_Q);
     if (adj) {
       k_set_active(L, W, 2);
-      selinv(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false);
+      selinv<R>(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false);
       k_set_active(L, W, 0);
     }
   }
   if (M.lik == INLA_LIK_GAUSSIAN) {
-    factor(L, M, W, ASM_QC, SC_LOGDET_QC);
+    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC);
     k_rhs_gaussian(L, M, W);
-    solve(L, M, W, W.rhs, W.x);
+    solve<R>(L, M, W, W.rhs, W.x);
     k_obs_reduce(L, M, W, 0);
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
       k_set_active(L, W, 1);
-      selinv(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+      selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false);
       k_set_active(L, W, 0);
     }
   } else {
@@ -671,8 +708,8 @@ void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o
       k_poisson_eta(L, M, W, W.x);
       k_obs_assemble(L, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp, W.sArwp,
                      W.Tipp, W.sNb2, W.rhs, W.sVec, W.tippart);
-      factor(L, M, W, ASM_QC, SC_LOGDET_QC);
-      solve(L, M, W, W.rhs, W.x);
+      factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC);
+      solve<R>(L, M, W, W.rhs, W.x);
       CUDA_OK(cudaMemsetAsync(W.any_active, 0, sizeof(int), L.st));
       k_poisson_step(L, M, W, tol, it, max_it);
       int any = 0;
@@ -685,19 +722,19 @@ void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o
     k_poisson_eta(L, M, W, W.x);
     k_obs_assemble(L, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp, W.sArwp,
                    W.Tipp, W.sNb2, nullptr, 0, W.tippart);
-    factor(L, M, W, ASM_QC, SC_LOGDET_QC);
+    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC);
     k_obs_reduce(L, M, W, 1);
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
       k_set_active(L, W, 1);
-      selinv(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+      selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
       if (adj) {
         k_set_active(L, W, 2);
         k_poisson_wobs(L, M, W);
         CUDA_OK(cudaMemsetAsync(W.rhs, 0, sizeof(double) * W.sVec * W.P, L.st));
         k_obs_assemble(L, M, W.P, W.active, nullptr, 0, W.wobs, W.sM, false, nullptr, nullptr, 0, nullptr, 0,
                        nullptr, 0, W.rhs, W.sVec, W.tippart);
-        solve(L, M, W, W.rhs, W.xprev);
+        solve<R>(L, M, W, W.rhs, W.xprev);
         k_quadforms(L, M, W, W.xprev, W.x, PT_LD_C, SC_TIP_LX);
       }
       k_set_active(L, W, 0);
@@ -707,6 +744,12 @@ void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o
   k_finalize(L, M, W, o.grad, o.prior_mode, w0, bb.f_all, bb.grad_all, bb.status_all, bb.iters_all);
 }
 
+void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o, int64_t w0,
+              const BatchBufs &bb, double *x_out, double *mv_out, int centre_flags) {
+  if (W.rb == 4) run_wave_t<float>(mdl, L, W, o, w0, bb, x_out, mv_out, centre_flags);
+  else run_wave_t<double>(mdl, L, W, o, w0, bb, x_out, mv_out, centre_flags);
+}
+
 int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_eval_opts *opts,
                   const inla_eval_out *out, cudaStream_t st) {
   if (!mdl || !opts || !out || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
@@ -714,10 +757,11 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_ADJOINT) throw ApiError(INLA_ERR_ARG, "bad grad mode");
   if (opts->prior_mode != INLA_PRIOR_KRONECKER && opts->prior_mode != INLA_PRIOR_BTA)
     throw ApiError(INLA_ERR_ARG, "bad prior mode");
-  if (opts->precision != INLA_FP64) throw ApiError(INLA_ERR_UNSUPPORTED, "only INLA_FP64 is available");
+  if (opts->precision != INLA_FP64 && opts->precision != INLA_MIXED) throw ApiError(INLA_ERR_ARG, "bad precision");
   if (opts->grad != INLA_GRAD_NONE && !out->grad_dev) throw ApiError(INLA_ERR_ARG, "grad_dev required");
   if (opts->want_mode && !out->x_mode_dev) throw ApiError(INLA_ERR_ARG, "x_mode_dev required");
   if (opts->want_marg_var && !out->marg_var_dev) throw ApiError(INLA_ERR_ARG, "marg_var_dev required");
+  const int rb = opts->precision == INLA_MIXED ? 4 : 8;
   CUDA_OK(cudaSetDevice(mdl->device));
   const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
   const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
@@ -726,8 +770,8 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   Launch L{st, &mdl->launches, &mdl->prof};
   // the workspace is shared by all calls on this model: order this call after the previous one
   if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
-  const int Pw = wave_points(mdl, P_total);
-  ensure_workspace(mdl, Pw);
+  const int Pw = wave_points(mdl, P_total, rb);
+  ensure_workspace(mdl, Pw, rb);
   BatchBufs bb = batch_buffers(mdl, P_total);
   point_out_kernel<<<(unsigned)((P_total + 127) / 128), 128, 0, st>>>((int)P_total, per, bb.point_out);
   L.tick();
@@ -738,7 +782,7 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   if (opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 2;
   for (int64_t w0 = 0; w0 < P_total; w0 += Pw) {
     const int P = (int)std::min<int64_t>(Pw, P_total - w0);
-    Work W = carve(mdl->M, mdl->ws, mdl->ws_points);
+    Work W = carve(mdl->M, mdl->ws, Pw, rb);
     W.P = P;
     CUDA_OK(cudaMemcpyAsync(W.theta, bb.theta_all + 4 * w0, sizeof(double) * 4 * P, cudaMemcpyDeviceToDevice, st));
     // theta rows are read with stride 4 by the parameter kernel
@@ -806,15 +850,16 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_ADJOINT) throw ApiError(INLA_ERR_ARG, "bad grad mode");
   if (opts->prior_mode != INLA_PRIOR_KRONECKER && opts->prior_mode != INLA_PRIOR_BTA)
     throw ApiError(INLA_ERR_ARG, "bad prior mode");
-  if (opts->precision != INLA_FP64) throw ApiError(INLA_ERR_UNSUPPORTED, "only INLA_FP64 is available");
+  if (opts->precision != INLA_FP64 && opts->precision != INLA_MIXED) throw ApiError(INLA_ERR_ARG, "bad precision");
   if (opts->grad != INLA_GRAD_NONE && !out->grad_dev) throw ApiError(INLA_ERR_ARG, "grad_dev required");
   if (opts->want_mode && !out->x_mode_dev) throw ApiError(INLA_ERR_ARG, "x_mode_dev required");
   if (opts->want_marg_var && !out->marg_var_dev) throw ApiError(INLA_ERR_ARG, "marg_var_dev required");
+  const int rb = opts->precision == INLA_MIXED ? 4 : 8;
   const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
   const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
   const int64_t P_total = (int64_t)B * per;
   // the whole batch is one wave: workspace, then the per-point batch arrays
-  const int64_t ws_bytes = point_bytes(mdl->M) * P_total;
+  const int64_t ws_bytes = point_bytes(mdl->M, rb) * P_total;
   const int64_t bb_bytes = rup(32 * P_total, 256) + rup(8 * P_total, 256) + rup(32 * P_total, 256) +
                            3 * rup(4 * P_total, 256);
   if (P_total > 65535 || ws_bytes + bb_bytes > (int64_t)INLA_STATIC_SCRATCH_BYTES)
@@ -826,7 +871,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   mdl->launches = 0;
   Launch L{st, &mdl->launches, nullptr};
   if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
-  Work W0 = carve(mdl->M, base, (int)P_total);
+  Work W0 = carve(mdl->M, base, (int)P_total, rb);
   char *p = base + ws_bytes;
   auto take = [&](int64_t bytes) { char *r = p; p += rup(bytes, 256); return r; };
   BatchBufs bb;
@@ -873,7 +918,7 @@ int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *o
   return guarded([&] {
     if (!model || !opts || !bytes || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
     const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
-    *bytes = (size_t)point_bytes(model->M) * (size_t)B * per;
+    *bytes = (size_t)point_bytes(model->M, opts->precision == INLA_MIXED ? 4 : 8) * (size_t)B * per;
   });
 }
 

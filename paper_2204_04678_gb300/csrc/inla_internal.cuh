@@ -70,21 +70,27 @@ struct DevModel {
   double tau_b_fixed;
 };
 
-// Per-wave workspace (device) with per-point strides (in doubles / ints).
+// Per-wave workspace (device) with per-point strides (in elements).  The dense
+// n_p x n_p blocks (Dinv, T1, S, SigN, SigC and the sweep scratch) have storage
+// type R = double (rb = 8) or float (rb = 4, mixed precision); everything else is
+// double.
 struct Work {
   int P;
+  int rb;                // bytes per element of the dense blocks
   int64_t sDinv, sMat, sRt, sVec, sNb2, sWV, sNbNp, sNnz, sPt, sM, sAtAp, sArwp;
   double *theta;         // [P][4]
   PointParams *prm;      // [P]
   double *qs;            // [P][nnz]     Q_s values on the pattern
-  double *Dinv;          // [P][n_t][n_p][n_p]
+  void *Dinv;            // [P][n_t][n_p][n_p]  (R)
   double *Rt;            // [P][n_t][n_b][n_p]
   double *Da;            // [P][n_b][n_b]  tip Schur complement, then its inverse
   double *rhs, *zf, *x, *xprev, *tmpv;  // [P][nv]
+  double *rvec, *dvec;                   // [P][nv]  refinement residual and correction
   double *wv;            // [P][1+n_b][n_p]  Dinv_t times vectors
-  double *T1, *S, *SigN, *SigC;          // [P][n_p][n_p]
+  void *T1, *S, *SigN, *SigC;            // [P][n_p][n_p]  (R)
   double *SigAn, *SigAc, *Y;             // [P][n_b][n_p]
-  double *gjP, *gjC, *gjO;               // [P][2][64*64], [P][n_p*64], [P][n_p*64]
+  void *gjP, *gjC, *gjO;                 // [P][2][32*32], [P][n_p*32], [P][n_p*32]  (R; sized for double)
+  double *QsI;                           // [P][n_p][n_p]  Q_s^-1 (Kronecker prior), always FP64
   double *sc;            // [P][SC_COUNT] per-point scalars
   double *pt;            // [P][n_t][PT_COUNT] per-time-block contractions
   double *part;          // [P][NPART][4] partial sums
@@ -173,29 +179,34 @@ struct Launch {
   }
 };
 
-// dense_fp64.cu
-void gj_invert(Launch &L, const DevModel &M, const Work &W, double *A, int64_t strideA, double *logdet,
-               int ld_stride);
-void gemm_nn(Launch &L, int P, int n, const double *A, int64_t sA, const double *B, int64_t sB, double *C,
-             int64_t sC, double alpha, const double *C0, int64_t sC0, double beta, bool lower_only,
-             const int *active);
-void mirror_lower(Launch &L, int P, int n, double *A, int64_t sA, const int *active);
+// dense_blocks.cu (R = double or float)
+template <typename R>
+void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet, int ld_stride);
+template <typename R>
+void gemm_nn(Launch &L, int P, int n, const R *A, int64_t sA, const R *B, int64_t sB, R *C, int64_t sC, R alpha,
+             const R *C0, int64_t sC0, R beta, bool lower_only, const int *active);
+template <typename R>
+void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active);
 
 // bta_kernels.cu
 void k_params(Launch &L, const DevModel &M, const Work &W);
 void k_qs_values(Launch &L, const DevModel &M, const Work &W);
 void k_set_active(Launch &L, const Work &W, int mask);
 void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode);
-void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *dst, int64_t sdst,
+template <typename R>
+void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, R *dst, int64_t sdst,
                      bool schur);
 // lower_band: compute only the columns that the lower-tile assembly of the
 // next diagonal block reads (the factorisation); false = the full matrix.
-void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
-                    int64_t sOut, bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band = false);
-void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const double *X, int64_t sX, double *out,
-                   int64_t sOut, bool with_X, const double *Rt_t, const double *Ymat);
-void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const double *Dinv_t, int nvec,
-                  const double *vecs, int64_t sVecs, double *out, int64_t sOut, double scale);
+template <typename R>
+void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const R *X, int64_t sX, R *out, int64_t sOut,
+                    bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band = false);
+template <typename R>
+void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const R *X, int64_t sX, R *out, int64_t sOut,
+                   bool with_X, const double *Rt_t, const double *Ymat);
+template <typename R>
+void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const R *Dinv_t, int nvec, const double *vecs,
+                  int64_t sVecs, double *out, int64_t sOut, double scale);
 void k_arrow_update(Launch &L, const DevModel &M, const Work &W, int t, int mode);
 void k_arrow_dots(Launch &L, const DevModel &M, const Work &W, int tprev);
 void k_tip(Launch &L, const DevModel &M, const Work &W, int ld_slot);
@@ -203,7 +214,9 @@ void k_fwd_update(Launch &L, const DevModel &M, const Work &W, int t, double *z)
 void k_tip_solve(Launch &L, const DevModel &M, const Work &W, const double *z, double *x);
 void k_bwd_rhs(Launch &L, const DevModel &M, const Work &W, int t, const double *z, const double *x);
 void k_selinv_Y(Launch &L, const DevModel &M, const Work &W, int t, bool has_next);
+template <typename R>
 void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int slot0);
+template <typename R>
 void k_contract_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *marg_var,
                      const int *point_out, int64_t point_base, int slot0);
 void k_contract_tip(Launch &L, const DevModel &M, const Work &W, int mode, double *marg_var,
@@ -212,7 +225,10 @@ void k_quadforms(Launch &L, const DevModel &M, const Work &W, const double *u, c
                  int tip_slot);
 void k_rhs_gaussian(Launch &L, const DevModel &M, const Work &W);
 void k_obs_reduce(Launch &L, const DevModel &M, const Work &W, int kind);
-void k_qs_traces(Launch &L, const DevModel &M, const Work &W);
+void k_qs_traces(Launch &L, const DevModel &M, const Work &W);   // tr(Q_s^-1 X) from W.QsI
+// y = Q_c x (mode ASM_QC) in FP64 from the sparse blocks; r = b - y when b != nullptr
+void k_qc_residual(Launch &L, const DevModel &M, const Work &W, const double *x, const double *b, double *r);
+void k_axpy(Launch &L, const DevModel &M, const Work &W, double *x, const double *d);
 void k_finalize(Launch &L, const DevModel &M, const Work &W, int grad_mode, int prior_mode, int64_t point_base,
                 double *f_all, double *grad_all, int *status_all, int *iters_all);
 void k_copy_mode(Launch &L, const DevModel &M, const Work &W, double *x_out, const int *point_out,
@@ -228,6 +244,7 @@ void k_obs_assemble(Launch &L, const DevModel &M, int P, const int *active, cons
                     double *Arw, int64_t sArw, double *Tip, int64_t sTip, double *rhs, int64_t sRhs,
                     double *tippart);
 void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter);
+template <typename R>
 void k_poisson_qobs(Launch &L, const DevModel &M, const Work &W, int t);
 void k_poisson_wobs(Launch &L, const DevModel &M, const Work &W);
 void k_zero(Launch &L, double *p, int64_t n);

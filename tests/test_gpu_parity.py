@@ -218,3 +218,52 @@ def test_config2_full_size_sampled(pkg):
         e[i] = 1.0
         vi = bta.solve(L, e)[i]
         assert abs(v[i] - vi) <= RTOL_V * vi
+
+
+# ---------------------------------------------------------------- mixed precision
+# Dense blocks in FP32, pivots' log-determinants accumulated in FP64, the mode
+# refined with FP64 residuals.  f is held to 1e-6 relative; the refined mode to
+# the FP64 tolerance.  The adjoint gradient and the marginal variances are read
+# from FP32 selected-inverse blocks, whose entries carry ~1e-6 relative error
+# (inverse and products both rounded to 2^-24, amplified by the block condition
+# numbers); the data trace tau_y tr(Q_c^-1 A^T A) ~ m/2 then moves the gradient
+# by up to ~5e-5 of its largest component, and the variances by up to 1e-4.
+MIX_F, MIX_G, MIX_X, MIX_V = 1e-6, 5e-5, 1e-9, 1e-4
+
+
+@pytest.mark.parametrize("lik,n_t,nx,n_b,m", [("gaussian", 4, 10, 3, 600), ("gaussian", 6, 13, 2, 1500),
+                                              ("gaussian", 1, 4, 0, 60), ("poisson", 3, 6, 2, 400)])
+def test_mixed_precision_matches_oracle(pkg, lik, n_t, nx, n_b, m):
+    mdl = build("mx", n_t, nx, n_b, m, lik, seed=7)
+    th = thetas(mdl, 3, seed=3)
+    if lik == "poisson":
+        th[:, 0] = np.log(np.array([1e-3, 0.1, 1.0]))
+    model = pkg.Model(mdl)
+    r = model.eval(cuda(th), grad="adjoint", want_mode=True, want_marg_var=True, precision="mixed")
+    torch.cuda.synchronize()
+    for b in range(th.shape[0]):
+        ref = bta.evaluate(mdl, th[b], want_grad=True, want_var=True)
+        assert int(r["status"][b]) == 0
+        assert abs(float(r["f"][b]) - ref["f"]) <= MIX_F * abs(ref["f"])
+        g = r["grad"][b].cpu().numpy()
+        assert np.abs(g - ref["grad"]).max() <= MIX_G * max(1.0, np.abs(ref["grad"]).max()), (g, ref["grad"])
+        x = r["x_mode"][b].cpu().numpy()
+        assert np.abs(x - ref["x"]).max() <= MIX_X * np.abs(ref["x"]).max()
+        v = r["marg_var"][b].cpu().numpy()
+        assert np.max(np.abs(v - ref["var"]) / ref["var"]) <= MIX_V
+
+
+def test_mixed_precision_full_size_config2(pkg):
+    mdl = config_model(2)
+    th = theta_batch(2, mdl)[:2]
+    model = pkg.Model(mdl)
+    r = model.eval(cuda(th), grad="adjoint", want_mode=True, precision="mixed")
+    d = model.eval(cuda(th), grad="adjoint", want_mode=True)
+    torch.cuda.synchronize()
+    ref = bta.gaussian(mdl, th[0])
+    assert abs(float(r["f"][0]) - ref["f"]) <= MIX_F * abs(ref["f"])
+    assert np.all(np.abs(r["f"].cpu().numpy() - d["f"].cpu().numpy()) <= MIX_F * np.abs(d["f"].cpu().numpy()))
+    gd, gm = d["grad"].cpu().numpy(), r["grad"].cpu().numpy()
+    assert np.abs(gm - gd).max() <= MIX_G * max(1.0, np.abs(gd).max())
+    x = r["x_mode"][0].cpu().numpy()
+    assert np.abs(x - ref["x"]).max() <= MIX_X * np.abs(ref["x"]).max()
