@@ -29,11 +29,20 @@ METRIC = "theta-evals/s (f+grad f)"
 PROFILE_EVERY = 8   # event-time every 8th launch of the instrumented kernels (keeps the overhead small)
 UNIT = "f+grad evaluations/s"
 CONFIG_WORKLOAD = {
-    2: "st-spde-ar1 n_t=50 grid=32x32 (n_s=1024) n_b=4 m=100000 gaussian; one step = 9-point "
-       "central-difference stencil in one FP64 launch",
     1: "st-spde-ar1 n_t=8 grid=8x8 (n_s=64) n_b=2 m=2000 gaussian; one step = 9-point "
        "central-difference stencil in one FP64 launch",
+    2: "st-spde-ar1 n_t=50 grid=32x32 (n_s=1024) n_b=4 m=100000 gaussian; one step = 9-point "
+       "central-difference stencil in one FP64 launch",
+    3: "st-spde-ar1 n_t=100 grid=45x45 (n_s=2025) n_b=6 m=400000 gaussian; one step = 16 line-search "
+       "points with adjoint gradients, FP64",
+    4: "st-spde-ar1 n_t=200 grid=50x50 (n_s=2500) n_b=6 m=1000000 gaussian; one step = 9 stencil "
+       "points with adjoint gradients, mixed precision",
+    5: "st-spde-ar1 n_t=100 grid=64x64 (n_s=4096) n_b=8 m=500000 poisson; one step = 25-point CCD "
+       "design with Newton modes and adjoint gradients, mixed precision",
 }
+# natural gradient mode and precision of each workload
+MODES = {1: ("fd", "fp64"), 2: ("fd", "fp64"), 3: ("adjoint", "fp64"), 4: ("adjoint", "mixed"),
+         5: ("adjoint", "mixed")}
 
 
 def parse():
@@ -42,53 +51,77 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--grad", default="fd", choices=["fd", "adjoint"],
-                    help="fd: one f+grad from the 9-point stencil per step (the workload's definition); "
-                         "adjoint: the 9 stencil points each get f and an adjoint gradient")
+    ap.add_argument("--grad", default=None, choices=["fd", "adjoint"],
+                    help="fd: one f+grad from the 9-point stencil per step; adjoint: every point of the "
+                         "workload's batch gets f and an adjoint gradient (default: the workload's own)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1, help="stencil centres per step (FD mode)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--evals", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--nt-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--with-grad", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_sample(cfg, evals):
-    """Time `evals` oracle f evaluations at the stencil centre (runs in a child process)."""
+def oracle_sample(cfg, evals, nt_sample, with_grad):
+    """Time `evals` oracle evaluations at the first point of the workload (child process).
+
+    For the large workloads the model is built with n_t = nt_sample time steps
+    (same grid, observations and batch) and the time is scaled by n_t / nt_sample:
+    the block algorithms cost the same per time step.
+    """
     from oracle import bta
-    from synth import config_model, theta_batch
-    mdl = config_model(cfg)
-    th = theta_batch(cfg, mdl)
+    from synth import CONFIGS, build, theta_batch, config_model
+    c = dict(CONFIGS[cfg])
+    scale = 1.0
+    if nt_sample and nt_sample < c["n_t"]:
+        scale = c["n_t"] / nt_sample
+        c["n_t"] = nt_sample
+    mdl = build(**c)
+    th = theta_batch(cfg, config_model(1) if cfg == 1 else mdl)
     t0 = time.perf_counter()
     for k in range(evals):
-        bta.gaussian(mdl, th[k % th.shape[0]])
-    dt = time.perf_counter() - t0
-    print(json.dumps({"seconds_per_f": dt / evals, "evals": evals}))
+        bta.evaluate(mdl, th[k % th.shape[0]], want_grad=with_grad)
+    dt = (time.perf_counter() - t0) * scale
+    print(json.dumps({"seconds_per_f": dt / evals, "evals": evals, "scale": scale}))
 
 
-def run_oracle_child(cfg, evals):
+def run_oracle_child(cfg, evals, nt_sample=0, with_grad=False):
     cores = os.cpu_count() or 1
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(cores)
     env["CUDA_VISIBLE_DEVICES"] = ""
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--config", str(cfg),
-                        "--evals", str(evals)], capture_output=True, text=True, env=env, timeout=1800)
+                        "--evals", str(evals), "--nt-sample", str(nt_sample)] + (["--with-grad"] if with_grad else []),
+                       capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])["seconds_per_f"], cores
 
 
-def cpu_baseline(cfg):
-    sec, cores = run_oracle_child(cfg, 1 if cfg == 2 else 9)
-    per_grad = 9 * sec   # one f + grad f by central differences = 9 f evaluations
+NT_SAMPLE = {1: 0, 2: 0, 3: 4, 4: 2, 5: 2}
+
+
+def cpu_baseline(cfg, grad):
+    if grad == "fd":
+        sec, cores = run_oracle_child(cfg, 1 if cfg == 2 else 9, NT_SAMPLE[cfg])
+        per_grad = 9 * sec   # one f + grad f by central differences = 9 f evaluations
+        what = f"oracle f at the stencil centre, {sec:.3f} s per f; 9 f per f+grad f"
+    else:
+        per_grad, cores = run_oracle_child(cfg, 1, NT_SAMPLE[cfg], with_grad=True)
+        what = f"oracle f + adjoint gradient at one point, {per_grad:.3f} s"
+    if NT_SAMPLE[cfg]:
+        what += f" (built with n_t = {NT_SAMPLE[cfg]}, time scaled linearly to the workload's n_t)"
     return {"value": 1.0 / per_grad, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"oracle f at the stencil centre timed on {cores} host threads (numpy BLAS), "
-                      f"{sec:.3f} s per f; 9 f per f+grad f"}
+            "sample": what + f"; {cores} host threads (numpy BLAS)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -151,29 +184,38 @@ def run_reference(args, rank, world):
         pass  # the oracle has no warm-up state; every step below is a fresh evaluation
     times = []
     cores = None
+    fd = args.grad == "fd"
     for _ in range(args.steps):
-        sec, cores = run_oracle_child(cfg, 1)
+        sec, cores = run_oracle_child(cfg, 1, NT_SAMPLE[cfg], with_grad=not fd)
         times.append(sec)
     t = sum(times) / len(times)
-    value = 1.0 / (9 * t)
+    per = 9 * t if fd else t
+    value = 1.0 / per
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * 9 * t, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * per, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_dict(cfg, world),
+            "config": config_dict(cfg, world, args.grad, args.precision),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "each step: one oracle f evaluation at the stencil centre; "
-                                       "f + grad f = 9 such evaluations"},
+                             "sample": ("each step: one oracle f evaluation at the stencil centre; "
+                                        "f + grad f = 9 such evaluations") if fd else
+                                       "each step: one oracle f + adjoint gradient at one point"
+                                       + (f" (n_t = {NT_SAMPLE[cfg]}, scaled to the workload's n_t)"
+                                          if NT_SAMPLE[cfg] else "")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def config_dict(cfg, world):
+def config_dict(cfg, world, grad=None, precision=None, points=9):
     from synth import CONFIGS
     c = CONFIGS[cfg]
+    grad = grad or MODES[cfg][0]
+    precision = precision or MODES[cfg][1]
     return {"workload": CONFIG_WORKLOAD[cfg], "n_t": c["n_t"], "n_s": c["nx"] ** 2, "n_b": c["n_b"], "m": c["m"],
-            "theta_points_per_step": 9, "grad": "central differences (9 points)", "prior_logdet": "kronecker",
+            "theta_points_per_step": points,
+            "grad": "central differences (9 points per centre)" if grad == "fd" else "adjoint",
+            "precision": precision, "prior_logdet": "kronecker",
             "likelihood": c["lik"], "parallelism": f"theta-replicas x{world}",
-            "l2": "working set (>= 3.8 GB factor storage per step) exceeds L2; no flush"}
+            "l2": "working set (GBs of factor storage per step) exceeds L2; no flush"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -181,8 +223,12 @@ def config_dict(cfg, world):
 def main():
     args = parse()
     if args.oracle_sample:
-        oracle_sample(args.config, args.evals)
+        oracle_sample(args.config, args.evals, args.nt_sample, args.with_grad)
         return
+    if args.grad is None:
+        args.grad = MODES[args.config][0]
+    if args.precision is None:
+        args.precision = MODES[args.config][1]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -210,6 +256,7 @@ def main():
     cfg = args.config
     peak_fp64 = pkg.measure_fp64_peak(local, tensor=False)
     peak_dmma = pkg.measure_fp64_peak(local, tensor=True)
+    peak_fp32 = pkg.measure_fp32_peak(local)
     if args.nt:
         from synth import CONFIGS, build
         mdl = build(**dict(CONFIGS[cfg], n_t=args.nt, name="profiling case"))
@@ -222,20 +269,28 @@ def main():
         cen = centre[None, :] + 0.01 * np.arange(args.centres)[:, None]
         theta = torch.tensor(cen, dtype=torch.float64, device="cuda")
         per_step = args.centres
+        points = 9 * args.centres
     else:
         from synth import fd_stencil
-        theta = torch.tensor(fd_stencil(centre), dtype=torch.float64, device="cuda")
+        batch = fd_stencil(centre) if cfg in (1, 2) else theta_batch(cfg, mdl) + 0.01 * rank
+        theta = torch.tensor(batch, dtype=torch.float64, device="cuda")
         per_step = theta.shape[0]
+        points = per_step
     grad = args.grad
-    out = model.eval(theta, grad=grad)
+    prec = args.precision
+    out = model.eval(theta, grad=grad, precision=prec)
     for w in range(max(args.warmup, 1)):
         if w == args.warmup - 1:
             model.profile_enable(PROFILE_EVERY)   # creates the event pool outside the timed region
-        model.eval(theta, grad=grad, out=out)
+        model.eval(theta, grad=grad, out=out, precision=prec)
     torch.cuda.synchronize()
-    assert int(out["status"][0]) == 0, "evaluation failed"
+    assert int(out["status"].abs().sum()) == 0, "evaluation failed"
     model.profile_enable(PROFILE_EVERY)
 
+    if args.graph:
+        model.profile_enable(0)          # event timing and graph replay exclude each other
+        model.eval(theta, grad=grad, out=out, precision=prec, use_graph=True)   # capture
+        torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -244,7 +299,7 @@ def main():
     launches = 0
     e0.record(stream)
     for _ in range(args.steps):
-        model.eval(theta, grad=grad, out=out)
+        model.eval(theta, grad=grad, out=out, precision=prec, use_graph=args.graph)
         launches += model.last_launch_count()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -253,45 +308,50 @@ def main():
     clk = clocks.stop()
     elapsed = e0.elapsed_time(e1) / 1e3
     if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t[0])
+        from paper_2204_04678_gb300.replicas import max_over_ranks
+        elapsed = max_over_ranks(elapsed)
     value = world * args.steps * per_step / elapsed
 
-    # dominant kernel: rank-64 tile update of the block sweep inversion
+    # dominant instrumented kernel: the sweep's tile update or the selected-inversion GEMM
     ms, nl, units = model.profile_read(capi.KERNEL_GJ_UPDATE)
     gms, gnl, gunits = model.profile_read(capi.KERNEL_GEMM)
     model.profile_enable(0)
     flop_per_unit = 2.0 * 64 ** 3
-    avg_s = ms / 1e3 / max(nl, 1)
-    flops_per_launch = units / max(nl, 1) * flop_per_unit
-    achieved = flops_per_launch / avg_s / 1e12 if nl else None
+    fp32 = prec == "mixed"
+    peak = peak_fp32 if fp32 else peak_fp64
+    kernels = {"gj_update_kernel": (ms, nl, units), "gemm_nn_kernel": (gms, gnl, gunits)}
+    kname = max(kernels, key=lambda k: kernels[k][0])
+    kms, knl, kunits = kernels[kname]
+    avg_s = kms / 1e3 / max(knl, 1)
+    achieved = kunits / max(knl, 1) * flop_per_unit / avg_s / 1e12 if knl else None
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "gj_update_traffic.txt")
-    if os.path.exists(tfile):
+    if kname == "gj_update_kernel" and not fp32 and os.path.exists(tfile):
         for line in open(tfile):
             if line.startswith("bytes_per_unit="):
-                traffic = float(line.split("=")[1]) * units / max(nl, 1)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64 if achieved else None, "traffic": traffic,
-                "kernel": "gj_update_kernel (FP64 rank-32 tile update of the block sweep inversion)",
+                traffic = float(line.split("=")[1]) * kunits / max(knl, 1)
+    desc = {"gj_update_kernel": "rank-32 tile update of the block sweep inversion",
+            "gemm_nn_kernel": "64x64 tile GEMM of the selected inversion"}[kname]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "kernel": f"{kname} ({'FP32' if fp32 else 'FP64'} {desc})",
                 "timed_every": PROFILE_EVERY,
-                "peak_source": "measured on this GPU: FP64 FMA loop over all SMs (inla_measure_fp64_peak)",
-                "launches_timed": nl, "share_of_step": ms / 1e3 / elapsed if elapsed else None}
+                "peak_source": ("measured on this GPU: " + ("FP32" if fp32 else "FP64")
+                                + " FMA loop over all SMs (inla_measure_fp32/fp64_peak)"),
+                "launches_timed": knl, "share_of_step": PROFILE_EVERY * kms / 1e3 / elapsed if elapsed else None}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
         th_host = theta.cpu().numpy().copy()
-        model.eval_host(th_host, grad=grad)
+        model.eval_host(th_host, grad=grad, precision=prec)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            model.eval_host(th_host, grad=grad)
+            model.eval_host(th_host, grad=grad, precision=prec)
         e2e_s = (time.perf_counter() - t0) / args.steps
         if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t[0])
+            from paper_2204_04678_gb300.replicas import max_over_ranks
+            e2e_s = max_over_ranks(e2e_s)
         nb = th_host.shape[0]
         e2e = {"value": world * per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * nb,
                "d2h_bytes_per_step": nb * (8 + 4 * 8 + 4 + 4)}
@@ -299,7 +359,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(cfg)
+            cpu = cpu_baseline(cfg, grad)
         except Exception as e:  # reported, not fatal
             cpu = {"value": None, "error": str(e)[:200]}
 
@@ -307,14 +367,16 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config_dict(cfg, world), "clocks": clk, "gpu_launches": launches,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
+                "data": "synthetic", "config": config_dict(cfg, world, grad, prec, points), "clocks": clk,
+                "gpu_launches": launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "f_evals_per_s": 9 * value if grad == "fd" else value,
                 "grad_mode": grad,
-                "fp64_peaks_tflops": {"fma": peak_fp64, "dmma": peak_dmma},
-                "gemm_kernel": {"ms": gms, "launches": gnl,
-                                "tflops": gunits * flop_per_unit / (gms / 1e3) / 1e12 if gms else None}}
+                "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32},
+                "kernels": {k: {"ms_sampled": v[0], "launches_sampled": v[1],
+                                "tflops": v[2] * flop_per_unit / (v[0] / 1e3) / 1e12 if v[0] else None}
+                            for k, v in kernels.items()}}
         if not (args.nt or args.centres != 1):
             print(json.dumps(line))
     if args.nt or args.centres != 1:

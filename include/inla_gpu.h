@@ -112,6 +112,9 @@ typedef struct {
   int32_t max_newton;     /* Poisson: iteration limit (<= 0: 50)                   */
   double newton_tol;      /* Poisson: stop when ||x^{k+1} - x^k||_2 < tol (<= 0: 1e-8) */
   double fd_eps;          /* central-difference step (<= 0: 1e-3)                  */
+  int32_t use_graph;      /* nonzero (Gaussian likelihood, batch in one wave): the  */
+                          /* whole evaluation is captured once per batch size and   */
+                          /* options as a CUDA graph and replayed on later calls    */
 } inla_eval_opts;
 
 /* Outputs of inla_eval_batch: DEVICE pointers owned by the caller.  Layout
@@ -223,6 +226,11 @@ const char *inla_last_error(void);
  * quoted against a measured FP64 peak.  use_tensor != 0 times the
  * warp-level double-precision MMA instruction instead of scalar FMA. */
 int inla_measure_fp64_peak(int device, int use_tensor, double *tflops);
+
+/* Measurement utility (no counterpart in the paper): FP32 scalar FMA
+ * throughput of this GPU in TFLOP/s (the denominator of the mixed-precision
+ * rooflines), measured like inla_measure_fp64_peak. */
+int inla_measure_fp32_peak(int device, double *tflops);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,7 @@ _PREC = {"fp64": C.INLA_FP64, "mixed": C.INLA_MIXED}
 
 
 def make_opts(grad="none", prior="kronecker", want_mode=False, want_marg_var=False, max_newton=50,
-              newton_tol=1e-8, fd_eps=1e-3, precision="fp64"):
+              newton_tol=1e-8, fd_eps=1e-3, precision="fp64", use_graph=False):
     o = C.inla_eval_opts()
     o.grad = _GRAD[grad]
     o.prior_mode = _PRIOR[prior]
@@ -34,6 +34,7 @@ def make_opts(grad="none", prior="kronecker", want_mode=False, want_marg_var=Fal
     o.max_newton = int(max_newton)
     o.newton_tol = float(newton_tol)
     o.fd_eps = float(fd_eps)
+    o.use_graph = int(bool(use_graph))
     return o
 
 
@@ -108,7 +109,7 @@ class Model:
         return ms.value, n.value, u.value
 
     def eval(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False, max_newton=50,
-             newton_tol=1e-8, fd_eps=1e-3, stream=None, out=None, precision="fp64"):
+             newton_tol=1e-8, fd_eps=1e-3, stream=None, out=None, precision="fp64", use_graph=False):
         """Evaluate a batch on the GPU.  theta: CUDA float64 tensor [B, 4].
 
         Returns a dict of CUDA tensors: f [B], grad [B, 4] (if requested),
@@ -133,7 +134,7 @@ class Model:
                 out["x_mode"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
             if want_marg_var:
                 out["marg_var"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
-        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision, use_graph)
         so = C.inla_eval_out()
         so.f_dev = out["f"].data_ptr()
         so.status_dev = out["status"].data_ptr()
@@ -208,6 +209,14 @@ def measure_fp64_peak(device=0, tensor=False):
     lib = C.load()
     v = c_double()
     C.check(lib.inla_measure_fp64_peak(int(device), int(bool(tensor)), byref(v)))
+    return v.value
+
+
+def measure_fp32_peak(device=0):
+    """Measured FP32 scalar FMA throughput (TFLOP/s)."""
+    lib = C.load()
+    v = c_double()
+    C.check(lib.inla_measure_fp32_peak(int(device), byref(v)))
     return v.value
 
 

@@ -48,7 +48,7 @@ class inla_model_desc(ctypes.Structure):
 class inla_eval_opts(ctypes.Structure):
     _fields_ = [("grad", c_int32), ("prior_mode", c_int32), ("precision", c_int32), ("want_mode", c_int32),
                 ("want_marg_var", c_int32), ("max_newton", c_int32), ("newton_tol", c_double),
-                ("fd_eps", c_double)]
+                ("fd_eps", c_double), ("use_graph", c_int32)]
 
 
 class inla_eval_out(ctypes.Structure):
@@ -76,6 +76,7 @@ SIGNATURES = {
     "inla_model_destroy": (None, [c_void_p]),
     "inla_last_error": (c_char_p, []),
     "inla_measure_fp64_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
+    "inla_measure_fp32_peak": (c_int, [c_int, POINTER(c_double)]),
     "inla_profile_enable": (c_int, [c_void_p, c_int]),
     "inla_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]),
 }

@@ -90,6 +90,17 @@ struct inla_model {
   bool done_valid = false;
   int64_t launches = 0;
   Profiler prof;
+  struct GraphEntry {
+    int B, grad, prior, precision, want_mode, want_marg_var;
+    double fd_eps;
+    void *ws, *bb;                 // workspace the graph was captured on
+    cudaGraphExec_t exec = nullptr;
+    void *stage = nullptr;         // theta in, outputs out (device)
+    double *theta, *f, *grad_out, *x, *mv;
+    int *status, *iters;
+    int64_t launches = 0;
+  };
+  std::vector<GraphEntry> graphs;
   // host-API staging buffers (device)
   void *hb = nullptr;
   size_t hb_bytes = 0;
@@ -118,6 +129,10 @@ struct inla_model {
     if (hb) cudaFree(hb);
     if (stream) cudaStreamDestroy(stream);
     if (done) cudaEventDestroy(done);
+    for (auto &g : graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.stage) cudaFree(g.stage);
+    }
     cudaSetDevice(cur);
   }
 };
@@ -750,6 +765,11 @@ void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o
   else run_wave_t<double>(mdl, L, W, o, w0, bb, x_out, mv_out, centre_flags);
 }
 
+void enqueue_eval(inla_model *mdl, Launch &L, int B, const double *theta_dev, const inla_eval_opts *opts,
+                  const inla_eval_out *out, const BatchBufs &bb, int Pw, int rb);
+void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_eval_opts *opts,
+                  const inla_eval_out *out, cudaStream_t st, const BatchBufs &bb, int rb);
+
 int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_eval_opts *opts,
                   const inla_eval_out *out, cudaStream_t st) {
   if (!mdl || !opts || !out || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
@@ -764,15 +784,32 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   const int rb = opts->precision == INLA_MIXED ? 4 : 8;
   CUDA_OK(cudaSetDevice(mdl->device));
   const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
-  const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
   const int64_t P_total = (int64_t)B * per;
   mdl->launches = 0;
-  Launch L{st, &mdl->launches, &mdl->prof};
   // the workspace is shared by all calls on this model: order this call after the previous one
   if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
   const int Pw = wave_points(mdl, P_total, rb);
   ensure_workspace(mdl, Pw, rb);
   BatchBufs bb = batch_buffers(mdl, P_total);
+  if (opts->use_graph && mdl->M.lik == INLA_LIK_GAUSSIAN && Pw == P_total && !mdl->prof.enabled) {
+    replay_graph(mdl, B, theta_dev, opts, out, st, bb, rb);
+  } else {
+    Launch L{st, &mdl->launches, &mdl->prof};
+    enqueue_eval(mdl, L, B, theta_dev, opts, out, bb, Pw, rb);
+  }
+  CUDA_OK(cudaEventRecord(mdl->done, st));
+  mdl->done_valid = true;
+  CUDA_OK(cudaGetLastError());
+  return mdl->launches;
+}
+
+// The whole evaluation of one call, enqueued on L.st (eager path and graph capture).
+void enqueue_eval(inla_model *mdl, Launch &L, int B, const double *theta_dev, const inla_eval_opts *opts,
+                  const inla_eval_out *out, const BatchBufs &bb, int Pw, int rb) {
+  cudaStream_t st = L.st;
+  const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+  const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
+  const int64_t P_total = (int64_t)B * per;
   point_out_kernel<<<(unsigned)((P_total + 127) / 128), 128, 0, st>>>((int)P_total, per, bb.point_out);
   L.tick();
   if (per == 9) k_fd_points(L, B, theta_dev, eps, bb.theta_all);
@@ -792,10 +829,79 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   k_outputs(L, B, per, eps, 4, bb.f_all, opts->grad == INLA_GRAD_ADJOINT ? bb.grad_all : nullptr, bb.status_all,
             bb.iters_all, out->f_dev, opts->grad != INLA_GRAD_NONE ? out->grad_dev : nullptr, out->status_dev,
             out->newton_iters_dev);
-  CUDA_OK(cudaEventRecord(mdl->done, st));
-  mdl->done_valid = true;
-  CUDA_OK(cudaGetLastError());
-  return mdl->launches;
+}
+
+// CUDA graph of the whole evaluation for one (batch size, options, workspace):
+// captured once on the model's stream with model-owned input/output buffers,
+// then replayed with one copy of theta in and one copy per output out.
+void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_eval_opts *opts,
+                  const inla_eval_out *out, cudaStream_t st, const BatchBufs &bb, int rb) {
+  const int64_t n = mdl->M.n;
+  inla_model::GraphEntry *g = nullptr;
+  for (auto &e : mdl->graphs)
+    if (e.B == B && e.grad == opts->grad && e.prior == opts->prior_mode && e.precision == opts->precision &&
+        e.want_mode == (opts->want_mode != 0) && e.want_marg_var == (opts->want_marg_var != 0) &&
+        e.fd_eps == opts->fd_eps && e.ws == mdl->ws && e.bb == mdl->bb)
+      g = &e;
+  if (!g) {
+    inla_model::GraphEntry e{};
+    e.B = B; e.grad = opts->grad; e.prior = opts->prior_mode; e.precision = opts->precision;
+    e.want_mode = opts->want_mode != 0; e.want_marg_var = opts->want_marg_var != 0; e.fd_eps = opts->fd_eps;
+    e.ws = mdl->ws; e.bb = mdl->bb;
+    const size_t bytes = rup(32 * B, 256) + rup(8 * B, 256) + rup(32 * B, 256) + 2 * rup(4 * B, 256) +
+                         2 * rup(8 * n * B, 256);
+    CUDA_OK(cudaDeviceSynchronize());
+    CUDA_OK(cudaMalloc(&e.stage, bytes));
+    char *p = static_cast<char *>(e.stage);
+    auto take = [&](size_t b) { char *r = p; p += rup(b, 256); return r; };
+    e.theta = reinterpret_cast<double *>(take(32 * B));
+    e.f = reinterpret_cast<double *>(take(8 * B));
+    e.grad_out = reinterpret_cast<double *>(take(32 * B));
+    e.status = reinterpret_cast<int *>(take(4 * B));
+    e.iters = reinterpret_cast<int *>(take(4 * B));
+    e.x = reinterpret_cast<double *>(take(8 * n * B));
+    e.mv = reinterpret_cast<double *>(take(8 * n * B));
+    inla_eval_out so{};
+    so.f_dev = e.f; so.grad_dev = e.grad_out; so.status_dev = e.status; so.newton_iters_dev = e.iters;
+    so.x_mode_dev = e.x; so.marg_var_dev = e.mv;
+    dense_prepare();
+    int64_t count = 0;
+    Launch L{mdl->stream, &count, nullptr};
+    cudaGraph_t graph = nullptr;
+    CUDA_OK(cudaStreamBeginCapture(mdl->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_eval(mdl, L, B, e.theta, opts, &so, bb, (int)((int64_t)B * (opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1)),
+                   rb);
+    } catch (...) {
+      cudaStreamEndCapture(mdl->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaFree(e.stage);
+      throw;
+    }
+    CUDA_OK(cudaStreamEndCapture(mdl->stream, &graph));
+    cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaFree(e.stage);
+      throw ApiError(INLA_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    e.launches = count;
+    mdl->graphs.push_back(e);
+    g = &mdl->graphs.back();
+  }
+  CUDA_OK(cudaMemcpyAsync(g->theta, theta_dev, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(cudaGraphLaunch(g->exec, st));
+  CUDA_OK(cudaMemcpyAsync(out->f_dev, g->f, sizeof(double) * B, cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(cudaMemcpyAsync(out->status_dev, g->status, sizeof(int) * B, cudaMemcpyDeviceToDevice, st));
+  if (out->newton_iters_dev)
+    CUDA_OK(cudaMemcpyAsync(out->newton_iters_dev, g->iters, sizeof(int) * B, cudaMemcpyDeviceToDevice, st));
+  if (opts->grad != INLA_GRAD_NONE)
+    CUDA_OK(cudaMemcpyAsync(out->grad_dev, g->grad_out, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
+  if (opts->want_mode)
+    CUDA_OK(cudaMemcpyAsync(out->x_mode_dev, g->x, sizeof(double) * n * B, cudaMemcpyDeviceToDevice, st));
+  if (opts->want_marg_var)
+    CUDA_OK(cudaMemcpyAsync(out->marg_var_dev, g->mv, sizeof(double) * n * B, cudaMemcpyDeviceToDevice, st));
+  mdl->launches = g->launches;
 }
 
 template <class F>

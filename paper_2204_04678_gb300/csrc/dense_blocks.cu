@@ -383,6 +383,11 @@ void ensure_attrs() {
 
 }  // namespace
 
+void dense_prepare() {
+  ensure_attrs<double>();
+  ensure_attrs<float>();
+}
+
 template <typename R>
 void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet_out,
                int logdet_slot_stride) {

@@ -180,6 +180,7 @@ struct Launch {
 };
 
 // dense_blocks.cu (R = double or float)
+void dense_prepare();   // one-time kernel attributes (call before a stream capture)
 template <typename R>
 void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet, int ld_stride);
 template <typename R>

@@ -1,7 +1,7 @@
-// FP64 throughput probe (measurement utility; no counterpart in the paper).
-// Every SM runs register-resident chains of independent FP64 fused
-// multiply-adds (scalar FMA, or the warp-level m8n8k4 double-precision MMA
-// instruction) for a fixed number of iterations; the rate is
+// Throughput probes (measurement utilities; no counterpart in the paper).
+// Every SM runs register-resident chains of independent fused multiply-adds
+// (FP64 scalar FMA, the warp-level m8n8k4 double-precision MMA instruction,
+// or FP32 scalar FMA) for a fixed number of iterations; the rate is
 // flops / CUDA-event time.  The loops are bounded and touch no memory except
 // one store per thread at the end (so the compiler cannot drop them).
 #include <cuda_runtime.h>
@@ -47,7 +47,64 @@ __global__ void __launch_bounds__(256) dmma_probe(int iters, double *sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void __launch_bounds__(256) ffma_probe(int iters, float *sink) {
+  float a[CHAINS];
+  const float x = 1.0f + 1e-7f * threadIdx.x, y = 1.0f - 1e-7f * blockIdx.x;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) a[c] = 0.5f * c;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) a[c] = fmaf(a[c], x, y);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < CHAINS; ++c) s += a[c];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
+
+extern "C" int inla_measure_fp32_peak(int device, double *tflops) {
+  if (!tflops) {
+    inla::set_error("tflops is NULL");
+    return INLA_ERR_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    inla::set_error("cudaSetDevice failed");
+    return INLA_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, device);
+  const int blocks = prop.multiProcessorCount * 8, threads = 256, iters = 1 << 16;
+  float *sink = nullptr;
+  if (cudaMalloc(&sink, sizeof(float) * blocks * threads) != cudaSuccess) {
+    inla::set_error("cudaMalloc failed");
+    return INLA_ERR_OOM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0);
+    ffma_probe<<<blocks, threads>>>(iters, sink);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (err != cudaSuccess) {
+    inla::set_error(cudaGetErrorString(err));
+    return INLA_ERR_CUDA;
+  }
+  *tflops = (double)blocks * threads * CHAINS * 2 * iters / (best * 1e-3) / 1e12;
+  return INLA_OK;
+}
 
 extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops) {
   if (!tflops) {

@@ -267,3 +267,18 @@ def test_mixed_precision_full_size_config2(pkg):
     assert np.abs(gm - gd).max() <= MIX_G * max(1.0, np.abs(gd).max())
     x = r["x_mode"][0].cpu().numpy()
     assert np.abs(x - ref["x"]).max() <= MIX_X * np.abs(ref["x"]).max()
+
+
+def test_cuda_graph_replay_matches_eager(pkg):
+    mdl = build("g", 4, 9, 2, 500, "gaussian", seed=12)
+    model = pkg.Model(mdl)
+    for kw in (dict(grad="adjoint", want_mode=True, want_marg_var=True), dict(grad="fd"),
+               dict(grad="adjoint", precision="mixed")):
+        for k in (3, 2, 3):     # the third call replays the graph captured by the first
+            th = cuda(thetas(mdl, k, seed=k))
+            eager = model.eval(th, **kw)
+            graph = model.eval(th, use_graph=True, **kw)
+            torch.cuda.synchronize()
+            for key in ("f", "grad", "x_mode", "marg_var", "status"):
+                if key in eager:
+                    assert torch.equal(eager[key], graph[key]), (kw, k, key)
