@@ -144,8 +144,9 @@ __global__ void init_step0_kernel(DevModel M, Work W, int mode) {
 
 // Dense diagonal block: D_t = c_t Q_s + (likelihood block) - [schur] q_off^2 Q_s T1,
 // with T1 = Dinv_{t-1} Q_s; identity in the padding.  mode ASM_QS builds Q_s alone.
-// Only the lower 32-wide tiles are written: the block sweep reads nothing else.
-constexpr int SWEEP_TILE = 32;
+// Only the lower 32-wide tiles are written: the block sweep (32- or 64-wide
+// tiles) reads nothing else.  T1 is computed up to 64-wide tiles past the band.
+constexpr int SWEEP_TILE = 32, SWEEP_TILE_MAX = 64;
 template <typename R>
 __global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, R *dst, int64_t sdst, int schur) {
   const int b = blockIdx.z;
@@ -185,6 +186,53 @@ __global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, R *dst
 // out[i][j] = coef * sum_k X[i][k] Q_s[k][j] + sum_l SigA[l][i] Rt[l][j]   (i, j < n_s; 0 elsewhere)
 // lower_band: only columns j < (floor((i + pbw) / 32) + 1) * 32, the ones the
 // lower-tile assembly of rows within the pattern bandwidth of i reads.
+// Tiled form: a block computes 64 rows x 32 columns of the output.  The pattern
+// rows of its 32 columns are staged once in shared memory (SR_PMAX entries
+// each), so the CSR is read once per 64 output rows instead of once per row.
+constexpr int SR_COLS = 32, SR_ROWS = 64, SR_PMAX = 32;
+template <typename R>
+__global__ void __launch_bounds__(256) sparse_right_tiled_kernel(DevModel M, Work W, const R *X, int64_t sX, R *outp,
+                                                                int64_t sOut, int coef_qoff, const double *SigA,
+                                                                const double *Rt_t, int lower_band) {
+  const int b = blockIdx.z;
+  if (!W.active[b]) return;
+  __shared__ int pc[SR_COLS][SR_PMAX + 1];   // +1: consecutive columns in distinct banks
+  __shared__ R pv[SR_COLS][SR_PMAX + 1];
+  __shared__ int pn[SR_COLS];
+  const int n_p = M.n_p, n_s = M.n_s;
+  const int j0 = blockIdx.x * SR_COLS, i0 = blockIdx.y * SR_ROWS;
+  const int tj = threadIdx.x & 31, ti = threadIdx.x >> 5;
+  const double *qs = W.qs + b * W.sNnz;
+  const R coef = coef_qoff ? (R)W.prm[b].q_off : R(1);
+  for (int c = ti; c < SR_COLS; c += 8) {
+    const int j = j0 + c;
+    const int e0 = (j < n_s) ? M.prow[j] : 0, len = (j < n_s) ? M.prow[j + 1] - e0 : 0;
+    if (tj == 0) pn[c] = len;
+    if (tj < len) {
+      pc[c][tj] = M.pcol[e0 + tj];
+      pv[c][tj] = coef * (R)qs[e0 + tj];
+    }
+  }
+  __syncthreads();
+  const int j = j0 + tj;
+  const int len = pn[tj];
+  const double *sa = SigA ? SigA + b * W.sNbNp : nullptr;
+  const double *rt = SigA ? Rt_t + b * W.sRt : nullptr;
+  for (int r = 0; r < SR_ROWS / 8; ++r) {
+    const int i = i0 + ti + 8 * r;
+    if (i >= n_p || j >= n_p) continue;
+    if (lower_band && j >= ((i + M.pbw) / SWEEP_TILE_MAX + 1) * SWEEP_TILE_MAX) continue;
+    R *out = outp + b * sOut + (int64_t)i * n_p + j;
+    if (i >= n_s || j >= n_s) { *out = R(0); continue; }
+    const R *Xi = X + b * sX + (int64_t)i * n_p;
+    R acc = 0;
+    for (int e = 0; e < len; ++e) acc = fma(Xi[pc[tj][e]], pv[tj][e], acc);
+    if (sa)
+      for (int l = 0; l < M.n_b; ++l) acc = fma((R)sa[(int64_t)l * n_p + i], (R)rt[(int64_t)l * n_p + j], acc);
+    *out = acc;
+  }
+}
+
 template <typename R>
 __global__ void sparse_right_kernel(DevModel M, Work W, const R *X, int64_t sX, R *outp, int64_t sOut,
                                     int coef_qoff, const double *SigA, const double *Rt_t, int lower_band) {
@@ -194,7 +242,7 @@ __global__ void sparse_right_kernel(DevModel M, Work W, const R *X, int64_t sX, 
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_p = M.n_p, n_s = M.n_s;
   if (j >= n_p) return;
-  if (lower_band && j >= ((i + M.pbw) / SWEEP_TILE + 1) * SWEEP_TILE) return;
+  if (lower_band && j >= ((i + M.pbw) / SWEEP_TILE_MAX + 1) * SWEEP_TILE_MAX) return;
   R *out = outp + b * sOut + (int64_t)i * n_p + j;
   if (i >= n_s || j >= n_s) { *out = R(0); return; }
   const R *Xi = X + b * sX + (int64_t)i * n_p;
@@ -242,23 +290,24 @@ constexpr int DA_ROWS_PER_WARP = 2;
 constexpr int DA_ROWS = 8 * DA_ROWS_PER_WARP;
 constexpr int DA_CHUNK = 256;
 constexpr int DA_MAXV = 1 + MAX_NB;
-template <typename R>
+// NV: the number of vectors the kernel is compiled for (1, or up to 1 + MAX_NB).
+template <typename R, int NV>
 __global__ void __launch_bounds__(256) dinv_apply_kernel(DevModel M, Work W, const R *Dinv_t, int nvec,
                                                         const double *vecs, int64_t sVecs, double *outp,
                                                         int64_t sOut, double scale) {
   const int b = blockIdx.y;
   if (!W.active[b]) return;
-  __shared__ R vs[DA_MAXV * DA_CHUNK];
+  __shared__ R vs[NV * DA_CHUNK];
   const int n_p = M.n_p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * DA_ROWS + warp * DA_ROWS_PER_WARP;
   const R *D = Dinv_t + b * W.sDinv;
   const double *V = vecs + b * sVecs;
-  R acc[DA_ROWS_PER_WARP][DA_MAXV];
+  R acc[DA_ROWS_PER_WARP][NV];
 #pragma unroll
   for (int r = 0; r < DA_ROWS_PER_WARP; ++r)
 #pragma unroll
-    for (int c = 0; c < DA_MAXV; ++c) acc[r][c] = 0;
+    for (int c = 0; c < NV; ++c) acc[r][c] = 0;
   for (int k0 = 0; k0 < n_p; k0 += DA_CHUNK) {
     __syncthreads();
     for (int e = threadIdx.x; e < nvec * DA_CHUNK; e += blockDim.x) {
@@ -274,8 +323,8 @@ __global__ void __launch_bounds__(256) dinv_apply_kernel(DevModel M, Work W, con
       for (int q = lane; q < DA_CHUNK && k0 + q < n_p; q += 32) {
         const R d = Dr[q];
 #pragma unroll
-        for (int c = 0; c < DA_MAXV; ++c)
-          if (c < nvec) acc[r][c] = fma(d, vs[c * DA_CHUNK + q], acc[r][c]);
+        for (int c = 0; c < NV; ++c)
+          if (NV == 1 || c < nvec) acc[r][c] = fma(d, vs[c * DA_CHUNK + q], acc[r][c]);
       }
     }
   }
@@ -284,7 +333,7 @@ __global__ void __launch_bounds__(256) dinv_apply_kernel(DevModel M, Work W, con
   for (int r = 0; r < DA_ROWS_PER_WARP; ++r) {
     const int row = row0 + r;
 #pragma unroll
-    for (int c = 0; c < DA_MAXV; ++c) {
+    for (int c = 0; c < NV; ++c) {
       if (c >= nvec) break;
       const R s = warp_sum(acc[r][c]);
       if (lane == 0 && row < n_p) O[(int64_t)c * n_p + row] = scale * (double)s;
@@ -1118,6 +1167,12 @@ void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mod
 template <typename R>
 void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const R *X, int64_t sX, R *out, int64_t sOut,
                     bool coef_qoff, const double *SigA, const double *Rt_t, bool lower_band) {
+  if (M.pmax <= SR_PMAX) {
+    sparse_right_tiled_kernel<R><<<dim3(blocks(M.n_p, SR_COLS), blocks(M.n_p, SR_ROWS), W.P), 256, 0, L.st>>>(
+        M, W, X, sX, out, sOut, coef_qoff ? 1 : 0, SigA, Rt_t, lower_band ? 1 : 0);
+    L.tick();
+    return;
+  }
   sparse_right_kernel<R><<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
                                                                                coef_qoff ? 1 : 0, SigA, Rt_t,
                                                                                lower_band ? 1 : 0);
@@ -1134,8 +1189,12 @@ template <typename R>
 void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const R *Dinv_t, int nvec, const double *vecs,
                   int64_t sVecs, double *out, int64_t sOut, double scale) {
   if (nvec <= 0) return;
-  dinv_apply_kernel<R><<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs, sVecs, out,
-                                                                         sOut, scale);
+  if (nvec == 1)
+    dinv_apply_kernel<R, 1><<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs, sVecs,
+                                                                               out, sOut, scale);
+  else
+    dinv_apply_kernel<R, DA_MAXV><<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs,
+                                                                                     sVecs, out, sOut, scale);
   L.tick();
 }
 void k_arrow_update(Launch &L, const DevModel &M, const Work &W, int t, int mode) {

@@ -281,6 +281,9 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     for (int i = 0; i < n_s; ++i)
       for (int e = prow[i]; e < prow[i + 1]; ++e) pbw = std::max(pbw, std::abs(pcol[e] - i));
     M.pbw = pbw;
+    int pmax = 0;
+    for (int i = 0; i < n_s; ++i) pmax = std::max(pmax, prow[i + 1] - prow[i]);
+    M.pmax = pmax;
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);

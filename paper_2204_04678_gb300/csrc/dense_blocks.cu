@@ -42,34 +42,157 @@ __device__ __forceinline__ void tri_index(int x, int &I, int &J) {
 }
 
 // ---------------------------------------------------------------- block sweep
-// Pivot blocks and update tiles are 32 x 32 (GT); a block of 128 threads
-// owns one tile, so one update launch has P * nt(nt+1)/2 small blocks that
-// balance well over 152 SMs (up to 16 resident blocks per SM).
-constexpr int GT = 32;
-constexpr int GLD = GT + 1;
-constexpr int GTHREADS = 128;
-constexpr int GTRI = GT * (GT + 1) / 2;                    // 528 lower entries
-constexpr int GPER = (GTRI + GTHREADS - 1) / GTHREADS;     // entries per thread
-constexpr int SWEEP_SMEM_DOUBLES = GT * GLD + 3 * GT;
+// Pivot blocks and update tiles are G x G: G = 32 in FP64 (128 threads, 2 x 4
+// outputs per thread) and G = 64 in FP32 (256 threads, 4 x 4 outputs per
+// thread).  One update launch has P * nt(nt+1)/2 blocks that balance well over
+// the 152 SMs.
+template <int G>
+struct Sweep {
+  static constexpr int LD = G + 1;                         // padded shared-memory row
+  static constexpr int TX = G / 4;                         // threads along a tile row
+  static constexpr int THREADS = 4 * G;                    // 16 rows of threads
+  static constexpr int MI = G / 16;                        // output rows per thread
+  static constexpr int TRI = G * (G + 1) / 2;              // lower entries
+  static constexpr int PER = (TRI + THREADS - 1) / THREADS;
+  static constexpr int SMEM_ELEMS = G * LD + 16 * 17 + 2 * G * 16 + G;   // sweep workspace (both forms)
+  static constexpr int SHIFT = G == 32 ? 5 : 6;
+};
 
-// Scalar sweep of a 32 x 32 SPD block held (lower triangle) in shared memory:
-// after 32 steps it holds -A^-1.  Writes P = A^-1 (full symmetric tile) to
-// Pout and adds log|A| = sum_p log(pivot_p), accumulated in double, to
-// *logdet; a non-positive pivot sets *status.  One FMA per lower entry and
-// step; one reciprocal per step; the logarithms once at the end.  The sweep
-// runs in the storage type R of the blocks.  Called by all GTHREADS threads.
-template <typename R>
-__device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
-  R *a = sm;                       // [32][33]
-  R *colp = sm + GT * GLD;         // [32]  column p of the current state
-  R *cinv = colp + GT;             // [32]  column p divided by the pivot
-  R *pivs = cinv + GT;             // [32]  pivots
+// Inversion of a G x G SPD block held (lower triangle) in shared memory, by the
+// same sweep applied recursively: for each 16-wide sub-pivot, one warp sweeps
+// the 16 x 16 sub-pivot element by element (warp-synchronous), then all
+// threads form the sub-panel C = A_iK P_K and apply the rank-16 update to the
+// whole block.  On return Pout holds A^-1 (full symmetric tile) and *logdet
+// has gained log|A| = sum of log pivots (accumulated in double); a non-positive
+// pivot sets *status.  Arithmetic in the storage type R.  Called by all
+// Sweep<G>::THREADS threads; shared workspace Sweep<G>::SMEM_ELEMS elements.
+constexpr int SB = 16;
+template <typename R, int G>
+__device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) {
+  using S = Sweep<G>;
+  constexpr int LD = S::LD;
+  R *a = sm;                          // [G][LD]   full symmetric working copy
+  R *sp = sm + G * LD;                // [SB][SB+1] sub-pivot, then its inverse
+  R *Cp = sp + SB * (SB + 1);         // [G][SB]   sub-panel C = A_iK P
+  R *Op = Cp + G * SB;                // [G][SB]   old column block A_iK
+  R *pv = Op + G * SB;                // [G]       scalar pivots
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // mirror the lower triangle so that the working copy is full
+  for (int e = tid; e < G * G; e += S::THREADS) {
+    const int i = e >> S::SHIFT, j = e & (G - 1);
+    if (j > i) a[i * LD + j] = a[j * LD + i];
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int kb = 0; kb < G / SB; ++kb) {
+    const int K0 = kb * SB;
+    if (warp == 0) {
+      // 1. scalar sweep of the 16 x 16 sub-pivot by one warp: 8 entries per lane
+      R v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = lane + 32 * q, i = e >> 4, j = e & 15;
+        v[q] = a[(K0 + i) * LD + K0 + j];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int e = lane + 32 * q;
+        sp[(e >> 4) * (SB + 1) + (e & 15)] = v[q];
+      }
+      __syncwarp();
+      bool bad = false;
+      for (int p = 0; p < SB; ++p) {
+        const R piv = sp[p * (SB + 1) + p];
+        const bool ok = (piv > R(0)) && (piv < R(INFINITY));
+        if (!ok) bad = true;
+        const R inv = ok ? R(1) / piv : R(0);
+        R ip[8], pj[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = lane + 32 * q, i = e >> 4, j = e & 15;
+          ip[q] = sp[i * (SB + 1) + p];
+          pj[q] = sp[p * (SB + 1) + j];
+          v[q] = sp[i * (SB + 1) + j];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int e = lane + 32 * q, i = e >> 4, j = e & 15;
+          R w;
+          if (i == p) w = (j == p) ? -inv : pj[q] * inv;
+          else if (j == p) w = ip[q] * inv;
+          else w = fma(-ip[q] * inv, pj[q], v[q]);
+          sp[i * (SB + 1) + j] = w;
+        }
+        if (lane == 0) pv[K0 + p] = ok ? piv : R(1);
+        __syncwarp();
+      }
+      if (bad && lane == 0) s_bad = 1;
+      // sp now holds -P, P = (sub-pivot)^-1
+    }
+    __syncthreads();
+    // 2. sub-panel C_i = A_iK P for rows i outside the sub-pivot; keep the old A_iK
+    for (int e = tid; e < G * SB; e += S::THREADS) {
+      const int i = e / SB, c = e % SB;
+      if (i >= K0 && i < K0 + SB) continue;
+      R acc = 0;
+#pragma unroll
+      for (int k = 0; k < SB; ++k) acc = fma(a[i * LD + K0 + k], -sp[k * (SB + 1) + c], acc);
+      Cp[i * SB + c] = acc;
+      Op[i * SB + c] = a[i * LD + K0 + c];
+    }
+    __syncthreads();
+    // 3. rank-16 update of everything outside the sub-pivot rows/columns; the
+    //    sub-pivot row/column become C, the sub-pivot block -P
+    for (int e = tid; e < G * G; e += S::THREADS) {
+      const int i = e >> S::SHIFT, j = e & (G - 1);
+      const bool ik = i >= K0 && i < K0 + SB, jk = j >= K0 && j < K0 + SB;
+      R w;
+      if (ik && jk) w = sp[(i - K0) * (SB + 1) + (j - K0)];
+      else if (jk) w = Cp[i * SB + (j - K0)];
+      else if (ik) w = Cp[j * SB + (i - K0)];
+      else {
+        w = a[i * LD + j];
+#pragma unroll
+        for (int c = 0; c < SB; ++c) w = fma(-Cp[i * SB + c], Op[j * SB + c], w);
+      }
+      a[i * LD + j] = w;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < G * G; e += S::THREADS) {
+    const int i = e >> S::SHIFT, j = e & (G - 1);
+    Pout[e] = -a[i * LD + j];
+  }
+  if (tid < 32) {
+    double l = 0.0;
+    for (int p = tid; p < G; p += 32) l += log((double)pv[p]);
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if (tid == 0) {
+      *logdet += l;
+      if (s_bad) *status = INLA_ERR_NOT_SPD;
+    }
+  }
+}
+
+// Scalar sweep of the lower triangle: G steps, each one FMA per lower entry;
+// the fewest FP64 instructions, which matters when the fused sweep shares an
+// SM whose FP64 pipe the update blocks saturate.
+template <typename R, int G>
+__device__ void sweep_tile_scalar(R *sm, R *Pout, double *logdet, int *status) {
+  using S = Sweep<G>;
+  R *a = sm;                       // [G][LD]
+  R *colp = sm + G * S::LD;        // [G]  column p of the current state
+  R *cinv = colp + G;              // [G]  column p divided by the pivot
+  R *pivs = cinv + G;              // [G]  pivots
   __shared__ R s_inv;
   __shared__ int s_bad;
+  __shared__ double s_log[2];
   const int tid = threadIdx.x;
-  int ei[GPER], ej[GPER];
+  int ei[S::PER], ej[S::PER];
   int ne = 0;
-  for (int e = tid; e < GTRI; e += GTHREADS) {
+  for (int e = tid; e < S::TRI; e += S::THREADS) {
     int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
     while ((i + 1) * (i + 2) / 2 <= e) ++i;
     while (i * (i + 1) / 2 > e) --i;
@@ -79,125 +202,137 @@ __device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
   }
   if (tid == 0) s_bad = 0;
   __syncthreads();
-  for (int p = 0; p < GT; ++p) {
+  for (int p = 0; p < G; ++p) {
     if (tid == 0) {
-      const R piv = a[p * GLD + p];
+      const R piv = a[p * S::LD + p];
       const bool ok = (piv > R(0)) && (piv < R(INFINITY));
       pivs[p] = ok ? piv : R(1);
       s_inv = ok ? R(1) / piv : R(0);
       if (!ok) s_bad = 1;
     }
     __syncthreads();
-    if (tid < GT) {
-      const R c = (tid >= p) ? a[tid * GLD + p] : a[p * GLD + tid];
+    if (tid < G) {
+      const R c = (tid >= p) ? a[tid * S::LD + p] : a[p * S::LD + tid];
       colp[tid] = c;
       cinv[tid] = c * s_inv;
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < GPER; ++k) {
+    for (int k = 0; k < S::PER; ++k) {
       if (k >= ne) break;
       const int i = ei[k], j = ej[k];
-      R *ap = &a[i * GLD + j];
+      R *ap = &a[i * S::LD + j];
       if (i == p) *ap = (j == p) ? -s_inv : cinv[j];
       else if (j == p) *ap = cinv[i];
       else *ap = fma(-cinv[i], colp[j], *ap);
     }
     __syncthreads();
   }
-  for (int e = tid; e < GT * GT; e += GTHREADS) {
-    const int i = e >> 5, j = e & 31;
-    Pout[e] = -((j <= i) ? a[i * GLD + j] : a[j * GLD + i]);
+  for (int e = tid; e < G * G; e += S::THREADS) {
+    const int i = e >> S::SHIFT, j = e & (G - 1);
+    Pout[e] = -((j <= i) ? a[i * S::LD + j] : a[j * S::LD + i]);
   }
-  if (tid < 32) {
+  if (tid < G) {
     double l = log((double)pivs[tid]);
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if (tid == 0) {
-      *logdet += l;
-      if (s_bad) *status = INLA_ERR_NOT_SPD;
-    }
+    if ((tid & 31) == 0) s_log[tid >> 5] = l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    *logdet += s_log[0] + (G > 32 ? s_log[1] : 0.0);
+    if (s_bad) *status = INLA_ERR_NOT_SPD;
   }
 }
 
+// FP64: scalar sweep; FP32: two-level sweep (12 block barriers instead of 192).
+template <typename R, int G>
+__device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
+  if (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
+  else sweep_tile_scalar<R, G>(sm, Pout, logdet, status);
+}
+
 // Pivot block 0 of an inversion (later pivots are inverted by the update
-// kernel of the previous step).  Pbuf holds two 32 x 32 slots per point.
-template <typename R>
-__global__ void __launch_bounds__(GTHREADS) gj_pivot_kernel(R *A, int64_t sA, int n_p, int K, R *Pbuf,
-                                                           double *logdet, int ld_stride, int *status,
-                                                           const int *active) {
+// kernel of the previous step).  Pbuf holds two G x G slots per point.
+template <typename R, int G>
+__global__ void __launch_bounds__(Sweep<G>::THREADS) gj_pivot_kernel(R *A, int64_t sA, int n_p, int K, R *Pbuf,
+                                                                    double *logdet, int ld_stride, int *status,
+                                                                    const int *active) {
+  using S = Sweep<G>;
   const int b = blockIdx.x;
   if (active && !active[b]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   R *sm = reinterpret_cast<R *>(smraw);
-  const R *src = A + b * sA + (int64_t)(K * GT) * n_p + K * GT;
-  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
-    const int i = e >> 5, j = e & 31;
-    if (j <= i) sm[i * GLD + j] = src[(int64_t)i * n_p + j];
+  const R *src = A + b * sA + (int64_t)(K * G) * n_p + K * G;
+  for (int e = threadIdx.x; e < G * G; e += S::THREADS) {
+    const int i = e >> S::SHIFT, j = e & (G - 1);
+    if (j <= i) sm[i * S::LD + j] = src[(int64_t)i * n_p + j];
   }
   __syncthreads();
-  sweep_tile(sm, Pbuf + ((int64_t)b * 2 + (K & 1)) * GT * GT, logdet + (int64_t)b * ld_stride, status + b);
+  sweep_tile<R, G>(sm, Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G, logdet + (int64_t)b * ld_stride, status + b);
 }
 
 // C_I = A_IK P for every row tile I != K; the old A_IK is kept in Obuf.
-template <typename R>
-__global__ void __launch_bounds__(GTHREADS) gj_panel_kernel(const R *A, int64_t sA, int n_p, int K,
-                                                           const R *Pbuf, R *Cbuf, R *Obuf,
-                                                           int64_t sCO, const int *active) {
+template <typename R, int G>
+__global__ void __launch_bounds__(Sweep<G>::THREADS) gj_panel_kernel(const R *A, int64_t sA, int n_p, int K,
+                                                                    const R *Pbuf, R *Cbuf, R *Obuf,
+                                                                    int64_t sCO, const int *active) {
+  using S = Sweep<G>;
   const int I = blockIdx.x, b = blockIdx.y;
   if (I == K || (active && !active[b])) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  R *Os = reinterpret_cast<R *>(smraw);   // [32][33]  O[r][k]
-  R *Ps = Os + GT * GLD;                  // [32][33]  P[k][c]
+  R *Os = reinterpret_cast<R *>(smraw);   // [G][LD]  O[r][k]
+  R *Ps = Os + G * S::LD;                 // [G][LD]  P[k][c]
   const R *Ab = A + b * sA;
   if (I > K) {
-    const R *src = Ab + (int64_t)(I * GT) * n_p + K * GT;
-    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
-      const int r = e >> 5, c = e & 31;
-      Os[r * GLD + c] = src[(int64_t)r * n_p + c];
+    const R *src = Ab + (int64_t)(I * G) * n_p + K * G;
+    for (int e = threadIdx.x; e < G * G; e += S::THREADS) {
+      const int r = e >> S::SHIFT, c = e & (G - 1);
+      Os[r * S::LD + c] = src[(int64_t)r * n_p + c];
     }
   } else {  // upper tile (I, K) = transpose of the stored lower tile (K, I)
-    const R *src = Ab + (int64_t)(K * GT) * n_p + I * GT;
-    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
-      const int c = e >> 5, r = e & 31;
-      Os[r * GLD + c] = src[(int64_t)c * n_p + r];
+    const R *src = Ab + (int64_t)(K * G) * n_p + I * G;
+    for (int e = threadIdx.x; e < G * G; e += S::THREADS) {
+      const int c = e >> S::SHIFT, r = e & (G - 1);
+      Os[r * S::LD + c] = src[(int64_t)c * n_p + r];
     }
   }
-  const R *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * GT * GT;
-  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) Ps[(e >> 5) * GLD + (e & 31)] = Pb[e];
+  const R *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G;
+  for (int e = threadIdx.x; e < G * G; e += S::THREADS) Ps[(e >> S::SHIFT) * S::LD + (e & (G - 1))] = Pb[e];
   __syncthreads();
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;   // rows ty + 16 i, cols tx + 8 j
-  R acc[2][4] = {};
+  const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;   // rows ty + 16 i, cols tx + TX j
+  R acc[S::MI][4] = {};
 #pragma unroll 8
-  for (int k = 0; k < GT; ++k) {
-    R av[2], bv[4];
+  for (int k = 0; k < G; ++k) {
+    R av[S::MI], bv[4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) av[i] = Os[(ty + 16 * i) * GLD + k];
+    for (int i = 0; i < S::MI; ++i) av[i] = Os[(ty + 16 * i) * S::LD + k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bv[j] = Ps[k * GLD + tx + 8 * j];
+    for (int j = 0; j < 4; ++j) bv[j] = Ps[k * S::LD + tx + S::TX * j];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < S::MI; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
-  R *Cb = Cbuf + b * sCO + (int64_t)(I * GT) * GT;
-  R *Ob = Obuf + b * sCO + (int64_t)(I * GT) * GT;
+  R *Cb = Cbuf + b * sCO + (int64_t)(I * G) * G;
+  R *Ob = Obuf + b * sCO + (int64_t)(I * G) * G;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < S::MI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) Cb[(ty + 16 * i) * GT + tx + 8 * j] = acc[i][j];
-  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) Ob[e] = Os[(e >> 5) * GLD + (e & 31)];
+    for (int j = 0; j < 4; ++j) Cb[(ty + 16 * i) * G + tx + S::TX * j] = acc[i][j];
+  for (int e = threadIdx.x; e < G * G; e += S::THREADS) Ob[e] = Os[(e >> S::SHIFT) * S::LD + (e & (G - 1))];
 }
 
-// Rank-32 update of every lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K;
+// Rank-G update of every lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K;
 // the pivot row/column become C (resp. C^T) and the pivot block -P.  With
 // lookahead (K + 1 < nt) block 0 takes tile (K+1, K+1) and, once updated,
 // inverts it as the next pivot (slot (K+1)&1 of Pbuf), so no separate pivot
 // launch sits on the critical path.
-template <typename R>
-__global__ void __launch_bounds__(GTHREADS) gj_update_kernel(R *A, int64_t sA, int n_p, int K, int nt,
-                                                            R *Pbuf, const R *Cbuf, const R *Obuf,
-                                                            int64_t sCO, double *logdet, int ld_stride, int *status,
-                                                            const int *active) {
+template <typename R, int G>
+__global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int64_t sA, int n_p, int K, int nt,
+                                                                     R *Pbuf, const R *Cbuf, const R *Obuf,
+                                                                     int64_t sCO, double *logdet, int ld_stride,
+                                                                     int *status, const int *active) {
+  using S = Sweep<G>;
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const bool look = K + 1 < nt;
@@ -211,69 +346,71 @@ __global__ void __launch_bounds__(GTHREADS) gj_update_kernel(R *A, int64_t sA, i
   } else {
     tri_index(blockIdx.x, I, J);
   }
-  R *dst = A + b * sA + (int64_t)(I * GT) * n_p + J * GT;
+  R *dst = A + b * sA + (int64_t)(I * G) * n_p + J * G;
   const R *Cb = Cbuf + b * sCO;
   if (I == K && J == K) {
-    const R *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * GT * GT;
-    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) dst[(int64_t)(e >> 5) * n_p + (e & 31)] = -Pb[e];
+    const R *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G;
+    for (int e = threadIdx.x; e < G * G; e += S::THREADS)
+      dst[(int64_t)(e >> S::SHIFT) * n_p + (e & (G - 1))] = -Pb[e];
     return;
   }
   if (J == K) {  // tile (I, K), I > K
-    const R *src = Cb + (int64_t)(I * GT) * GT;
-    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) dst[(int64_t)(e >> 5) * n_p + (e & 31)] = src[e];
+    const R *src = Cb + (int64_t)(I * G) * G;
+    for (int e = threadIdx.x; e < G * G; e += S::THREADS)
+      dst[(int64_t)(e >> S::SHIFT) * n_p + (e & (G - 1))] = src[e];
     return;
   }
   if (I == K) {  // tile (K, J), J < K: transpose of C_J
-    const R *src = Cb + (int64_t)(J * GT) * GT;
-    for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
-      const int c = e >> 5, r = e & 31;
-      dst[(int64_t)r * n_p + c] = src[c * GT + r];
+    const R *src = Cb + (int64_t)(J * G) * G;
+    for (int e = threadIdx.x; e < G * G; e += S::THREADS) {
+      const int c = e >> S::SHIFT, r = e & (G - 1);
+      dst[(int64_t)r * n_p + c] = src[c * G + r];
     }
     return;
   }
   extern __shared__ __align__(16) unsigned char smraw[];
-  R *Cs = reinterpret_cast<R *>(smraw);   // [32][33]  C_I[r][k]
-  R *Os = Cs + GT * GLD;                  // [32][33]  O_J[c][k]
+  R *Cs = reinterpret_cast<R *>(smraw);   // [G][LD]  C_I[r][k]
+  R *Os = Cs + G * S::LD;                 // [G][LD]  O_J[c][k]
   R *sm = Cs;                             // the fused pivot sweep's workspace
-  const R *ci = Cb + (int64_t)(I * GT) * GT;
-  const R *oj = Obuf + b * sCO + (int64_t)(J * GT) * GT;
-  for (int e = threadIdx.x; e < GT * GT; e += GTHREADS) {
-    Cs[(e >> 5) * GLD + (e & 31)] = ci[e];
-    Os[(e >> 5) * GLD + (e & 31)] = oj[e];
+  const R *ci = Cb + (int64_t)(I * G) * G;
+  const R *oj = Obuf + b * sCO + (int64_t)(J * G) * G;
+  for (int e = threadIdx.x; e < G * G; e += S::THREADS) {
+    Cs[(e >> S::SHIFT) * S::LD + (e & (G - 1))] = ci[e];
+    Os[(e >> S::SHIFT) * S::LD + (e & (G - 1))] = oj[e];
   }
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
-  R acc[2][4];   // starts at A_IJ; each step subtracts with one FMA
+  const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
+  R acc[S::MI][4];   // starts at A_IJ; each step subtracts with one FMA
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < S::MI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = dst[(int64_t)(ty + 16 * i) * n_p + tx + 8 * j];
+    for (int j = 0; j < 4; ++j) acc[i][j] = dst[(int64_t)(ty + 16 * i) * n_p + tx + S::TX * j];
   __syncthreads();
 #pragma unroll 8
-  for (int k = 0; k < GT; ++k) {
-    R av[2], bv[4];
+  for (int k = 0; k < G; ++k) {
+    R av[S::MI], bv[4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) av[i] = -Cs[(ty + 16 * i) * GLD + k];
+    for (int i = 0; i < S::MI; ++i) av[i] = -Cs[(ty + 16 * i) * S::LD + k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bv[j] = Os[(tx + 8 * j) * GLD + k];
+    for (int j = 0; j < 4; ++j) bv[j] = Os[(tx + S::TX * j) * S::LD + k];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < S::MI; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
   const bool next_pivot = look && I == K + 1 && J == K + 1;
   if (next_pivot) __syncthreads();   // Cs/Os are reused as the sweep's workspace
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < S::MI; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int r = ty + 16 * i, c = tx + 8 * j;
+      const int r = ty + 16 * i, c = tx + S::TX * j;
       dst[(int64_t)r * n_p + c] = acc[i][j];
-      if (next_pivot && c <= r) sm[r * GLD + c] = acc[i][j];
+      if (next_pivot && c <= r) sm[r * S::LD + c] = acc[i][j];
     }
   if (next_pivot) {
     __syncthreads();
-    sweep_tile(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * GT * GT, logdet + (int64_t)b * ld_stride,
-               status + b);
+    sweep_tile<R, G>(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * G * G, logdet + (int64_t)b * ld_stride,
+                     status + b);
   }
 }
 
@@ -363,22 +500,149 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(int n, const R *A, int64_t
     }
 }
 
+// FP32 C = alpha A B + beta C0 with 128 x 128 tiles of C (n a multiple of 128):
+// 256 threads, each owning an 8 x 8 block of outputs (rows ty*4+{0..3} and
+// 64+ty*4+{0..3}, likewise for columns), operands staged through shared memory
+// in 16-deep k slabs read as float4; the next slab is prefetched into
+// registers while the current one is multiplied.
+constexpr int G128 = 128, KC = 16, APAD = 4;
+__global__ void __launch_bounds__(256, 2) gemm128_f32_kernel(int n, const float *A, int64_t sA, const float *B,
+                                                         int64_t sB, float *C, int64_t sC, float alpha,
+                                                         const float *C0, int64_t sC0, float beta, int lower_only,
+                                                         const int *active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int nt = n / G128;
+  int I, J;
+  if (lower_only) tri_index(blockIdx.x, I, J);
+  else { I = blockIdx.x / nt; J = blockIdx.x % nt; }
+  __shared__ __align__(16) float As[KC][G128 + APAD];   // A transposed: As[k][row]
+  __shared__ __align__(16) float Bs[KC][G128];          // Bs[k][col]
+  const float *Ab = A + b * sA + (int64_t)(I * G128) * n;
+  const float *Bb = B + b * sB + J * G128;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float4 ra[2], rb[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int r = (tid >> 2) + 64 * q, c4 = tid & 3;
+      ra[q] = *reinterpret_cast<const float4 *>(Ab + (int64_t)r * n + k0 + c4 * 4);
+      const int kk = (tid >> 5) + 8 * q, cc = tid & 31;
+      rb[q] = *reinterpret_cast<const float4 *>(Bb + (int64_t)(k0 + kk) * n + cc * 4);
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int r = (tid >> 2) + 64 * q, c4 = tid & 3;
+      As[c4 * 4 + 0][r] = ra[q].x;
+      As[c4 * 4 + 1][r] = ra[q].y;
+      As[c4 * 4 + 2][r] = ra[q].z;
+      As[c4 * 4 + 3][r] = ra[q].w;
+      const int kk = (tid >> 5) + 8 * q, cc = tid & 31;
+      *reinterpret_cast<float4 *>(&Bs[kk][cc * 4]) = rb[q];
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < n; k0 += KC) {
+    __syncthreads();
+    store();
+    __syncthreads();
+    if (k0 + KC < n) load(k0 + KC);
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[k][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+  }
+  float *Cb = C + b * sC + (int64_t)(I * G128) * n + J * G128;
+  const float *C0b = C0 ? C0 + b * sC0 + (int64_t)(I * G128) * n + J * G128 : nullptr;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = h * 64 + tx * 4;
+      float4 v = make_float4(alpha * acc[i][4 * h + 0], alpha * acc[i][4 * h + 1], alpha * acc[i][4 * h + 2],
+                             alpha * acc[i][4 * h + 3]);
+      if (C0b) {
+        const float4 z = *reinterpret_cast<const float4 *>(C0b + (int64_t)r * n + c);
+        v.x += beta * z.x;
+        v.y += beta * z.y;
+        v.z += beta * z.z;
+        v.w += beta * z.w;
+      }
+      *reinterpret_cast<float4 *>(Cb + (int64_t)r * n + c) = v;
+    }
+  }
+}
+
 template <typename R>
 constexpr size_t smem_gemm() { return 2 * T * LDS * sizeof(R); }
-template <typename R>
+template <typename R, int G>
 constexpr size_t smem_update() {
-  return 2 * GT * GLD * sizeof(R) > SWEEP_SMEM_DOUBLES * sizeof(R) ? 2 * GT * GLD * sizeof(R)
-                                                                     : SWEEP_SMEM_DOUBLES * sizeof(R);
+  return (2 * G * Sweep<G>::LD > Sweep<G>::SMEM_ELEMS ? 2 * G * Sweep<G>::LD : Sweep<G>::SMEM_ELEMS) * sizeof(R);
 }
-constexpr size_t SMEM_PIV = SWEEP_SMEM_DOUBLES * sizeof(double);
+template <typename R, int G>
+constexpr size_t smem_pivot() { return Sweep<G>::SMEM_ELEMS * sizeof(R); }
 
 template <typename R>
 void ensure_attrs() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(gemm_nn_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gemm<R>());
-  cudaFuncSetAttribute(gj_pivot_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_PIV);
   done = true;
+}
+
+// Block sweep inversion with G x G pivots (see the kernels above).
+template <typename R, int G>
+void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet_out,
+                 int logdet_slot_stride) {
+  using S = Sweep<G>;
+  const int n_p = M.n_p, nt = n_p / G, P = W.P;
+  const int ntri = nt * (nt + 1) / 2;
+  const int64_t sCO = (int64_t)n_p * G;
+  const int tnt = n_p / T, tntri = tnt * (tnt + 1) / 2;
+  R *Pb = reinterpret_cast<R *>(W.gjP);
+  R *Cb = reinterpret_cast<R *>(W.gjC);
+  R *Ob = reinterpret_cast<R *>(W.gjO);
+  const double unit = (double)G * G * G / (64.0 * 64.0 * 64.0);   // one tile product in 64^3 units
+  for (int K = 0; K < nt; ++K) {
+    if (K == 0) {
+      L.start(KID_GJ_PIVOT, (double)P);
+      gj_pivot_kernel<R, G><<<P, S::THREADS, smem_pivot<R, G>(), L.st>>>(A, strideA, n_p, K, Pb, logdet_out,
+                                                                          logdet_slot_stride, W.status, W.active);
+      L.stop();
+      L.tick();
+    }
+    if (nt > 1) {
+      L.start(KID_GJ_PANEL, (double)P * (nt - 1) * unit);
+      gj_panel_kernel<R, G><<<dim3(nt, P), S::THREADS, 2 * G * S::LD * sizeof(R), L.st>>>(
+          A, strideA, n_p, K, Pb, Cb, Ob, sCO, W.active);
+      L.stop();
+      L.tick();
+    }
+    L.start(KID_GJ_UPDATE, (double)P * (ntri - nt) * unit);
+    gj_update_kernel<R, G><<<dim3(ntri, P), S::THREADS, smem_update<R, G>(), L.st>>>(
+        A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride, W.status, W.active);
+    L.stop();
+    L.tick();
+  }
+  gj_finalize_kernel<R><<<dim3(tntri, P), 256, 0, L.st>>>(A, strideA, n_p, W.active);
+  L.tick();
 }
 
 }  // namespace
@@ -388,47 +652,32 @@ void dense_prepare() {
   ensure_attrs<float>();
 }
 
+// FP64: 32-wide pivots keep the serial pivot sweep short on the slow FP64
+// pipe; FP32: 64-wide pivots give each block 4x the work.
 template <typename R>
 void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet_out,
                int logdet_slot_stride) {
   ensure_attrs<R>();
-  const int n_p = M.n_p, nt = n_p / GT, P = W.P;
-  const int ntri = nt * (nt + 1) / 2;
-  const int64_t sCO = (int64_t)n_p * GT;
-  const int tnt = n_p / T, tntri = tnt * (tnt + 1) / 2;
-  R *Pb = reinterpret_cast<R *>(W.gjP);
-  R *Cb = reinterpret_cast<R *>(W.gjC);
-  R *Ob = reinterpret_cast<R *>(W.gjO);
-  for (int K = 0; K < nt; ++K) {
-    if (K == 0) {
-      L.start(KID_GJ_PIVOT, (double)P);
-      gj_pivot_kernel<R><<<P, GTHREADS, SMEM_PIV, L.st>>>(A, strideA, n_p, K, Pb, logdet_out, logdet_slot_stride,
-                                                           W.status, W.active);
-      L.stop();
-      L.tick();
-    }
-    if (nt > 1) {
-      L.start(KID_GJ_PANEL, (double)P * (nt - 1) / 8.0);
-      gj_panel_kernel<R><<<dim3(nt, P), GTHREADS, 2 * GT * GLD * sizeof(R), L.st>>>(A, strideA, n_p, K, Pb, Cb, Ob,
-                                                                                   sCO, W.active);
-      L.stop();
-      L.tick();
-    }
-    // units: 64 x 64 x 64 tile products (2 * 64^3 flops); a 32-tile update is 1/8 of one
-    L.start(KID_GJ_UPDATE, (double)P * (ntri - nt) / 8.0);
-    gj_update_kernel<R><<<dim3(ntri, P), GTHREADS, smem_update<R>(), L.st>>>(
-        A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride, W.status, W.active);
-    L.stop();
-    L.tick();
-  }
-  gj_finalize_kernel<R><<<dim3(tntri, P), 256, 0, L.st>>>(A, strideA, n_p, W.active);
-  L.tick();
+  if (sizeof(R) == 4) gj_invert_g<R, 64>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
+  else gj_invert_g<R, 32>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
 }
 
 template <typename R>
 void gemm_nn(Launch &L, int P, int n, const R *A, int64_t sA, const R *B, int64_t sB, R *C, int64_t sC, R alpha,
              const R *C0, int64_t sC0, R beta, bool lower_only, const int *active) {
   ensure_attrs<R>();
+  if (sizeof(R) == 4 && n % G128 == 0) {
+    const int nt = n / G128;
+    const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
+    L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
+    gemm128_f32_kernel<<<dim3(tiles, P), 256, 0, L.st>>>(
+        n, reinterpret_cast<const float *>(A), sA, reinterpret_cast<const float *>(B), sB,
+        reinterpret_cast<float *>(C), sC, (float)alpha, reinterpret_cast<const float *>(C0), sC0, (float)beta,
+        lower_only ? 1 : 0, active);
+    L.stop();
+    L.tick();
+    return;
+  }
   const int nt = n / T;
   const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
   // units: 64 x 64 x 64 tile products (2 * 64^3 flops each)

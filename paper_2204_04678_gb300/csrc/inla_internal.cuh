@@ -45,6 +45,7 @@ struct DevModel {
   int n_t, n_s, n_b, n_p, lik, nnz;
   int max_mt;                    // largest number of observations in one time block
   int pbw;                       // bandwidth of the pattern: max |column - row|
+  int pmax;                      // longest pattern row
   int64_t m, n, nv;              // nv = n_t*n_p + n_b (padded latent length)
   const int *prow, *pcol;        // union pattern, CSR [n_s+1], [nnz]
   const int *prow_of;            // [nnz] row of each pattern entry
