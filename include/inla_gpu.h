@@ -196,6 +196,22 @@ int inla_eval_batch_static(inla_model *model, int B, const double *theta_dev, co
 int inla_eval_batch_host(inla_model *model, int B, const double *theta, const inla_eval_opts *opts,
                          const inla_eval_out_host *out);
 
+/* Tile autotuner (the project's own; no counterpart in the paper).  Times
+ * full evaluations of this batch (theta_dev: DEVICE [B][4], opts as for
+ * inla_eval_batch) for each candidate block-tile shape of the precision in
+ * opts -- the sweep's pivot/tile width (32 or 64) and, in INLA_MIXED, the
+ * FP32 GEMM tile (64 or 128) -- keeps the fastest in the model for later
+ * calls, and writes {FP64 sweep width, FP32 sweep width, FP32 GEMM tile} to
+ * choice[3] (may be NULL).  Synchronous; allocates and frees its own trial
+ * output buffers; drops captured graphs of the model.  Results of every
+ * candidate agree to rounding (all are the same algorithm). */
+int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts, int32_t *choice);
+
+/* Set the tile shapes explicitly (e.g. a choice saved from inla_autotune):
+ * sweep widths 32 or 64 for FP64 and FP32 blocks, FP32 GEMM tile 64 or 128.
+ * Errors: INLA_ERR_ARG for other values. */
+int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_fp32);
+
 /* Latent dimension n = n_t n_s + n_b of a model. */
 int64_t inla_model_latent_dim(const inla_model *model);
 

@@ -95,6 +95,18 @@ class Model:
         C.check(self.lib.inla_workspace_bytes(self.handle, int(B), byref(o), byref(out)))
         return out.value
 
+    def autotune(self, theta, grad="none", precision="fp64", **kw):
+        """Pick the fastest block-tile shapes for this batch; returns the chosen
+        (FP64 sweep width, FP32 sweep width, FP32 GEMM tile)."""
+        theta = theta.contiguous()
+        o = make_opts(grad=grad, precision=precision, **kw)
+        ch = (ctypes.c_int32 * 3)()
+        C.check(self.lib.inla_autotune(self.handle, int(theta.shape[0]), c_void_p(theta.data_ptr()), byref(o), ch))
+        return tuple(ch)
+
+    def set_tiles(self, sweep_fp64=32, sweep_fp32=64, gemm_fp32=128):
+        C.check(self.lib.inla_set_tiles(self.handle, int(sweep_fp64), int(sweep_fp32), int(gemm_fp32)))
+
     def last_launch_count(self):
         return int(self.lib.inla_last_launch_count(self.handle))
 

@@ -71,6 +71,8 @@ SIGNATURES = {
                                        c_void_p]),
     "inla_eval_batch_host": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts),
                                      POINTER(inla_eval_out_host)]),
+    "inla_autotune": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts), POINTER(c_int32)]),
+    "inla_set_tiles": (c_int, [c_void_p, c_int, c_int, c_int]),
     "inla_model_latent_dim": (c_int64, [c_void_p]),
     "inla_last_launch_count": (c_int64, [c_void_p]),
     "inla_model_destroy": (None, [c_void_p]),

@@ -284,6 +284,9 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     int pmax = 0;
     for (int i = 0; i < n_s; ++i) pmax = std::max(pmax, prow[i + 1] - prow[i]);
     M.pmax = pmax;
+    M.sweep_g64 = 32;
+    M.sweep_g32 = 64;
+    M.gemm_t32 = 128;
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);
@@ -665,8 +668,9 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
     k_sparse_left<R>(L, M, W, T1, W.sMat, S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
     if (contractions && nxt) k_contract_offdiag<R>(L, M, W, t, slotO);
     if (M.n_b > 0) k_dinv_apply<R>(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
-    gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active);
-    gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active);
+    gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, M.gemm_t32);
+    gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active,
+               M.gemm_t32);
     mirror_lower<R>(L, W.P, M.n_p, SigC, W.sMat, W.active);
     k_contract_diag<R>(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
     if (poisson_q) k_poisson_qobs<R>(L, M, W, t);
@@ -1039,6 +1043,93 @@ int inla_eval_batch(inla_model *model, int B, const double *theta_dev, const inl
 int inla_eval_batch_static(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
                            const inla_eval_out *out, void *stream) {
   return guarded([&] { eval_static_impl(model, B, theta_dev, opts, out, static_cast<cudaStream_t>(stream)); });
+}
+
+int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_fp32) {
+  return guarded([&] {
+    if (!model) throw ApiError(INLA_ERR_ARG, "model is NULL");
+    if ((sweep_fp64 != 32 && sweep_fp64 != 64) || (sweep_fp32 != 32 && sweep_fp32 != 64) ||
+        (gemm_fp32 != 64 && gemm_fp32 != 128))
+      throw ApiError(INLA_ERR_ARG, "tile widths: sweep 32 or 64, FP32 GEMM 64 or 128");
+    CUDA_OK(cudaSetDevice(model->device));
+    CUDA_OK(cudaDeviceSynchronize());
+    model->M.sweep_g64 = sweep_fp64;
+    model->M.sweep_g32 = sweep_fp32;
+    model->M.gemm_t32 = gemm_fp32;
+    for (auto &g : model->graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.stage) cudaFree(g.stage);
+    }
+    model->graphs.clear();
+  });
+}
+
+int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts, int32_t *choice) {
+  return guarded([&] {
+    if (!model || !opts || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
+    CUDA_OK(cudaSetDevice(model->device));
+    DevModel &M = model->M;
+    const bool fp32 = opts->precision == INLA_MIXED;
+    const int64_t n = M.n;
+    // outputs of the trial evaluations (device, freed before returning)
+    void *buf = nullptr;
+    const size_t bytes = (size_t)B * (8 + 32 + 4 + 4 + 16 * n) + 4096;
+    CUDA_OK(cudaMalloc(&buf, bytes));
+    char *p = static_cast<char *>(buf);
+    auto take = [&](size_t b) { char *r = p; p += rup(b, 256); return r; };
+    inla_eval_out out{};
+    out.f_dev = reinterpret_cast<double *>(take(8 * B));
+    out.grad_dev = reinterpret_cast<double *>(take(32 * B));
+    out.status_dev = reinterpret_cast<int *>(take(4 * B));
+    out.newton_iters_dev = reinterpret_cast<int *>(take(4 * B));
+    out.x_mode_dev = reinterpret_cast<double *>(take(8 * n * B));
+    out.marg_var_dev = reinterpret_cast<double *>(take(8 * n * B));
+    inla_eval_opts o = *opts;
+    o.use_graph = 0;
+    struct Cand { int g, t; };
+    std::vector<Cand> cands;
+    if (fp32) cands = {{64, 128}, {32, 128}, {64, 64}, {32, 64}};
+    else cands = {{32, M.gemm_t32}, {64, M.gemm_t32}};
+    cudaEvent_t e0, e1;
+    CUDA_OK(cudaEventCreate(&e0));
+    CUDA_OK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand bc = cands[0];
+    try {
+      for (const Cand &c : cands) {
+        if (fp32) { M.sweep_g32 = c.g; M.gemm_t32 = c.t; }
+        else M.sweep_g64 = c.g;
+        eval_impl(model, B, theta_dev, &o, &out, model->stream);   // warm-up (allocations, caches)
+        CUDA_OK(cudaEventRecord(e0, model->stream));
+        eval_impl(model, B, theta_dev, &o, &out, model->stream);
+        CUDA_OK(cudaEventRecord(e1, model->stream));
+        CUDA_OK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bc = c; }
+      }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaFree(buf);
+      throw;
+    }
+    if (fp32) { M.sweep_g32 = bc.g; M.gemm_t32 = bc.t; }
+    else M.sweep_g64 = bc.g;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_OK(cudaFree(buf));
+    for (auto &g : model->graphs) {          // graphs captured with other tiles are stale
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.stage) cudaFree(g.stage);
+    }
+    model->graphs.clear();
+    if (choice) {
+      choice[0] = M.sweep_g64;
+      choice[1] = M.sweep_g32;
+      choice[2] = M.gemm_t32;
+    }
+  });
 }
 
 int inla_eval_batch_host(inla_model *model, int B, const double *theta, const inla_eval_opts *opts,

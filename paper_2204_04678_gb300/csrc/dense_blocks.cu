@@ -604,6 +604,12 @@ void ensure_attrs() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(gemm_nn_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gemm<R>());
+  // 64-wide FP64 tiles need more than the default 48 KB of dynamic shared memory
+  cudaFuncSetAttribute(gj_update_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_update<R, 64>());
+  cudaFuncSetAttribute(gj_panel_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(2 * 64 * Sweep<64>::LD * sizeof(R)));
+  cudaFuncSetAttribute(gj_pivot_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pivot<R, 64>());
   done = true;
 }
 
@@ -652,21 +658,23 @@ void dense_prepare() {
   ensure_attrs<float>();
 }
 
-// FP64: 32-wide pivots keep the serial pivot sweep short on the slow FP64
-// pipe; FP32: 64-wide pivots give each block 4x the work.
+// Tile width per precision from the model (defaults: 32 for FP64, where short
+// pivot sweeps matter on the slow FP64 pipe; 64 for FP32, which gives each
+// block 4x the work); inla_autotune may change them.
 template <typename R>
 void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet_out,
                int logdet_slot_stride) {
   ensure_attrs<R>();
-  if (sizeof(R) == 4) gj_invert_g<R, 64>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
+  const int g = sizeof(R) == 4 ? M.sweep_g32 : M.sweep_g64;
+  if (g == 64) gj_invert_g<R, 64>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
   else gj_invert_g<R, 32>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
 }
 
 template <typename R>
 void gemm_nn(Launch &L, int P, int n, const R *A, int64_t sA, const R *B, int64_t sB, R *C, int64_t sC, R alpha,
-             const R *C0, int64_t sC0, R beta, bool lower_only, const int *active) {
+             const R *C0, int64_t sC0, R beta, bool lower_only, const int *active, int tile) {
   ensure_attrs<R>();
-  if (sizeof(R) == 4 && n % G128 == 0) {
+  if (sizeof(R) == 4 && tile == 128 && n % G128 == 0) {
     const int nt = n / G128;
     const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
     L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
@@ -698,9 +706,9 @@ void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active) 
 template void gj_invert<double>(Launch &, const DevModel &, const Work &, double *, int64_t, double *, int);
 template void gj_invert<float>(Launch &, const DevModel &, const Work &, float *, int64_t, double *, int);
 template void gemm_nn<double>(Launch &, int, int, const double *, int64_t, const double *, int64_t, double *, int64_t,
-                              double, const double *, int64_t, double, bool, const int *);
+                              double, const double *, int64_t, double, bool, const int *, int);
 template void gemm_nn<float>(Launch &, int, int, const float *, int64_t, const float *, int64_t, float *, int64_t,
-                             float, const float *, int64_t, float, bool, const int *);
+                             float, const float *, int64_t, float, bool, const int *, int);
 template void mirror_lower<double>(Launch &, int, int, double *, int64_t, const int *);
 template void mirror_lower<float>(Launch &, int, int, float *, int64_t, const int *);
 

@@ -46,6 +46,8 @@ struct DevModel {
   int max_mt;                    // largest number of observations in one time block
   int pbw;                       // bandwidth of the pattern: max |column - row|
   int pmax;                      // longest pattern row
+  int sweep_g64, sweep_g32;      // sweep tile width for FP64 / FP32 blocks (32 or 64; autotuned)
+  int gemm_t32;                  // FP32 GEMM tile (64 or 128; autotuned)
   int64_t m, n, nv;              // nv = n_t*n_p + n_b (padded latent length)
   const int *prow, *pcol;        // union pattern, CSR [n_s+1], [nnz]
   const int *prow_of;            // [nnz] row of each pattern entry
@@ -186,7 +188,7 @@ template <typename R>
 void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet, int ld_stride);
 template <typename R>
 void gemm_nn(Launch &L, int P, int n, const R *A, int64_t sA, const R *B, int64_t sB, R *C, int64_t sC, R alpha,
-             const R *C0, int64_t sC0, R beta, bool lower_only, const int *active);
+             const R *C0, int64_t sC0, R beta, bool lower_only, const int *active, int tile = 128);
 template <typename R>
 void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active);
 

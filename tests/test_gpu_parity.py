@@ -282,3 +282,28 @@ def test_cuda_graph_replay_matches_eager(pkg):
             for key in ("f", "grad", "x_mode", "marg_var", "status"):
                 if key in eager:
                     assert torch.equal(eager[key], graph[key]), (kw, k, key)
+
+
+def test_autotune_keeps_results(pkg):
+    mdl = build("g", 3, 10, 2, 500, "gaussian", seed=21)
+    th = thetas(mdl, 2, seed=8)
+    model = pkg.Model(mdl)
+    for prec, tol in (("fp64", RTOL_F), ("mixed", MIX_F)):
+        choice = model.autotune(cuda(th), grad="adjoint", precision=prec)
+        assert choice[0] in (32, 64) and choice[1] in (32, 64) and choice[2] in (64, 128)
+        r = model.eval(cuda(th), grad="adjoint", precision=prec)
+        torch.cuda.synchronize()
+        for b in range(th.shape[0]):
+            ref = bta.gaussian(mdl, th[b], want_grad=True)
+            assert abs(float(r["f"][b]) - ref["f"]) <= tol * abs(ref["f"])
+    # every tile shape is the same algorithm: results agree to rounding
+    for prec, tol in (("fp64", RTOL_F), ("mixed", MIX_F)):
+        outs = []
+        for tiles in ((32, 32, 64), (64, 64, 128)):
+            model.set_tiles(*tiles)
+            outs.append(model.eval(cuda(th), grad="adjoint", precision=prec))
+        torch.cuda.synchronize()
+        fa, fb = outs[0]["f"].cpu().numpy(), outs[1]["f"].cpu().numpy()
+        assert np.all(np.abs(fa - fb) <= tol * np.abs(fa))
+    with pytest.raises(pkg.capi.InlaError):
+        model.set_tiles(48, 64, 128)
