@@ -61,6 +61,11 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1, help="stencil centres per step (FD mode)")
+    ap.add_argument("--theta-iter", action="store_true",
+                    help="time theta-iterations (gradient + 16-point line search) in the FD/FP64 form and "
+                         "the adjoint/mixed form on the same workload, and run BFGS to the mode with both")
+    ap.add_argument("--no-bfgs", action="store_true", help="with --theta-iter: skip the runs to the mode")
+    ap.add_argument("--bfgs-iters", type=int, default=30, help="with --theta-iter: BFGS iteration limit")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--evals", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--nt-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -218,6 +223,90 @@ def config_dict(cfg, world, grad=None, precision=None, points=9):
             "l2": "working set (GBs of factor storage per step) exceeds L2; no flush"}
 
 
+# ------------------------------------------------------------------ theta-iterations
+
+def theta_iterations(args, local):
+    """One theta-iteration = the gradient at the current point plus one parallel
+    line search of 16 f-only points (Sec. 3.2).  FD form: the 9-point central-
+    difference stencil in FP64; adjoint form: one f + adjoint gradient.  Both
+    line searches are one batch each, in the form's precision."""
+    import numpy as np
+    import torch
+    import paper_2204_04678_gb300 as pkg
+    from paper_2204_04678_gb300 import capi, driver
+    from synth import config_model, line_points, theta_batch
+
+    pkg.build()
+    capi.load()
+    cfg = args.config
+    mdl = config_model(cfg)
+    model = pkg.Model(mdl, device=local)
+    stream = torch.cuda.current_stream()
+    centre = theta_batch(2, mdl)[0]          # theta_true + 0.1 N(0, I), the stencil centre of the workloads
+    ref = model.eval(torch.tensor(centre[None], dtype=torch.float64, device="cuda"), grad="adjoint")
+    g64 = ref["grad"][0].cpu().numpy()
+    pts = line_points(centre, -g64, 0.5)
+    c_t = torch.tensor(centre[None], dtype=torch.float64, device="cuda")
+    l_t = torch.tensor(pts, dtype=torch.float64, device="cuda")
+    forms = {"fd_fp64": ("fd", "fp64"), "adjoint_fp64": ("adjoint", "fp64"), "adjoint_mixed": ("adjoint", "mixed")}
+    res = {}
+    clocks = Clocks(local)
+    for name, (grad, prec) in forms.items():
+        def iteration():
+            a = model.eval(c_t, grad=grad, precision=prec)
+            b = model.eval(l_t, grad="none", precision=prec)
+            return a, b, model.last_launch_count()
+        for _ in range(max(args.warmup, 1)):
+            a, b, _ = iteration()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        e0.record(stream)
+        for _ in range(args.steps):
+            a, b, nl = iteration()
+            launches += nl
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / args.steps
+        assert int(a["status"].abs().sum()) + int(b["status"].abs().sum()) == 0, name
+        res[name] = {"theta_iterations_per_s": 1.0 / sec, "ms_per_iteration": 1e3 * sec,
+                     "f": np.concatenate([a["f"].cpu().numpy(), b["f"].cpu().numpy()]),
+                     "grad": a["grad"][0].cpu().numpy(), "gpu_launches_per_iteration": launches / args.steps}
+    clk = clocks.stop()
+    base = res["adjoint_fp64"]
+    for name, r in res.items():
+        r["max_rel_err_f_vs_fp64"] = float(np.max(np.abs(r["f"] - base["f"]) / np.abs(base["f"])))
+        r["max_rel_err_grad_vs_fp64_adjoint"] = float(np.max(np.abs(r["grad"] - base["grad"]))
+                                                      / np.max(np.abs(base["grad"])))
+    for r in res.values():
+        del r["f"], r["grad"]
+    # BFGS to the mode with each form (host driver over the same batched calls)
+    to_mode = {}
+    if not args.no_bfgs:
+        for name, (grad, prec) in forms.items():
+            fg, fb, _, _ = driver.model_evaluators(model, grad=grad, precision=prec)
+            t0 = time.perf_counter()
+            r = driver.bfgs(fg, fb, centre, max_iter=args.bfgs_iters, gtol=1e-2, ftol=1e-10)
+            sec = time.perf_counter() - t0
+            f64 = model.eval(torch.tensor(r["theta"][None], dtype=torch.float64, device="cuda"), grad="adjoint")
+            to_mode[name] = {"iterations": r["iterations"], "seconds": sec, "theta": r["theta"].tolist(),
+                             "f_fp64_at_end": float(f64["f"][0]),
+                             "max_abs_grad_fp64_at_end": float(f64["grad"][0].abs().max())}
+    fast, slow = res["adjoint_mixed"], res["fd_fp64"]
+    line = {"metric": "theta-iterations/s (gradient + 16-point line search)",
+            "value": fast["theta_iterations_per_s"], "unit": "theta-iterations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fast["ms_per_iteration"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": dict(config_dict(cfg, 1, "adjoint", "mixed", 17),
+                                                workload=CONFIG_WORKLOAD[cfg].split(";")[0]
+                                                + "; one step = gradient at the centre + 16 line-search points"),
+            "clocks": clk, "forms": res, "speedup_adjoint_mixed_over_fd_fp64":
+                fast["theta_iterations_per_s"] / slow["theta_iterations_per_s"],
+            "bfgs_to_mode": to_mode}
+    print(json.dumps(line))
+    model.close()
+
+
 # ------------------------------------------------------------------ our arm
 
 def main():
@@ -234,6 +323,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.theta_iter:
+        import torch
+        torch.cuda.set_device(local)
+        theta_iterations(args, local)
         return
 
     import numpy as np
