@@ -60,10 +60,12 @@ def parse():
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
-    ap.add_argument("--centres", type=int, default=1, help="stencil centres per step (FD mode)")
+    ap.add_argument("--centres", type=int, default=1,
+                    help="stencil centres per step (FD mode) / copies of the batch (adjoint mode); profiling only")
     ap.add_argument("--theta-iter", action="store_true",
                     help="time theta-iterations (gradient + 16-point line search) in the FD/FP64 form and "
                          "the adjoint/mixed form on the same workload, and run BFGS to the mode with both")
+    ap.add_argument("--no-errors", action="store_true", help="skip the mixed-vs-FP64 accuracy check")
     ap.add_argument("--no-bfgs", action="store_true", help="with --theta-iter: skip the runs to the mode")
     ap.add_argument("--bfgs-iters", type=int, default=30, help="with --theta-iter: BFGS iteration limit")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -223,6 +225,27 @@ def config_dict(cfg, world, grad=None, precision=None, points=9):
             "l2": "working set (GBs of factor storage per step) exceeds L2; no flush"}
 
 
+# ------------------------------------------------------------------ mixed-precision accuracy
+
+def mixed_errors(model, theta, grad):
+    """Relative errors of the mixed path against the FP64 path at the given points:
+    f (|df| / |f|), the gradient (max |dg| / max |g|), the mode (max |dx| / max |x|)
+    and the marginal variances (max |dv| / v)."""
+    import numpy as np
+    r = {}
+    for prec in ("fp64", "mixed"):
+        o = model.eval(theta, grad=grad, precision=prec, want_mode=True, want_marg_var=True)
+        r[prec] = {k: o[k].cpu().numpy() for k in ("f", "grad", "x_mode", "marg_var", "status")}
+    a, b = r["fp64"], r["mixed"]
+    if np.any(a["status"] != 0) or np.any(b["status"] != 0):
+        return {"error": "evaluation failed"}
+    return {"points": int(theta.shape[0]),
+            "f_rel": float(np.max(np.abs(b["f"] - a["f"]) / np.abs(a["f"]))),
+            "grad_rel": float(np.max(np.abs(b["grad"] - a["grad"])) / np.max(np.abs(a["grad"]))),
+            "x_rel": float(np.max(np.abs(b["x_mode"] - a["x_mode"])) / np.max(np.abs(a["x_mode"]))),
+            "var_rel": float(np.max(np.abs(b["marg_var"] - a["marg_var"]) / a["marg_var"]))}
+
+
 # ------------------------------------------------------------------ theta-iterations
 
 def theta_iterations(args, local):
@@ -254,8 +277,9 @@ def theta_iterations(args, local):
     for name, (grad, prec) in forms.items():
         def iteration():
             a = model.eval(c_t, grad=grad, precision=prec)
+            n = model.last_launch_count()
             b = model.eval(l_t, grad="none", precision=prec)
-            return a, b, model.last_launch_count()
+            return a, b, n + model.last_launch_count()
         for _ in range(max(args.warmup, 1)):
             a, b, _ = iteration()
         torch.cuda.synchronize()
@@ -367,6 +391,8 @@ def main():
     else:
         from synth import fd_stencil
         batch = fd_stencil(centre) if cfg in (1, 2) else theta_batch(cfg, mdl) + 0.01 * rank
+        if args.centres > 1:   # profiling case: the batch repeated around shifted centres
+            batch = np.concatenate([batch + 0.01 * k for k in range(args.centres)])
         theta = torch.tensor(batch, dtype=torch.float64, device="cuda")
         per_step = theta.shape[0]
         points = per_step
@@ -450,6 +476,12 @@ def main():
         e2e = {"value": world * per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * nb,
                "d2h_bytes_per_step": nb * (8 + 4 * 8 + 4 + 4)}
 
+    # accuracy of the mixed path against the FP64 path (which matches the oracle
+    # to 1e-10 on f): the first point of the batch, with marginal variances
+    errors = None
+    if prec == "mixed" and not args.no_errors:
+        errors = mixed_errors(model, theta[:1], grad)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -467,6 +499,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "f_evals_per_s": 9 * value if grad == "fd" else value,
                 "grad_mode": grad,
+                "errors_vs_fp64": errors,
                 "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32},
                 "kernels": {k: {"ms_sampled": v[0], "launches_sampled": v[1],
                                 "tflops": v[2] * flop_per_unit / (v[0] / 1e3) / 1e12 if v[0] else None}

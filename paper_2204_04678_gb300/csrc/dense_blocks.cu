@@ -20,6 +20,7 @@
 // In FP64 the kernels are bound by the FP64 pipe; all operand traffic is
 // staged through shared memory with conflict-free access (padded rows).
 #include <cmath>
+#include <type_traits>
 
 #include "inla_internal.cuh"
 
@@ -152,10 +153,11 @@ __device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) 
       if (ik && jk) w = sp[(i - K0) * (SB + 1) + (j - K0)];
       else if (jk) w = Cp[i * SB + (j - K0)];
       else if (ik) w = Cp[j * SB + (i - K0)];
-      else {
-        w = a[i * LD + j];
+      else {   // the rank-SB product is summed first and subtracted once
+        R u = R(0);
 #pragma unroll
-        for (int c = 0; c < SB; ++c) w = fma(-Cp[i * SB + c], Op[j * SB + c], w);
+        for (int c = 0; c < SB; ++c) u = fma(Cp[i * SB + c], Op[j * SB + c], u);
+        w = a[i * LD + j] - u;
       }
       a[i * LD + j] = w;
     }
@@ -379,11 +381,17 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
     Os[(e >> S::SHIFT) * S::LD + (e & (G - 1))] = oj[e];
   }
   const int tx = threadIdx.x % S::TX, ty = threadIdx.x / S::TX;
-  R acc[S::MI][4];   // starts at A_IJ; each step subtracts with one FMA
+  // FP64: the accumulator starts at A_IJ and each step subtracts with one FMA.
+  // FP32: the rank-G product is summed from zero and added to A_IJ once, so
+  // the tile takes one rounding per block step instead of G (a sequential
+  // FP32 accumulation loses about ten times more accuracy in log|D| and in
+  // the selected inverse at n_s ~ 1000).
+  constexpr bool kSumFirst = std::is_same<R, float>::value;
+  R acc[S::MI][4];
 #pragma unroll
   for (int i = 0; i < S::MI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = dst[(int64_t)(ty + 16 * i) * n_p + tx + S::TX * j];
+    for (int j = 0; j < 4; ++j) acc[i][j] = kSumFirst ? R(0) : dst[(int64_t)(ty + 16 * i) * n_p + tx + S::TX * j];
   __syncthreads();
 #pragma unroll 8
   for (int k = 0; k < G; ++k) {
@@ -404,6 +412,7 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = ty + 16 * i, c = tx + S::TX * j;
+      if (kSumFirst) acc[i][j] += dst[(int64_t)r * n_p + c];
       dst[(int64_t)r * n_p + c] = acc[i][j];
       if (next_pivot && c <= r) sm[r * S::LD + c] = acc[i][j];
     }

@@ -222,13 +222,13 @@ def test_config2_full_size_sampled(pkg):
 
 # ---------------------------------------------------------------- mixed precision
 # Dense blocks in FP32, pivots' log-determinants accumulated in FP64, the mode
-# refined with FP64 residuals.  f is held to 1e-6 relative; the refined mode to
-# the FP64 tolerance.  The adjoint gradient and the marginal variances are read
-# from FP32 selected-inverse blocks, whose entries carry ~1e-6 relative error
-# (inverse and products both rounded to 2^-24, amplified by the block condition
-# numbers); the data trace tau_y tr(Q_c^-1 A^T A) ~ m/2 then moves the gradient
-# by up to ~5e-5 of its largest component, and the variances by up to 1e-4.
-MIX_F, MIX_G, MIX_X, MIX_V = 1e-6, 5e-5, 1e-9, 1e-4
+# refined with FP64 residuals, and every FP32 block update summed before it is
+# added to the block (one rounding per block step).  Held to the stated error
+# budget of the mixed form: 1e-6 relative on f and 1e-5 on the gradient (of its
+# largest component); the refined mode to the FP64 tolerance.  The marginal
+# variances are read from FP32 selected-inverse blocks (entries ~1e-6 relative,
+# amplified by the block condition numbers): 5e-5.
+MIX_F, MIX_G, MIX_X, MIX_V = 1e-6, 1e-5, 1e-9, 5e-5
 
 
 @pytest.mark.parametrize("lik,n_t,nx,n_b,m", [("gaussian", 4, 10, 3, 600), ("gaussian", 6, 13, 2, 1500),
