@@ -59,6 +59,8 @@ def parse():
                          "workload's batch gets f and an adjoint gradient (default: the workload's own)")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
+    ap.add_argument("--gemm", default=None, choices=["cuda-core", "tensor"],
+                    help="FP32 selected-inversion GEMM: 128x128 FP32 FMA tiles or tcgen05 3xTF32")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1,
                     help="stencil centres per step (FD mode) / copies of the batch (adjoint mode); profiling only")
@@ -382,6 +384,8 @@ def main():
         mdl = config_model(cfg)
     centre = theta_batch(cfg, mdl)[0] + 0.01 * rank
     model = pkg.Model(mdl, device=local)
+    if args.gemm:
+        model.set_tiles(32, 64, capi.INLA_GEMM_TF32X3 if args.gemm == "tensor" else 128)
     stream = torch.cuda.current_stream()
     if args.grad == "fd":
         cen = centre[None, :] + 0.01 * np.arange(args.centres)[:, None]

@@ -60,6 +60,7 @@ typedef enum {
   INLA_ERR_OOM = 3,             /* device allocation failed                    */
   INLA_ERR_NOT_SPD = 4,         /* per point: Q or Q_c not positive definite   */
   INLA_ERR_NO_CONVERGENCE = 5,  /* per point: Newton iteration did not converge */
+  INLA_ERR_TIMEOUT = 6,         /* per point: a bounded device-side wait ran out */
   INLA_ERR_UNSUPPORTED = 7      /* option not available in this build          */
 } inla_status;
 
@@ -77,6 +78,12 @@ enum { INLA_PRIOR_KRONECKER = 0, INLA_PRIOR_BTA = 1 };
  * inputs, all vectors, reductions and traces stay FP64, and the mode is
  * refined with FP64 residuals r = b - Q_c x (three refinement steps). */
 enum { INLA_FP64 = 0, INLA_MIXED = 1 };
+/* FP32 GEMM of the mixed selected inversion (inla_set_tiles): 64 or 128 =
+ * FP32 FMA on the CUDA cores with 64 x 64 or 128 x 128 output tiles;
+ * INLA_GEMM_TF32X3 = 128 x 128 tiles on the tensor cores (tcgen05, kind::tf32)
+ * with the 3xTF32 split product, used where n_s rounded up to 64 is a
+ * multiple of 128 (elsewhere the 128 x 128 CUDA-core GEMM runs). */
+#define INLA_GEMM_TF32X3 3
 
 /* Model description.  Every pointer is a HOST pointer; the arrays are read
  * (and copied to the device) by inla_model_create and may be freed after it
@@ -200,7 +207,7 @@ int inla_eval_batch_host(inla_model *model, int B, const double *theta, const in
  * full evaluations of this batch (theta_dev: DEVICE [B][4], opts as for
  * inla_eval_batch) for each candidate block-tile shape of the precision in
  * opts -- the sweep's pivot/tile width (32 or 64) and, in INLA_MIXED, the
- * FP32 GEMM tile (64 or 128) -- keeps the fastest in the model for later
+ * FP32 GEMM (64, 128 or INLA_GEMM_TF32X3) -- keeps the fastest in the model for later
  * calls, and writes {FP64 sweep width, FP32 sweep width, FP32 GEMM tile} to
  * choice[3] (may be NULL).  Synchronous; allocates and frees its own trial
  * output buffers; drops captured graphs of the model.  Results of every
@@ -208,7 +215,8 @@ int inla_eval_batch_host(inla_model *model, int B, const double *theta, const in
 int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts, int32_t *choice);
 
 /* Set the tile shapes explicitly (e.g. a choice saved from inla_autotune):
- * sweep widths 32 or 64 for FP64 and FP32 blocks, FP32 GEMM tile 64 or 128.
+ * sweep widths 32 or 64 for FP64 and FP32 blocks; FP32 GEMM 64, 128 or
+ * INLA_GEMM_TF32X3.  A new model starts at (32, 64, INLA_GEMM_TF32X3).
  * Errors: INLA_ERR_ARG for other values. */
 int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_fp32);
 
@@ -229,6 +237,19 @@ int64_t inla_last_launch_count(const inla_model *model);
  *   kernel 2: pivot-block inversion        kernel 3: pivot-panel product */
 int inla_profile_enable(inla_model *model, int enable);
 int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *launches, double *units);
+
+/* C[b] = X[b] Y[b]^T for b < batch: n x n row-major FP32 matrices (DEVICE,
+ * contiguous one after another, 16-byte aligned; n a positive multiple of
+ * 128), on the tensor cores with the 3xTF32 split product: each FP32 value
+ * x = x_hi + x_lo with x_hi = tf32(x), x_lo = tf32(x - x_hi) (round to
+ * nearest, ties away), and X Y^T ~ X_lo Y_hi^T + X_hi Y_lo^T + X_hi Y_hi^T
+ * accumulated in FP32 -- the product the mixed selected inversion uses
+ * (Eq. sel_inv_cov on n_s x n_s blocks).  status (DEVICE [batch], may be
+ * NULL) receives INLA_OK, or INLA_ERR_TIMEOUT where a bounded wait of the
+ * kernel ran out (C is then not written).  Asynchronous on `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Errors: INLA_ERR_ARG
+ * (sizes, NULL or unaligned pointers), INLA_ERR_CUDA. */
+int inla_gemm_tf32x3(int n, int batch, const float *X, const float *Y, float *C, int32_t *status, void *stream);
 
 /* Free every device resource of the model.  NULL is allowed. */
 void inla_model_destroy(inla_model *model);

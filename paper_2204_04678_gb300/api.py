@@ -232,6 +232,27 @@ def measure_fp32_peak(device=0):
     return v.value
 
 
+def gemm_tf32x3(X, Y, stream=None):
+    """C[b] = X[b] @ Y[b].T on the tensor cores (3xTF32 split product) for CUDA
+    float32 tensors X, Y of shape [batch, n, n] (or [n, n]), n a multiple of 128.
+    Returns (C, status) with status [batch] int32 (0, or ERR_TIMEOUT)."""
+    import torch
+    lib = C.load()
+    squeeze = X.dim() == 2
+    X = (X[None] if squeeze else X).contiguous()
+    Y = (Y[None] if squeeze else Y).contiguous()
+    if X.dtype != torch.float32 or Y.dtype != torch.float32 or not X.is_cuda or X.shape != Y.shape:
+        raise TypeError("X and Y must be CUDA float32 tensors of the same shape")
+    batch, n = X.shape[0], X.shape[1]
+    Cm = torch.empty_like(X)
+    status = torch.empty(batch, dtype=torch.int32, device=X.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device)
+    C.check(lib.inla_gemm_tf32x3(int(n), int(batch), c_void_p(X.data_ptr()), c_void_p(Y.data_ptr()),
+                                 c_void_p(Cm.data_ptr()), c_void_p(status.data_ptr()), c_void_p(stream.cuda_stream)))
+    return (Cm[0] if squeeze else Cm), status
+
+
 def _make_function():
     import torch
 

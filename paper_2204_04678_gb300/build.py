@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libinla_gpu.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "probe.cu"]
+SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "probe.cu", "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -15,6 +15,7 @@ INLA_ERR_CUDA = 2
 INLA_ERR_OOM = 3
 INLA_ERR_NOT_SPD = 4
 INLA_ERR_NO_CONVERGENCE = 5
+INLA_ERR_TIMEOUT = 6
 INLA_ERR_UNSUPPORTED = 7
 INLA_LIK_GAUSSIAN = 0
 INLA_LIK_POISSON = 1
@@ -25,6 +26,7 @@ INLA_PRIOR_KRONECKER = 0
 INLA_PRIOR_BTA = 1
 INLA_FP64 = 0
 INLA_MIXED = 1
+INLA_GEMM_TF32X3 = 3
 KERNEL_GJ_UPDATE = 0
 KERNEL_GEMM = 1
 KERNEL_GJ_PIVOT = 2
@@ -33,7 +35,7 @@ KERNEL_GJ_PANEL = 3
 STATIC_SCRATCH_BYTES = 64 << 20
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_SPD",
-                5: "ERR_NO_CONVERGENCE", 7: "ERR_UNSUPPORTED"}
+                5: "ERR_NO_CONVERGENCE", 6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
 
 
 class inla_model_desc(ctypes.Structure):
@@ -79,6 +81,7 @@ SIGNATURES = {
     "inla_last_error": (c_char_p, []),
     "inla_measure_fp64_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
     "inla_measure_fp32_peak": (c_int, [c_int, POINTER(c_double)]),
+    "inla_gemm_tf32x3": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "inla_profile_enable": (c_int, [c_void_p, c_int]),
     "inla_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]),
 }

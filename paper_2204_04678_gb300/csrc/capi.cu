@@ -286,7 +286,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     M.pmax = pmax;
     M.sweep_g64 = 32;
     M.sweep_g32 = 64;
-    M.gemm_t32 = 128;
+    M.gemm_t32 = INLA_GEMM_TF32X3;   // tensor cores where n_p % 128 == 0, else 128-wide CUDA-core tiles
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);
@@ -646,6 +646,13 @@ void solve(Launch &L, const DevModel &M, const Work &W, const double *rhs, doubl
   }
 }
 
+// The FP32 selected-inversion products run on the tensor cores when asked
+// for and the padded block size is a multiple of their 128-wide tiles.
+template <typename R>
+bool tensor_gemm(const DevModel &M) {
+  return sizeof(R) == sizeof(float) && M.gemm_t32 == INLA_GEMM_TF32X3 && M.n_p % 128 == 0;
+}
+
 // Block Takahashi recursion from the last time block to the first.
 template <typename R>
 void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contractions, double *marg_var,
@@ -668,9 +675,21 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
     k_sparse_left<R>(L, M, W, T1, W.sMat, S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
     if (contractions && nxt) k_contract_offdiag<R>(L, M, W, t, slotO);
     if (M.n_b > 0) k_dinv_apply<R>(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
-    gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, M.gemm_t32);
-    gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active,
-               M.gemm_t32);
+    if (tensor_gemm<R>(M)) {
+      // U = D^-1 S^T (= (S D^-1)^T, D^-1 symmetric), then Sigma_tt = D^-1 U^T + D^-1:
+      // both products read their operands along rows (X Y^T), as the tensor-core kernel wants
+      const float *Df = reinterpret_cast<const float *>(Dt);
+      float *Uf = reinterpret_cast<float *>(T1);
+      gemm_nt_tf32x3(L, W.P, M.n_p, Df, W.sDinv, reinterpret_cast<const float *>(S), W.sMat, Uf, W.sMat, 1.0f,
+                     nullptr, 0, 0.0f, false, W.active, W.status);
+      gemm_nt_tf32x3(L, W.P, M.n_p, Df, W.sDinv, Uf, W.sMat, reinterpret_cast<float *>(SigC), W.sMat, 1.0f, Df,
+                     W.sDinv, 1.0f, true, W.active, W.status);
+    } else {
+      const int tile = M.gemm_t32 == INLA_GEMM_TF32X3 ? 128 : M.gemm_t32;   // CUDA-core fallback
+      gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, tile);
+      gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active,
+                 tile);
+    }
     mirror_lower<R>(L, W.P, M.n_p, SigC, W.sMat, W.active);
     k_contract_diag<R>(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
     if (poisson_q) k_poisson_qobs<R>(L, M, W, t);
@@ -1049,8 +1068,8 @@ int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_f
   return guarded([&] {
     if (!model) throw ApiError(INLA_ERR_ARG, "model is NULL");
     if ((sweep_fp64 != 32 && sweep_fp64 != 64) || (sweep_fp32 != 32 && sweep_fp32 != 64) ||
-        (gemm_fp32 != 64 && gemm_fp32 != 128))
-      throw ApiError(INLA_ERR_ARG, "tile widths: sweep 32 or 64, FP32 GEMM 64 or 128");
+        (gemm_fp32 != 64 && gemm_fp32 != 128 && gemm_fp32 != INLA_GEMM_TF32X3))
+      throw ApiError(INLA_ERR_ARG, "tile widths: sweep 32 or 64, FP32 GEMM 64, 128 or INLA_GEMM_TF32X3");
     CUDA_OK(cudaSetDevice(model->device));
     CUDA_OK(cudaDeviceSynchronize());
     model->M.sweep_g64 = sweep_fp64;
@@ -1088,7 +1107,13 @@ int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_
     o.use_graph = 0;
     struct Cand { int g, t; };
     std::vector<Cand> cands;
-    if (fp32) cands = {{64, 128}, {32, 128}, {64, 64}, {32, 64}};
+    if (fp32) {
+      cands = {{64, 128}, {32, 128}, {64, 64}, {32, 64}};
+      if (M.n_p % 128 == 0) {
+        cands.push_back({64, INLA_GEMM_TF32X3});
+        cands.push_back({32, INLA_GEMM_TF32X3});
+      }
+    }
     else cands = {{32, M.gemm_t32}, {64, M.gemm_t32}};
     cudaEvent_t e0, e1;
     CUDA_OK(cudaEventCreate(&e0));

@@ -665,6 +665,7 @@ void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stri
 void dense_prepare() {
   ensure_attrs<double>();
   ensure_attrs<float>();
+  tc_prepare();
 }
 
 // Tile width per precision from the model (defaults: 32 for FP64, where short

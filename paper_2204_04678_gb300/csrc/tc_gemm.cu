@@ -1,0 +1,345 @@
+// Split-product (3xTF32) GEMM on the fifth-generation tensor cores.
+//
+//   C[b] = alpha X[b] Y[b]^T + beta C0[b]      (n x n, row-major FP32, n % 128 == 0)
+//
+// Used by the FP32 selected inversion (the Takahashi products of Eq.
+// sel_inv_cov on n_s x n_s blocks), where both operands are read along their
+// rows: X Y^T with X and Y row-major is a product of two K-major operands.
+// Each FP32 value x is split into two TF32 values, x_hi = tf32(x) and
+// x_lo = tf32(x - x_hi) (round to nearest, ties away), and
+//   X Y^T ~ X_lo Y_hi^T + X_hi Y_lo^T + X_hi Y_hi^T
+// is accumulated in FP32 in tensor memory (the X_lo Y_lo^T term is below
+// FP32 rounding).  One CTA computes one 128 x 128 tile of C:
+//   * all 256 threads load a 128 x 32 slab of X and of Y per stage (coalesced
+//     float4 loads, issued one stage ahead), split it, and store the four
+//     TF32 slabs into shared memory in the 128-byte swizzled K-major layout;
+//   * one thread issues the MMAs (tcgen05.mma kind::tf32, M = N = 128, K = 8;
+//     12 per stage) and commits them to the stage's mbarrier, which guards
+//     the stage's reuse two stages later (double buffering);
+//   * each stage's partial product goes to a pair of 128 x 128 FP32
+//     accumulators in tensor memory (X_hi Y_hi^T in one, the two cross terms
+//     in the other; two stages x two = all 512 columns), which the threads
+//     read back with tcgen05.ld two stages later (each warp its 32-lane
+//     quarter, half of the columns) and add into registers.  The tensor
+//     cores' own accumulation loses about one FP32 unit in the last place per
+//     addition (an error that grows linearly with K: 4.5e-5 relative at
+//     K = 1024 when one accumulator took the whole sum), so the large hi*hi
+//     partial takes only the 4 MMAs of one 32-deep stage, the small cross
+//     terms never round it, and the sum over stages runs in FP32 arithmetic.
+// Every mbarrier wait is bounded (2 s of %globaltimer); a wait that runs out
+// marks the point INLA_ERR_TIMEOUT, skips the epilogue, releases the tensor
+// memory and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "inla_internal.cuh"
+
+namespace inla {
+namespace {
+
+constexpr int TCM = 128;                              // tile rows = tile columns
+constexpr int TCK = 32;                               // K per stage (one 128-byte swizzle row)
+constexpr int TC_THREADS = 256;
+constexpr int SLAB_BYTES = TCM * TCK * 4;             // 16 KB per operand slab
+constexpr int STAGE_BYTES = 4 * SLAB_BYTES;           // X_hi, X_lo, Y_hi, Y_lo
+constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024;       // two stages + alignment slack
+constexpr uint32_t TMEM_COLS = 512;                   // 2 stages x {hi*hi, cross terms} x 128 columns
+constexpr uint64_t WAIT_NS = 2000000000ull;           // bound on one mbarrier wait
+
+// Instruction descriptor of kind::tf32: D in F32 (bits 4-5 = 1), A and B in
+// TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22, M / 16 in bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TCM >> 3) << 17) |
+                           ((uint32_t)(TCM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading
+// byte offset / 16 (bits 16-29; unused by swizzled K-major operands, set to
+// 1), stride byte offset / 16 (bits 32-45: 1024 B between 8-row groups),
+// the fixed 0b001 in bits 46-48, swizzle mode 2 = 128-byte in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until the mbarrier phase of the given parity has completed; false if
+// the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > WAIT_NS) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem), "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Split four FP32 values into TF32 hi / lo parts and store them at byte
+// offset `off` of the hi and lo slabs.
+__device__ __forceinline__ void split_store(uint8_t *hi, uint8_t *lo, uint32_t off, float4 v) {
+  uint4 h, l;
+  h.x = tf32_rna(v.x);
+  h.y = tf32_rna(v.y);
+  h.z = tf32_rna(v.z);
+  h.w = tf32_rna(v.w);
+  l.x = tf32_rna(v.x - __uint_as_float(h.x));
+  l.y = tf32_rna(v.y - __uint_as_float(h.y));
+  l.z = tf32_rna(v.z - __uint_as_float(h.z));
+  l.w = tf32_rna(v.w - __uint_as_float(h.w));
+  *reinterpret_cast<uint4 *>(hi + off) = h;
+  *reinterpret_cast<uint4 *>(lo + off) = l;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tf32x3_kernel(int n, const float *__restrict__ X, int64_t sX, const float *__restrict__ Y, int64_t sY,
+                       float *__restrict__ C, int64_t sC, float alpha, const float *__restrict__ C0, int64_t sC0,
+                       float beta, int lower_only, const int *active, int *status) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  int ti, tj;
+  if (lower_only) {
+    const int t = blockIdx.x;
+    ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    tj = t - ti * (ti + 1) / 2;
+  } else {
+    const int nt = n / TCM;
+    ti = blockIdx.x / nt;
+    tj = blockIdx.x % nt;
+  }
+  const int i0 = ti * TCM, j0 = tj * TCM;
+  const float *Xb = X + b * sX + (int64_t)i0 * n;
+  const float *Yb = Y + b * sY + (int64_t)j0 * n;
+
+  extern __shared__ uint8_t smraw[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const uint32_t raw = smem_addr(smraw);
+  uint8_t *base = smraw + (((raw + 1023u) & ~1023u) - raw);   // 1024-aligned for the swizzle atoms
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1u) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1u) : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  // thread -> (row, 16-byte chunk) of a 128 x 32 slab, four slots per operand
+  float4 xv[4], yv[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int idx = tid + TC_THREADS * it, r = idx >> 3, q = idx & 7;
+      xv[it] = __ldg(reinterpret_cast<const float4 *>(Xb + (int64_t)r * n + k0 + 4 * q));
+      yv[it] = __ldg(reinterpret_cast<const float4 *>(Yb + (int64_t)r * n + k0 + 4 * q));
+    }
+  };
+  const int nch = n / TCK;
+  // This thread's 64 entries of the C tile: row 32 * quarter + lane, columns
+  // 64 * half .. 64 * half + 63 (a warp reads only its own 32-lane quarter of TMEM).
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
+  float racc[64];
+#pragma unroll
+  for (int e = 0; e < 64; ++e) racc[e] = 0.0f;
+  // add the stage's partial product (TMEM accumulator s) into the registers
+  auto drain = [&](int s) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      uint32_t big[32], small[32];
+      const uint32_t col = (uint32_t)(2 * s * TCM + half * 64 + cc * 32);
+      tmem_ld32(tmem + lane_addr + col, big);
+      tmem_ld32(tmem + lane_addr + col + TCM, small);
+#pragma unroll
+      for (int e = 0; e < 32; ++e) racc[cc * 32 + e] += __uint_as_float(big[e]) + __uint_as_float(small[e]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+  load(0);
+  bool aborted = false;
+  int last = -1;   // last stage whose MMAs were committed
+  for (int c = 0; c < nch; ++c) {
+    const int s = c & 1;
+    if (c >= 2) {
+      // stage s and accumulator s are free once the MMAs of chunk c - 2 completed
+      const bool ok = mbar_wait(smem_addr(&mbar[s]), (uint32_t)((c - 2) >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      drain(s);
+    }
+    uint8_t *st = base + s * STAGE_BYTES;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int idx = tid + TC_THREADS * it, r = idx >> 3, q = idx & 7;
+      const uint32_t off = (uint32_t)(r * 128 + ((q ^ (r & 7)) << 4));
+      split_store(st, st + SLAB_BYTES, off, xv[it]);
+      split_store(st + 2 * SLAB_BYTES, st + 3 * SLAB_BYTES, off, yv[it]);
+    }
+    if (c + 1 < nch) load((c + 1) * TCK);   // next slab in flight during this stage's MMAs
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t xh = smem_addr(st), xl = xh + SLAB_BYTES, yh = xh + 2 * SLAB_BYTES, yl = xh + 3 * SLAB_BYTES;
+      const uint32_t big = tmem + (uint32_t)(2 * s * TCM), small = big + TCM;
+#pragma unroll
+      for (int ks = 0; ks < TCK / 8; ++ks) {   // K = 8 TF32 = 32 bytes per MMA
+        const uint32_t o = 32u * ks, acc = ks > 0 ? 1u : 0u;
+        mma_tf32(small, sw128_desc(xl + o), sw128_desc(yh + o), acc);
+        mma_tf32(small, sw128_desc(xh + o), sw128_desc(yl + o), 1u);
+        mma_tf32(big, sw128_desc(xh + o), sw128_desc(yh + o), acc);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&mbar[s]))
+                   : "memory");
+    }
+    last = c;
+  }
+  if (!aborted) {
+    // the last two stages' partial products
+    for (int c = nch - 2; c < nch; ++c) {
+      const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      drain(c & 1);
+    }
+  }
+  if (aborted && last >= 0) {
+    // wait (bounded) for the MMAs in flight before the tensor memory is released
+    mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u);
+  }
+  if (!aborted) {
+    const int row = i0 + 32 * quarter + lane;
+    float *crow = C + b * sC + (int64_t)row * n + j0 + half * 64;
+    const float *c0row = C0 ? C0 + b * sC0 + (int64_t)row * n + j0 + half * 64 : nullptr;
+#pragma unroll
+    for (int e = 0; e < 64; e += 4) {
+      float4 o = make_float4(alpha * racc[e], alpha * racc[e + 1], alpha * racc[e + 2], alpha * racc[e + 3]);
+      if (c0row) {
+        const float4 z = *reinterpret_cast<const float4 *>(c0row + e);
+        o.x += beta * z.x;
+        o.y += beta * z.y;
+        o.z += beta * z.z;
+        o.w += beta * z.w;
+      }
+      *reinterpret_cast<float4 *>(crow + e) = o;
+    }
+  } else if (tid == 0 && status) {
+    status[b] = INLA_ERR_TIMEOUT;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace
+
+void tc_prepare() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  done = true;
+}
+
+void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const float *Y, int64_t sY, float *C,
+                    int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, bool lower_only,
+                    const int *active, int *status) {
+  tc_prepare();
+  const int nt = n / TCM;
+  const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
+  L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
+  gemm_tf32x3_kernel<<<dim3(tiles, P), TC_THREADS, TC_SMEM, L.st>>>(n, X, sX, Y, sY, C, sC, alpha, C0, sC0, beta,
+                                                                     lower_only ? 1 : 0, active, status);
+  L.stop();
+  L.tick();
+}
+
+}  // namespace inla
+
+// C[b] = X[b] Y[b]^T for a batch of n x n row-major FP32 matrices on the
+// tensor cores (3xTF32); see include/inla_gpu.h.
+extern "C" int inla_gemm_tf32x3(int n, int batch, const float *X, const float *Y, float *C, int32_t *status,
+                                void *stream) {
+  if (n <= 0 || n % 128 != 0 || batch <= 0 || !X || !Y || !C) {
+    inla::set_error("inla_gemm_tf32x3: n must be a positive multiple of 128, batch > 0, X, Y, C non-NULL");
+    return INLA_ERR_ARG;
+  }
+  if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(C)) & 15u) {
+    inla::set_error("inla_gemm_tf32x3: X, Y and C must be 16-byte aligned");
+    return INLA_ERR_ARG;
+  }
+  inla::Launch L{static_cast<cudaStream_t>(stream), nullptr};
+  const int64_t s = (int64_t)n * n;
+  if (status) cudaMemsetAsync(status, 0, sizeof(int32_t) * batch, L.st);
+  inla::gemm_nt_tf32x3(L, batch, n, X, s, Y, s, C, s, 1.0f, nullptr, 0, 0.0f, false, nullptr, status);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    inla::set_error(cudaGetErrorString(e));
+    return INLA_ERR_CUDA;
+  }
+  return INLA_OK;
+}
