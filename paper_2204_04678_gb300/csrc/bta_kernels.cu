@@ -14,6 +14,8 @@
 // only dense work per time step is one n_s x n_s inversion (dense_fp64.cu).
 #include <cmath>
 
+#include <cstring>
+
 #include "inla_internal.cuh"
 
 namespace inla {
@@ -48,6 +50,24 @@ template <typename V>
 __device__ __forceinline__ V warp_sum(V v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
+}
+
+
+// 16-byte vector access to R arrays (4 floats or 2 doubles); addresses 16-byte aligned.
+template <typename R>
+struct Vec16 {
+  static constexpr int N = 16 / sizeof(R);
+};
+template <typename R>
+__device__ __forceinline__ void ld16(R (&v)[16 / sizeof(R)], const R *p) {
+  const uint4 u = *reinterpret_cast<const uint4 *>(p);
+  memcpy(v, &u, 16);
+}
+template <typename R>
+__device__ __forceinline__ void st16(R *p, const R (&v)[16 / sizeof(R)]) {
+  uint4 u;
+  memcpy(&u, v, 16);
+  *reinterpret_cast<uint4 *>(p) = u;
 }
 
 // Likelihood part of the arrow block (a, t), row l, column i (scaled into Q_c).
@@ -147,40 +167,73 @@ __global__ void init_step0_kernel(DevModel M, Work W, int mode) {
 // Only the lower 32-wide tiles are written: the block sweep (32- or 64-wide
 // tiles) reads nothing else.  T1 is computed up to 64-wide tiles past the band.
 constexpr int SWEEP_TILE = 32, SWEEP_TILE_MAX = 64;
+// Row i of the lower 32-tiles of the diagonal block: the sparse part
+// c Q_s + (likelihood) staged in a shared row buffer, minus (Schur update)
+// q_off^2 (Q_s T1)_{i,:}, with T1 = D_{t-1}^-1 Q_s; identity in the padding.
+// One block per (row, point); the row's pattern (<= ROW_PMAX entries) is staged
+// in shared memory so that every thread streams 16-byte vectors of T1 rows.
 template <typename R>
-__global__ void assemble_diag_kernel(DevModel M, Work W, int t, int mode, R *dst, int64_t sdst, int schur) {
-  const int b = blockIdx.z;
+__global__ void __launch_bounds__(256) assemble_diag_kernel(DevModel M, Work W, int t, int mode, R *dst,
+                                                           int64_t sdst, int schur) {
+  constexpr int V = Vec16<R>::N;
+  const int b = blockIdx.y, i = blockIdx.x;
   if (!W.active[b]) return;
-  const int i = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ double rowbuf[];     // [n_p]: the sparse part of row i
+  __shared__ int pc[ROW_PMAX];
+  __shared__ R pv[ROW_PMAX];
   const int n_p = M.n_p, n_s = M.n_s;
-  if (j >= n_p || j >= (i / SWEEP_TILE + 1) * SWEEP_TILE) return;
-  R *out = dst + b * sdst + (int64_t)i * n_p + j;
-  if (i >= n_s || j >= n_s) {
-    *out = (i == j) ? R(1) : R(0);
+  const int jmax = min(n_p, (i / SWEEP_TILE + 1) * SWEEP_TILE);
+  R *out = dst + b * sdst + (int64_t)i * n_p;
+  if (i >= n_s) {
+    for (int j = threadIdx.x; j < jmax; j += blockDim.x) out[j] = (i == j) ? R(1) : R(0);
     return;
   }
   const PointParams &p = W.prm[b];
   const double c = (mode == ASM_QS) ? 1.0 : q_tt(p, t, M.n_t);
   const double *qs = W.qs + b * W.sNnz;
-  const R *T1 = static_cast<const R *>(W.T1) + b * W.sMat;
   const double *lik = nullptr;
   double lik_scale = 0.0;
   if (mode == ASM_QC) {
     if (M.lik == INLA_LIK_GAUSSIAN) { lik = M.AtA + (int64_t)t * M.nnz; lik_scale = p.tau_y; }
     else { lik = W.AtAp + b * W.sAtAp + (int64_t)t * M.nnz; lik_scale = 1.0; }
   }
-  R acc = 0;
-  double sparse = 0.0;
-  for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) {
-    const int k = M.pcol[e];
-    if (schur) acc = fma((R)qs[e], T1[(int64_t)k * n_p + j], acc);
-    if (k == j) {
-      sparse = c * qs[e];
-      if (lik) sparse += lik_scale * lik[e];
-    }
+  const int e0 = M.prow[i], len = M.prow[i + 1] - e0;
+  for (int j = threadIdx.x; j < jmax; j += blockDim.x) rowbuf[j] = 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < len; e += blockDim.x) {
+    const int k = M.pcol[e0 + e];
+    pc[e] = k;
+    pv[e] = (R)qs[e0 + e];
+    if (k < jmax) rowbuf[k] = c * qs[e0 + e] + (lik ? lik_scale * lik[e0 + e] : 0.0);
   }
-  *out = (R)(sparse - (schur ? p.q_off * p.q_off * (double)acc : 0.0));
+  __syncthreads();
+  const R *T1 = static_cast<const R *>(W.T1) + b * W.sMat;
+  const R q2 = (R)(p.q_off * p.q_off);
+  for (int j = threadIdx.x * V; j < jmax; j += blockDim.x * V) {
+    R acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = R(0);
+    if (schur) {
+      int e = 0;
+      for (; e + 2 <= len; e += 2) {
+        R x0[V], x1[V];
+        ld16<R>(x0, T1 + (int64_t)pc[e] * n_p + j);
+        ld16<R>(x1, T1 + (int64_t)pc[e + 1] * n_p + j);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fma(pv[e + 1], x1[v], fma(pv[e], x0[v], acc[v]));
+      }
+      if (e < len) {
+        R x0[V];
+        ld16<R>(x0, T1 + (int64_t)pc[e] * n_p + j);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = fma(pv[e], x0[v], acc[v]);
+      }
+    }
+    R o[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = (j + v < n_s) ? fma(-q2, acc[v], (R)rowbuf[j + v]) : R(0);
+    st16<R>(out + j, o);
+  }
 }
 
 // out[i][j] = coef * sum_k X[i][k] Q_s[k][j] + sum_l SigA[l][i] Rt[l][j]   (i, j < n_s; 0 elsewhere)
@@ -259,30 +312,109 @@ __global__ void sparse_right_kernel(DevModel M, Work W, const R *X, int64_t sX, 
 }
 
 // out[i][j] = [with_X] q_off * sum_k Q_s[i][k] X[k][j] + sum_l Rt[l][i] Y[l][j]
+// One block per (row, point): the row's pattern is staged in shared memory and
+// every thread streams 16-byte vectors of the pattern rows of X.
 template <typename R>
-__global__ void sparse_left_kernel(DevModel M, Work W, const R *X, int64_t sX, R *outp, int64_t sOut,
-                                   int with_X, const double *Rt_t, const double *Ymat) {
-  const int b = blockIdx.z;
+__global__ void __launch_bounds__(256) sparse_left_kernel(DevModel M, Work W, const R *X, int64_t sX, R *outp,
+                                                         int64_t sOut, int with_X, const double *Rt_t,
+                                                         const double *Ymat) {
+  constexpr int V = Vec16<R>::N;
+  const int b = blockIdx.y, i = blockIdx.x;
   if (!W.active[b]) return;
-  const int i = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ int pc[ROW_PMAX];
+  __shared__ R pv[ROW_PMAX];
+  __shared__ R rv[MAX_NB];
   const int n_p = M.n_p, n_s = M.n_s;
-  if (j >= n_p) return;
-  R *out = outp + b * sOut + (int64_t)i * n_p + j;
-  if (i >= n_s || j >= n_s) { *out = R(0); return; }
-  R acc = 0;
-  if (with_X) {
-    const R *Xb = X + b * sX;
-    const double *qs = W.qs + b * W.sNnz;
-    for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) acc = fma((R)qs[e], Xb[(int64_t)M.pcol[e] * n_p + j], acc);
-    acc *= (R)W.prm[b].q_off;
+  R *out = outp + b * sOut + (int64_t)i * n_p;
+  if (i >= n_s) {
+    R z[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) z[v] = R(0);
+    for (int j = threadIdx.x * V; j < n_p; j += blockDim.x * V) st16<R>(out + j, z);
+    return;
   }
-  if (Ymat) {
-    const double *rt = Rt_t + b * W.sRt;
-    const double *y = Ymat + b * W.sNbNp;
-    for (int l = 0; l < M.n_b; ++l) acc = fma((R)rt[(int64_t)l * n_p + i], (R)y[(int64_t)l * n_p + j], acc);
+  const int e0 = M.prow[i], len = with_X ? M.prow[i + 1] - e0 : 0;
+  const R q = (R)W.prm[b].q_off;
+  const double *qs = W.qs + b * W.sNnz;
+  for (int e = threadIdx.x; e < len; e += blockDim.x) {
+    pc[e] = M.pcol[e0 + e];
+    pv[e] = q * (R)qs[e0 + e];
   }
-  *out = acc;
+  const int nb = Ymat ? M.n_b : 0;
+  if (threadIdx.x < nb) rv[threadIdx.x] = (R)Rt_t[b * W.sRt + (int64_t)threadIdx.x * n_p + i];
+  __syncthreads();
+  const R *Xb = X + b * sX;
+  const double *Y = Ymat ? Ymat + b * W.sNbNp : nullptr;
+  for (int j = threadIdx.x * V; j < n_p; j += blockDim.x * V) {
+    R acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = R(0);
+    int e = 0;
+    for (; e + 2 <= len; e += 2) {
+      R x0[V], x1[V];
+      ld16<R>(x0, Xb + (int64_t)pc[e] * n_p + j);
+      ld16<R>(x1, Xb + (int64_t)pc[e + 1] * n_p + j);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = fma(pv[e + 1], x1[v], fma(pv[e], x0[v], acc[v]));
+    }
+    if (e < len) {
+      R x0[V];
+      ld16<R>(x0, Xb + (int64_t)pc[e] * n_p + j);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = fma(pv[e], x0[v], acc[v]);
+    }
+    for (int l = 0; l < nb; ++l)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[v] = fma(rv[l], (R)Y[(int64_t)l * n_p + j + v], acc[v]);
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+      if (j + v >= n_s) acc[v] = R(0);
+    st16<R>(out + j, acc);
+  }
+}
+
+// out[i] = scale * sum_k Dinv[i][k] v[k]: the block GEMV of the substitutions,
+// bound by streaming D_t^-1 from HBM.  The vector is staged once per block in
+// shared memory (as R); each warp reads 2 rows of D_t^-1 in 16-byte vectors.
+constexpr int GV_ROWS_PER_WARP = 2;
+constexpr int GV_ROWS = 8 * GV_ROWS_PER_WARP;
+template <typename R>
+__global__ void __launch_bounds__(256) dinv_gemv_kernel(DevModel M, Work W, const R *Dinv_t, const double *vecs,
+                                                       int64_t sVecs, double *outp, int64_t sOut, double scale) {
+  constexpr int V = Vec16<R>::N;
+  const int b = blockIdx.y;
+  if (!W.active[b]) return;
+  extern __shared__ __align__(16) unsigned char gv_raw[];
+  R *vs = reinterpret_cast<R *>(gv_raw);
+  const int n_p = M.n_p;
+  const double *vb = vecs + b * sVecs;
+  for (int k = threadIdx.x; k < n_p; k += blockDim.x) vs[k] = (R)vb[k];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * GV_ROWS + warp * GV_ROWS_PER_WARP;
+  if (row0 >= n_p) return;
+  const R *D0 = Dinv_t + b * W.sDinv + (int64_t)row0 * n_p;
+  const R *D1 = D0 + n_p;   // row0 + 1 < n_p: n_p is a multiple of 64
+  R a0 = R(0), a1 = R(0);
+#pragma unroll 4
+  for (int k = lane * V; k < n_p; k += 32 * V) {
+    R d0[V], d1[V], x[V];
+    ld16<R>(d0, D0 + k);
+    ld16<R>(d1, D1 + k);
+    ld16<R>(x, vs + k);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      a0 = fma(d0[v], x[v], a0);
+      a1 = fma(d1[v], x[v], a1);
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  if (lane == 0) {
+    double *O = outp + b * sOut;
+    O[row0] = scale * (double)a0;
+    O[row0 + 1] = scale * (double)a1;
+  }
 }
 
 // out[c][i] = scale * sum_k Dinv[i][k] vecs[c][k], c < nvec (Dinv symmetric).
@@ -539,7 +671,7 @@ __global__ void __launch_bounds__(256) contract_offdiag_kernel(DevModel M, Work 
       }
     }
   }
-  double *part = W.part + ((int64_t)b * NPART + blockIdx.x) * 4;
+  double *part = W.part + ((int64_t)b * NPART + blockIdx.x) * PART_W;
   sC = block_sum(sC, red);
   if (threadIdx.x == 0) part[0] = sC;
   sG = block_sum(sG, red);
@@ -548,33 +680,45 @@ __global__ void __launch_bounds__(256) contract_offdiag_kernel(DevModel M, Work 
   if (threadIdx.x == 0) part[2] = sH;
 }
 
-// dst[b*stride + slot_c] = sum of the first nparts partial sums of component c.
-__global__ void reduce_parts_kernel(Work W, int nparts, int ncomp, double *dst, int64_t dstride) {
+// dst[b*stride + slot[c]] = sum of the first nparts partial sums of component c.
+struct Slots {
+  int n;
+  int at[PART_W];
+};
+__global__ void reduce_parts_kernel(Work W, int nparts, Slots slots, double *dst, int64_t dstride) {
   const int b = blockIdx.x;
   if (!W.active[b]) return;
   __shared__ double red[32];
-  for (int c = 0; c < ncomp; ++c) {
+  for (int c = 0; c < slots.n; ++c) {
     double s = 0.0;
-    for (int p = threadIdx.x; p < nparts; p += blockDim.x) s += W.part[((int64_t)b * NPART + p) * 4 + c];
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) s += W.part[((int64_t)b * NPART + p) * PART_W + c];
     s = block_sum(s, red);
-    if (threadIdx.x == 0) dst[b * dstride + c] = s;
+    if (threadIdx.x == 0) dst[b * dstride + slots.at[c]] = s;
   }
+}
+Slots consecutive(int n, int first = 0) {
+  Slots s{n, {}};
+  for (int c = 0; c < n; ++c) s.at[c] = first + c;
+  return s;
 }
 
 // <Sigma_tt, X> on the pattern, <Sigma_{a,t}, Z^T D A_t>, and diag(Sigma_tt) output.
+// Grid-stride over the pattern entries across gridDim.x blocks per point; block
+// partial sums (C, G, H, A^T A, arrow) go to W.part and reduce_parts_kernel.
 template <typename R>
 __global__ void __launch_bounds__(256) contract_diag_kernel(DevModel M, Work W, int t, int mode, double *mv,
-                                                           const int *point_out, int64_t point_base, int slot0) {
-  const int b = blockIdx.x;
+                                                           const int *point_out, int64_t point_base) {
+  const int b = blockIdx.y;
   if (!W.active[b]) return;
   __shared__ double red[32];
   const int n_p = M.n_p;
+  const int stride = gridDim.x * blockDim.x, first = blockIdx.x * blockDim.x + threadIdx.x;
   const R *S = static_cast<const R *>(W.SigC) + b * W.sMat;
   const double *lik = nullptr;
   if (mode == ASM_QC)
     lik = (M.lik == INLA_LIK_GAUSSIAN) ? M.AtA + (int64_t)t * M.nnz : W.AtAp + b * W.sAtAp + (int64_t)t * M.nnz;
   double sC = 0.0, sG = 0.0, sH = 0.0, sA = 0.0;
-  for (int e = threadIdx.x; e < M.nnz; e += blockDim.x) {
+  for (int e = first; e < M.nnz; e += stride) {
     const double s = (double)S[(int64_t)M.prow_of[e] * n_p + M.pcol[e]];
     sC = fma(s, M.vC[e], sC);
     sG = fma(s, M.vG[e], sG);
@@ -586,30 +730,30 @@ __global__ void __launch_bounds__(256) contract_diag_kernel(DevModel M, Work W, 
     const double *arw = (M.lik == INLA_LIK_GAUSSIAN) ? M.Arw + (int64_t)t * M.n_b * M.n_s
                                                      : W.Arwp + b * W.sArwp + (int64_t)t * M.n_b * M.n_s;
     const double *sa = W.SigAc + b * W.sNbNp;
-    for (int e = threadIdx.x; e < M.n_b * M.n_s; e += blockDim.x) {
+    for (int e = first; e < M.n_b * M.n_s; e += stride) {
       const int l = e / M.n_s, i = e % M.n_s;
       sR = fma(sa[(int64_t)l * n_p + i], arw[e], sR);
     }
   }
-  double *pt = W.pt + (b * (int64_t)M.n_t + t) * PT_COUNT;
+  if (mode == ASM_QC && mv && point_out) {
+    const int o = point_out[point_base + b];
+    if (o >= 0) {
+      double *dst = mv + (int64_t)o * M.n + (int64_t)t * M.n_s;
+      for (int i = first; i < M.n_s; i += stride) dst[i] = (double)S[(int64_t)i * n_p + i];
+    }
+  }
+  double *part = W.part + ((int64_t)b * NPART + blockIdx.x) * PART_W;
   sC = block_sum(sC, red);
-  if (threadIdx.x == 0) pt[slot0 + 0] = sC;
+  if (threadIdx.x == 0) part[0] = sC;
   sG = block_sum(sG, red);
-  if (threadIdx.x == 0) pt[slot0 + 1] = sG;
+  if (threadIdx.x == 0) part[1] = sG;
   sH = block_sum(sH, red);
-  if (threadIdx.x == 0) pt[slot0 + 2] = sH;
+  if (threadIdx.x == 0) part[2] = sH;
   if (mode == ASM_QC) {
     sA = block_sum(sA, red);
-    if (threadIdx.x == 0) pt[PT_FD_ATA] = sA;
+    if (threadIdx.x == 0) part[3] = sA;
     sR = block_sum(sR, red);
-    if (threadIdx.x == 0) pt[PT_FA_ATA] = sR;
-    if (mv && point_out) {
-      const int o = point_out[point_base + b];
-      if (o >= 0) {
-        double *dst = mv + (int64_t)o * M.n + (int64_t)t * M.n_s;
-        for (int i = threadIdx.x; i < M.n_s; i += blockDim.x) dst[i] = (double)S[(int64_t)i * n_p + i];
-      }
-    }
+    if (threadIdx.x == 0) part[4] = sR;
   }
 }
 
@@ -703,7 +847,7 @@ __global__ void __launch_bounds__(256) obs_reduce_kernel(DevModel M, Work W, int
     }
   }
   s = block_sum(s, red);
-  if (threadIdx.x == 0) W.part[((int64_t)b * NPART + blockIdx.x) * 4] = s;
+  if (threadIdx.x == 0) W.part[((int64_t)b * NPART + blockIdx.x) * PART_W] = s;
 }
 
 // tr(Q_s^-1 X) for X in {C, G, H}, Q_s^-1 in T1.
@@ -1160,8 +1304,8 @@ void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode) {
 template <typename R>
 void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, R *dst, int64_t sdst,
                      bool schur) {
-  assemble_diag_kernel<R><<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, t, mode, dst, sdst,
-                                                                                schur ? 1 : 0);
+  assemble_diag_kernel<R><<<dim3(M.n_p, W.P), 256, sizeof(double) * M.n_p, L.st>>>(M, W, t, mode, dst, sdst,
+                                                                                   schur ? 1 : 0);
   L.tick();
 }
 template <typename R>
@@ -1181,8 +1325,7 @@ void k_sparse_right(Launch &L, const DevModel &M, const Work &W, const R *X, int
 template <typename R>
 void k_sparse_left(Launch &L, const DevModel &M, const Work &W, const R *X, int64_t sX, R *out, int64_t sOut,
                    bool with_X, const double *Rt_t, const double *Ymat) {
-  sparse_left_kernel<R><<<dim3(blocks(M.n_p, 128), M.n_p, W.P), 128, 0, L.st>>>(M, W, X, sX, out, sOut,
-                                                                              with_X ? 1 : 0, Rt_t, Ymat);
+  sparse_left_kernel<R><<<dim3(M.n_p, W.P), 256, 0, L.st>>>(M, W, X, sX, out, sOut, with_X ? 1 : 0, Rt_t, Ymat);
   L.tick();
 }
 template <typename R>
@@ -1190,8 +1333,8 @@ void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const R *Dinv_t, 
                   int64_t sVecs, double *out, int64_t sOut, double scale) {
   if (nvec <= 0) return;
   if (nvec == 1)
-    dinv_apply_kernel<R, 1><<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs, sVecs,
-                                                                               out, sOut, scale);
+    dinv_gemv_kernel<R><<<dim3(blocks(M.n_p, GV_ROWS), W.P), 256, sizeof(R) * M.n_p, L.st>>>(M, W, Dinv_t, vecs,
+                                                                                           sVecs, out, sOut, scale);
   else
     dinv_apply_kernel<R, DA_MAXV><<<dim3(blocks(M.n_p, DA_ROWS), W.P), 256, 0, L.st>>>(M, W, Dinv_t, nvec, vecs,
                                                                                      sVecs, out, sOut, scale);
@@ -1237,14 +1380,24 @@ void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int 
   if (nparts > NPART) nparts = NPART;
   contract_offdiag_kernel<R><<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W, t);
   L.tick();
-  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, 3, W.pt + (int64_t)t * PT_COUNT + slot0,
+  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, consecutive(3, slot0), W.pt + (int64_t)t * PT_COUNT,
                                             (int64_t)M.n_t * PT_COUNT);
   L.tick();
 }
 template <typename R>
 void k_contract_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *marg_var,
                      const int *point_out, int64_t point_base, int slot0) {
-  contract_diag_kernel<R><<<W.P, 256, 0, L.st>>>(M, W, t, mode, marg_var, point_out, point_base, slot0);
+  int nparts = (int)blocks(M.nnz, 1024);
+  if (nparts > 64) nparts = 64;
+  contract_diag_kernel<R><<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W, t, mode, marg_var, point_out, point_base);
+  L.tick();
+  Slots sl = consecutive(3, slot0);
+  if (mode == ASM_QC) {
+    sl.n = 5;
+    sl.at[3] = PT_FD_ATA;
+    sl.at[4] = PT_FA_ATA;
+  }
+  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, sl, W.pt + (int64_t)t * PT_COUNT, (int64_t)M.n_t * PT_COUNT);
   L.tick();
 }
 void k_contract_tip(Launch &L, const DevModel &M, const Work &W, int mode, double *marg_var, const int *point_out,
@@ -1266,7 +1419,8 @@ void k_obs_reduce(Launch &L, const DevModel &M, const Work &W, int kind) {
   if (nparts > NPART) nparts = NPART;
   obs_reduce_kernel<<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W, kind);
   L.tick();
-  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, 1, W.sc + (kind == 0 ? SC_RES2 : SC_LOGLIK), SC_COUNT);
+  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, consecutive(1), W.sc + (kind == 0 ? SC_RES2 : SC_LOGLIK),
+                                            SC_COUNT);
   L.tick();
 }
 void k_qs_traces(Launch &L, const DevModel &M, const Work &W) {

@@ -284,6 +284,8 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     int pmax = 0;
     for (int i = 0; i < n_s; ++i) pmax = std::max(pmax, prow[i + 1] - prow[i]);
     M.pmax = pmax;
+    if (pmax > ROW_PMAX)
+      throw ApiError(INLA_ERR_UNSUPPORTED, "a row of the pattern of G C^-1 G has more than 64 entries");
     M.sweep_g64 = 32;
     M.sweep_g32 = 64;
     M.gemm_t32 = INLA_GEMM_TF32X3;   // tensor cores where n_p % 128 == 0, else 128-wide CUDA-core tiles
@@ -445,7 +447,7 @@ Sizes sizes_of(const DevModel &M) {  // element counts per point
   s.gjCO = np * TILE;
   s.sc = 32;
   s.pt = rup((int64_t)M.n_t * PT_COUNT, 32);
-  s.part = NPART * 4;
+  s.part = NPART * PART_W;
   s.tippart = rup((int64_t)M.n_t * (nb * nb + nb), 32) + 32;
   s.ints = 32;
   if (M.lik == INLA_LIK_POISSON) {

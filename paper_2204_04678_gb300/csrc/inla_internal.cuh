@@ -26,6 +26,11 @@ constexpr int TILE = 64;        // dense tile edge (pivot blocks, GEMM tiles)
 constexpr int MAX_NB = 16;      // fixed effects supported by the small kernels
 constexpr int MAX_SPATIAL = 3;  // spatial entries per observation row
 constexpr int NPART = 256;      // partial sums per point for long reductions
+constexpr int PART_W = 8;       // components per partial sum
+// Longest row of the sparse pattern (Q_s and A^T A on one time block) that the
+// row kernels stage in shared memory; the 2-ring SPDE stencil of a triangle
+// mesh has ~19 entries per row.
+constexpr int ROW_PMAX = 64;
 
 // Scalars of one evaluation point, computed on the device from theta.
 struct PointParams {
@@ -96,7 +101,7 @@ struct Work {
   double *QsI;                           // [P][n_p][n_p]  Q_s^-1 (Kronecker prior), always FP64
   double *sc;            // [P][SC_COUNT] per-point scalars
   double *pt;            // [P][n_t][PT_COUNT] per-time-block contractions
-  double *part;          // [P][NPART][4] partial sums
+  double *part;          // [P][NPART][PART_W] partial sums
   double *tippart;       // [P][n_t][n_b*n_b + n_b] per-time-block partial sums
   int *status;           // [P]
   int *active;           // [P]  1 = this point takes part in the current pass
