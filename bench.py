@@ -227,6 +227,15 @@ def config_dict(cfg, world, grad=None, precision=None, points=9):
             "l2": "working set (GBs of factor storage per step) exceeds L2; no flush"}
 
 
+def measured_peaks_json():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
 # ------------------------------------------------------------------ mixed-precision accuracy
 
 def mixed_errors(model, theta, grad):
@@ -437,31 +446,42 @@ def main():
     value = world * args.steps * per_step / elapsed
 
     # dominant instrumented kernel: the sweep's tile update or the selected-inversion GEMM
-    ms, nl, units = model.profile_read(capi.KERNEL_GJ_UPDATE)
-    gms, gnl, gunits = model.profile_read(capi.KERNEL_GEMM)
+    fp32 = prec == "mixed"
+    n_p = -(-mdl.n_s // 64) * 64
+    tensor_gemm = fp32 and n_p % 128 == 0 and args.gemm != "cuda-core"
+    upd_id = capi.KERNEL_GJ_UPDATE32 if fp32 else capi.KERNEL_GJ_UPDATE
+    kernels = {"gj_update_kernel": model.profile_read(upd_id), "gemm_nn_kernel": model.profile_read(capi.KERNEL_GEMM)}
     model.profile_enable(0)
     flop_per_unit = 2.0 * 64 ** 3
-    fp32 = prec == "mixed"
-    peak = peak_fp32 if fp32 else peak_fp64
-    kernels = {"gj_update_kernel": (ms, nl, units), "gemm_nn_kernel": (gms, gnl, gunits)}
+    peaks = measured_peaks_json()
+    tf32x3_peak = None
+    if peaks.get("bf16_tflops_sustained"):
+        # nominal dense TF32 / BF16 = 1.1 / 2.25; three TF32 products per algorithmic product
+        tf32x3_peak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
     kname = max(kernels, key=lambda k: kernels[k][0])
     kms, knl, kunits = kernels[kname]
     avg_s = kms / 1e3 / max(knl, 1)
     achieved = kunits / max(knl, 1) * flop_per_unit / avg_s / 1e12 if knl else None
+    if kname == "gemm_nn_kernel" and tensor_gemm and tf32x3_peak:
+        peak, bound = tf32x3_peak, "tensor"
+        peak_source = ("MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/BF16 ratio / 3 "
+                       "TF32 products per 3xTF32 product, of measured")
+        desc = "128x128 tile 3xTF32 GEMM of the selected inversion on the tensor cores (tcgen05)"
+    else:
+        peak, bound = (peak_fp32 if fp32 else peak_fp64), "alu"
+        peak_source = ("measured on this GPU: " + ("FP32" if fp32 else "FP64")
+                       + " FMA loop over all SMs (inla_measure_fp32/fp64_peak), of measured")
+        desc = {"gj_update_kernel": ("FP32" if fp32 else "FP64") + " tile update of the block sweep inversion",
+                "gemm_nn_kernel": ("FP32" if fp32 else "FP64") + " tile GEMM of the selected inversion"}[kname]
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "gj_update_traffic.txt")
     if kname == "gj_update_kernel" and not fp32 and os.path.exists(tfile):
         for line in open(tfile):
             if line.startswith("bytes_per_unit="):
                 traffic = float(line.split("=")[1]) * kunits / max(knl, 1)
-    desc = {"gj_update_kernel": "rank-32 tile update of the block sweep inversion",
-            "gemm_nn_kernel": "64x64 tile GEMM of the selected inversion"}[kname]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": f"{kname} ({'FP32' if fp32 else 'FP64'} {desc})",
-                "timed_every": PROFILE_EVERY,
-                "peak_source": ("measured on this GPU: " + ("FP32" if fp32 else "FP64")
-                                + " FMA loop over all SMs (inla_measure_fp32/fp64_peak)"),
+                "kernel": f"{kname} ({desc})", "timed_every": PROFILE_EVERY, "peak_source": peak_source,
                 "launches_timed": knl, "share_of_step": PROFILE_EVERY * kms / 1e3 / elapsed if elapsed else None}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -504,7 +524,8 @@ def main():
                 "f_evals_per_s": 9 * value if grad == "fd" else value,
                 "grad_mode": grad,
                 "errors_vs_fp64": errors,
-                "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32},
+                "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32,
+                                          "tf32x3_tensor_from_bf16_sustained": tf32x3_peak},
                 "kernels": {k: {"ms_sampled": v[0], "launches_sampled": v[1],
                                 "tflops": v[2] * flop_per_unit / (v[0] / 1e3) / 1e12 if v[0] else None}
                             for k, v in kernels.items()}}

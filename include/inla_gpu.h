@@ -232,9 +232,11 @@ int64_t inla_last_launch_count(const inla_model *model);
  * kernel, the summed event time in ms, the number of launches and the
  * number of algorithmic units processed (a unit is one 64 x 64 x 64 tile
  * product, 2 * 64^3 flops).  Enabling resets the records.
- *   kernel 0: rank-32 tile update of the block sweep inversion
- *   kernel 1: 64 x 64 tile GEMM of the selected inversion
- *   kernel 2: pivot-block inversion        kernel 3: pivot-panel product */
+ *   kernel 0: tile update of the block sweep inversion, FP64 blocks
+ *   kernel 1: tile GEMM of the selected inversion (FP64, FP32, or 3xTF32
+ *             on the tensor cores)
+ *   kernel 2: pivot-block inversion        kernel 3: pivot-panel product
+ *   kernel 4: tile update of the block sweep inversion, FP32 blocks */
 int inla_profile_enable(inla_model *model, int enable);
 int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *launches, double *units);
 

@@ -31,6 +31,7 @@ KERNEL_GJ_UPDATE = 0
 KERNEL_GEMM = 1
 KERNEL_GJ_PIVOT = 2
 KERNEL_GJ_PANEL = 3
+KERNEL_GJ_UPDATE32 = 4
 
 STATIC_SCRATCH_BYTES = 64 << 20
 

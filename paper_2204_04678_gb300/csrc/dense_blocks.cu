@@ -75,7 +75,7 @@ __device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) 
   R *a = sm;                          // [G][LD]   full symmetric working copy
   R *sp = sm + G * LD;                // [SB][SB+1] sub-pivot, then its inverse
   R *Cp = sp + SB * (SB + 1);         // [G][SB]   sub-panel C = A_iK P
-  R *Op = Cp + G * SB;                // [G][SB]   old column block A_iK
+  R *Op = Cp + G * SB;                // [SB][G]   old column block A_iK, transposed
   R *pv = Op + G * SB;                // [G]       scalar pivots
   __shared__ int s_bad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -89,51 +89,43 @@ __device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) 
   for (int kb = 0; kb < G / SB; ++kb) {
     const int K0 = kb * SB;
     if (warp == 0) {
-      // 1. scalar sweep of the 16 x 16 sub-pivot by one warp: 8 entries per lane
+      // 1. scalar sweep of the 16 x 16 sub-pivot by one warp, in registers:
+      //    lane l holds entries (2 q + l / 16, l % 16), q < 8; the pivot row and
+      //    column reach every lane by shuffles, so a pivot step is a short
+      //    dependency chain (shuffle, reciprocal, one FMA) with no shared memory
       R v[8];
+      const int hi = lane >> 4, j = lane & 15;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int e = lane + 32 * q, i = e >> 4, j = e & 15;
-        v[q] = a[(K0 + i) * LD + K0 + j];
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int e = lane + 32 * q;
-        sp[(e >> 4) * (SB + 1) + (e & 15)] = v[q];
-      }
-      __syncwarp();
+      for (int q = 0; q < 8; ++q) v[q] = a[(K0 + 2 * q + hi) * LD + K0 + j];
       bool bad = false;
+#pragma unroll
       for (int p = 0; p < SB; ++p) {
-        const R piv = sp[p * (SB + 1) + p];
+        const int qp = p >> 1, lp = ((p & 1) << 4);
+        const R piv = __shfl_sync(0xffffffffu, v[qp], lp + p);
         const bool ok = (piv > R(0)) && (piv < R(INFINITY));
         if (!ok) bad = true;
         const R inv = ok ? R(1) / piv : R(0);
-        R ip[8], pj[8];
+        const R pj = __shfl_sync(0xffffffffu, v[qp], lp + j);        // entry (p, j)
+        R ip[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ip[q] = __shfl_sync(0xffffffffu, v[q], (lane & 16) + p);   // entry (i, p)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int e = lane + 32 * q, i = e >> 4, j = e & 15;
-          ip[q] = sp[i * (SB + 1) + p];
-          pj[q] = sp[p * (SB + 1) + j];
-          v[q] = sp[i * (SB + 1) + j];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int e = lane + 32 * q, i = e >> 4, j = e & 15;
-          R w;
-          if (i == p) w = (j == p) ? -inv : pj[q] * inv;
-          else if (j == p) w = ip[q] * inv;
-          else w = fma(-ip[q] * inv, pj[q], v[q]);
-          sp[i * (SB + 1) + j] = w;
+          const int i = 2 * q + hi;
+          if (i == p) v[q] = (j == p) ? -inv : pj * inv;
+          else if (j == p) v[q] = ip[q] * inv;
+          else v[q] = fma(-ip[q] * inv, pj, v[q]);
         }
         if (lane == 0) pv[K0 + p] = ok ? piv : R(1);
-        __syncwarp();
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sp[(2 * q + hi) * (SB + 1) + j] = v[q];
       if (bad && lane == 0) s_bad = 1;
       // sp now holds -P, P = (sub-pivot)^-1
     }
     __syncthreads();
-    // 2. sub-panel C_i = A_iK P for rows i outside the sub-pivot; keep the old A_iK
+    // 2. sub-panel C_i = A_iK P for rows i outside the sub-pivot; keep the old
+    //    A_iK, transposed (OpT[c][i]) so that step 3 reads it without bank conflicts
     for (int e = tid; e < G * SB; e += S::THREADS) {
       const int i = e / SB, c = e % SB;
       if (i >= K0 && i < K0 + SB) continue;
@@ -141,25 +133,49 @@ __device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) 
 #pragma unroll
       for (int k = 0; k < SB; ++k) acc = fma(a[i * LD + K0 + k], -sp[k * (SB + 1) + c], acc);
       Cp[i * SB + c] = acc;
-      Op[i * SB + c] = a[i * LD + K0 + c];
+      Op[c * G + i] = a[i * LD + K0 + c];
     }
     __syncthreads();
-    // 3. rank-16 update of everything outside the sub-pivot rows/columns; the
-    //    sub-pivot row/column become C, the sub-pivot block -P
-    for (int e = tid; e < G * G; e += S::THREADS) {
-      const int i = e >> S::SHIFT, j = e & (G - 1);
-      const bool ik = i >= K0 && i < K0 + SB, jk = j >= K0 && j < K0 + SB;
-      R w;
-      if (ik && jk) w = sp[(i - K0) * (SB + 1) + (j - K0)];
-      else if (jk) w = Cp[i * SB + (j - K0)];
-      else if (ik) w = Cp[j * SB + (i - K0)];
-      else {   // the rank-SB product is summed first and subtracted once
-        R u = R(0);
+    // 3. rank-SB update of everything outside the sub-pivot rows/columns (each
+    //    thread a MI x 4 patch: rows ty + 16 i, columns tx + TX j, the product
+    //    summed first and subtracted once); the sub-pivot row/column become C,
+    //    the sub-pivot block -P
+    {
+      const int tx = tid % S::TX, ty = tid / S::TX;
+      R u[S::MI][4];
 #pragma unroll
-        for (int c = 0; c < SB; ++c) u = fma(Cp[i * SB + c], Op[j * SB + c], u);
-        w = a[i * LD + j] - u;
+      for (int i = 0; i < S::MI; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) u[i][j] = R(0);
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        R cv[S::MI], ov[4];
+#pragma unroll
+        for (int i = 0; i < S::MI; ++i) cv[i] = Cp[(ty + 16 * i) * SB + c];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ov[j] = Op[c * G + tx + S::TX * j];
+#pragma unroll
+        for (int i = 0; i < S::MI; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) u[i][j] = fma(cv[i], ov[j], u[i][j]);
       }
-      a[i * LD + j] = w;
+      R w[S::MI][4];
+#pragma unroll
+      for (int i = 0; i < S::MI; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int r = ty + 16 * i, c = tx + S::TX * j;
+          const bool ik = r >= K0 && r < K0 + SB, jk = c >= K0 && c < K0 + SB;
+          if (ik && jk) w[i][j] = sp[(r - K0) * (SB + 1) + (c - K0)];
+          else if (jk) w[i][j] = Cp[r * SB + (c - K0)];
+          else if (ik) w[i][j] = Cp[c * SB + (r - K0)];
+          else w[i][j] = a[r * LD + c] - u[i][j];
+        }
+      __syncthreads();   // every read of the old block is done
+#pragma unroll
+      for (int i = 0; i < S::MI; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[(ty + 16 * i) * LD + tx + S::TX * j] = w[i][j];
     }
     __syncthreads();
   }
@@ -335,18 +351,18 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
                                                                      int64_t sCO, double *logdet, int ld_stride,
                                                                      int *status, const int *active) {
   using S = Sweep<G>;
-  const int b = blockIdx.y;
+  const int b = blockIdx.x;   // points fastest: every point's lookahead tile is among the first blocks
   if (active && !active[b]) return;
   const bool look = K + 1 < nt;
   int I, J;
   if (look) {
     const int nxt = (K + 1) * (K + 2) / 2 + (K + 1);   // linear index of tile (K+1, K+1)
-    int x = blockIdx.x;
+    int x = blockIdx.y;
     if (x == 0) x = nxt;
     else if (x <= nxt) x = x - 1;
     tri_index(x, I, J);
   } else {
-    tri_index(blockIdx.x, I, J);
+    tri_index(blockIdx.y, I, J);
   }
   R *dst = A + b * sA + (int64_t)(I * G) * n_p + J * G;
   const R *Cb = Cbuf + b * sCO;
@@ -420,6 +436,161 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
     __syncthreads();
     sweep_tile<R, G>(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * G * G, logdet + (int64_t)b * ld_stride,
                      status + b);
+  }
+}
+
+// FP32 pivot panel (G = 64): C_I = A_IK P for every row tile I != K, split in
+// four 16-row quarters per tile so that a launch has 4 (nt - 1) blocks per
+// point instead of nt - 1 (one 64-row tile per block left most SMs idle).
+// Thread t computes row 16 q + t / 16, columns 4 (t % 16) .. + 3.
+__global__ void __launch_bounds__(256) gj_panel_f32_kernel(const float *A, int64_t sA, int n_p, int K,
+                                                          const float *Pbuf, float *Cbuf, float *Obuf, int64_t sCO,
+                                                          const int *active) {
+  constexpr int G = 64, QR = 16;
+  const int I = blockIdx.x >> 2, q = blockIdx.x & 3, b = blockIdx.y;
+  if (I == K || (active && !active[b])) return;
+  __shared__ __align__(16) float As[QR][G];   // rows 16 q .. 16 q + 15 of A_IK
+  __shared__ __align__(16) float Ps[G][G];    // P (symmetric)
+  const float *Ab = A + b * sA;
+  const int tid = threadIdx.x;
+  if (I > K) {
+    const float *src = Ab + (int64_t)(I * G + QR * q) * n_p + K * G;
+    for (int e = tid; e < QR * G; e += 256) As[e >> 6][e & 63] = src[(int64_t)(e >> 6) * n_p + (e & 63)];
+  } else {  // upper tile (I, K) = transpose of the stored lower tile (K, I)
+    const float *src = Ab + (int64_t)(K * G) * n_p + I * G + QR * q;
+    for (int e = tid; e < QR * G; e += 256) {
+      const int c = e >> 4, r = e & 15;
+      As[r][c] = src[(int64_t)c * n_p + r];
+    }
+  }
+  const float *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G;
+  for (int e = tid; e < G * G / 4; e += 256)
+    reinterpret_cast<float4 *>(&Ps[0][0])[e] = reinterpret_cast<const float4 *>(Pb)[e];
+  __syncthreads();
+  const int r = tid >> 4, c4 = (tid & 15) * 4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+  for (int k = 0; k < G; ++k) {
+    const float a = As[r][k];
+    const float4 pk = *reinterpret_cast<const float4 *>(&Ps[k][c4]);
+    acc.x = fmaf(a, pk.x, acc.x);
+    acc.y = fmaf(a, pk.y, acc.y);
+    acc.z = fmaf(a, pk.z, acc.z);
+    acc.w = fmaf(a, pk.w, acc.w);
+  }
+  const int64_t off = (int64_t)(I * G + QR * q + r) * G + c4;
+  *reinterpret_cast<float4 *>(Cbuf + b * sCO + off) = acc;
+  *reinterpret_cast<float4 *>(Obuf + b * sCO + off) = *reinterpret_cast<const float4 *>(&As[r][c4]);
+}
+
+// FP32 rank-64 update (G = 64): the same tiles and lookahead as
+// gj_update_kernel, with the three 16 KB tiles (C_I, O_J and the old A_IJ)
+// staged by asynchronous 16-byte copies issued together, so that their
+// latencies overlap, and the product read from shared memory four k at a time
+// (rows padded to 68 floats: 16-byte aligned, conflict-free along a quarter
+// warp).  The rank-64 product is summed from zero and subtracted from A_IJ once.
+constexpr int U32_LD = 68;
+constexpr int U32_SMEM = (2 * 64 * U32_LD + 64 * 64) * 4;   // C_I, O_J, old A_IJ
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(256, 3) gj_update_f32_kernel(float *A, int64_t sA, int n_p, int K, int nt,
+                                                           float *Pbuf, const float *Cbuf, const float *Obuf,
+                                                           int64_t sCO, double *logdet, int ld_stride, int *status,
+                                                           const int *active) {
+  constexpr int G = 64;
+  using S = Sweep<G>;
+  const int b = blockIdx.x;   // points fastest: every point's lookahead tile is among the first blocks
+  if (active && !active[b]) return;
+  const bool look = K + 1 < nt;
+  int I, J;
+  if (look) {
+    const int nxt = (K + 1) * (K + 2) / 2 + (K + 1);   // linear index of tile (K+1, K+1)
+    int x = blockIdx.y;
+    if (x == 0) x = nxt;
+    else if (x <= nxt) x = x - 1;
+    tri_index(x, I, J);
+  } else {
+    tri_index(blockIdx.y, I, J);
+  }
+  float *dst = A + b * sA + (int64_t)(I * G) * n_p + J * G;
+  const float *Cb = Cbuf + b * sCO;
+  if (I == K && J == K) {
+    const float *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G;
+    for (int e = threadIdx.x; e < G * G; e += 256) dst[(int64_t)(e >> 6) * n_p + (e & 63)] = -Pb[e];
+    return;
+  }
+  if (J == K) {  // tile (I, K), I > K
+    const float *src = Cb + (int64_t)(I * G) * G;
+    for (int e = threadIdx.x; e < G * G; e += 256) dst[(int64_t)(e >> 6) * n_p + (e & 63)] = src[e];
+    return;
+  }
+  if (I == K) {  // tile (K, J), J < K: transpose of C_J
+    const float *src = Cb + (int64_t)(J * G) * G;
+    for (int e = threadIdx.x; e < G * G; e += 256) {
+      const int c = e >> 6, r = e & 63;
+      dst[(int64_t)r * n_p + c] = src[c * G + r];
+    }
+    return;
+  }
+  extern __shared__ __align__(16) float u32s[];
+  float *Cs = u32s;                 // [64][68]  C_I[r][k]
+  float *Os = Cs + G * U32_LD;      // [64][68]  O_J[c][k]
+  float *Ds = Os + G * U32_LD;      // [64][64]  old A_IJ
+  const float *ci = Cb + (int64_t)(I * G) * G;
+  const float *oj = Obuf + b * sCO + (int64_t)(J * G) * G;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {   // 1024 16-byte chunks per tile, 4 per thread
+    const int q = threadIdx.x + 256 * it, r = q >> 4, c4 = (q & 15) * 4;
+    cp_async16(Cs + r * U32_LD + c4, ci + r * G + c4);
+    cp_async16(Os + r * U32_LD + c4, oj + r * G + c4);
+    cp_async16(Ds + r * G + c4, dst + (int64_t)r * n_p + c4);
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // rows ty + 16 i, columns tx + 16 j
+  float acc[4][4] = {};
+#pragma unroll 4
+  for (int k = 0; k < G; k += 4) {
+    float4 a[4], o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4 *>(Cs + (ty + 16 * i) * U32_LD + k);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = *reinterpret_cast<const float4 *>(Os + (tx + 16 * j) * U32_LD + k);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc[i][j] = fmaf(a[i].x, o[j].x, acc[i][j]);
+        acc[i][j] = fmaf(a[i].y, o[j].y, acc[i][j]);
+        acc[i][j] = fmaf(a[i].z, o[j].z, acc[i][j]);
+        acc[i][j] = fmaf(a[i].w, o[j].w, acc[i][j]);
+      }
+  }
+  const bool next_pivot = look && I == K + 1 && J == K + 1;
+  float out[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[i][j] = Ds[(ty + 16 * i) * G + tx + 16 * j] - acc[i][j];
+  if (next_pivot) __syncthreads();   // the staged tiles are reused as the sweep's workspace
+  float *sm = u32s;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      dst[(int64_t)r * n_p + c] = out[i][j];
+      if (next_pivot && c <= r) sm[r * S::LD + c] = out[i][j];
+    }
+  if (next_pivot) {
+    __syncthreads();
+    sweep_tile<float, G>(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * G * G, logdet + (int64_t)b * ld_stride,
+                         status + b);
   }
 }
 
@@ -619,6 +790,8 @@ void ensure_attrs() {
   cudaFuncSetAttribute(gj_panel_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(2 * 64 * Sweep<64>::LD * sizeof(R)));
   cudaFuncSetAttribute(gj_pivot_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pivot<R, 64>());
+  if (sizeof(R) == 4)
+    cudaFuncSetAttribute(gj_update_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, U32_SMEM);
   done = true;
 }
 
@@ -645,14 +818,25 @@ void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stri
     }
     if (nt > 1) {
       L.start(KID_GJ_PANEL, (double)P * (nt - 1) * unit);
-      gj_panel_kernel<R, G><<<dim3(nt, P), S::THREADS, 2 * G * S::LD * sizeof(R), L.st>>>(
-          A, strideA, n_p, K, Pb, Cb, Ob, sCO, W.active);
+      if (sizeof(R) == 4 && G == 64)
+        gj_panel_f32_kernel<<<dim3(4 * nt, P), 256, 0, L.st>>>(
+            reinterpret_cast<const float *>(A), strideA, n_p, K, reinterpret_cast<const float *>(Pb),
+            reinterpret_cast<float *>(Cb), reinterpret_cast<float *>(Ob), sCO, W.active);
+      else
+        gj_panel_kernel<R, G><<<dim3(nt, P), S::THREADS, 2 * G * S::LD * sizeof(R), L.st>>>(
+            A, strideA, n_p, K, Pb, Cb, Ob, sCO, W.active);
       L.stop();
       L.tick();
     }
-    L.start(KID_GJ_UPDATE, (double)P * (ntri - nt) * unit);
-    gj_update_kernel<R, G><<<dim3(ntri, P), S::THREADS, smem_update<R, G>(), L.st>>>(
-        A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride, W.status, W.active);
+    L.start(sizeof(R) == 4 ? KID_GJ_UPDATE32 : KID_GJ_UPDATE, (double)P * (ntri - nt) * unit);
+    if (sizeof(R) == 4 && G == 64)
+      gj_update_f32_kernel<<<dim3(P, ntri), 256, U32_SMEM, L.st>>>(
+          reinterpret_cast<float *>(A), strideA, n_p, K, nt, reinterpret_cast<float *>(Pb),
+          reinterpret_cast<const float *>(Cb), reinterpret_cast<const float *>(Ob), sCO, logdet_out,
+          logdet_slot_stride, W.status, W.active);
+    else
+      gj_update_kernel<R, G><<<dim3(P, ntri), S::THREADS, smem_update<R, G>(), L.st>>>(
+          A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride, W.status, W.active);
     L.stop();
     L.tick();
   }
