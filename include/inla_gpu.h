@@ -253,6 +253,33 @@ int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *
  * (sizes, NULL or unaligned pointers), INLA_ERR_CUDA. */
 int inla_gemm_tf32x3(int n, int batch, const float *X, const float *Y, float *C, int32_t *status, void *stream);
 
+/* Synthetic workload (host helper, not on the hot path; no counterpart in the
+ * paper): fills *desc with a spatio-temporal SPDE x AR(1) model on an nx x nx
+ * vertex grid of [0,1]^2 (n_s = nx^2; P1 lumped mass C and stiffness G), n_t
+ * time steps, n_b covariates and m observations at uniform random times and
+ * locations (A rows: the 3 barycentric weights of the containing triangle,
+ * then the covariates), simulated at theta_true (HOST [4]; NULL: (1, -1, 0,
+ * 1.5), Poisson (log 1e-3, -1, 0, 1.5)) from a Matern(nu = 1) field with an
+ * AR(1) recursion; lik INLA_LIK_GAUSSIAN (y = A x + noise) or
+ * INLA_LIK_POISSON (y ~ Pois(E exp(A x)), E ~ U(0.5, 2)).  Random numbers are
+ * counter-based SplitMix64 streams keyed by seed, the same as the project's
+ * Python generator.  Every pointer in *desc is a HOST pointer into *owner,
+ * which the caller releases with inla_synth_free (after inla_model_create,
+ * which copies the arrays).  Errors: INLA_ERR_ARG (sizes: n_t >= 1, nx >= 2,
+ * 0 <= n_b <= 16, m >= 1; or a Poisson mean above 700), INLA_ERR_OOM. */
+int inla_synth_build(int32_t n_t, int32_t nx, int32_t n_b, int64_t m, int32_t lik, uint64_t seed,
+                     const double *theta_true, inla_model_desc *desc, void **owner);
+
+/* The five benchmark workloads (cfg_id 1..5): n_t / grid / n_b / m / likelihood =
+ * 8 / 8x8 / 2 / 2000 / Gaussian, 50 / 32x32 / 4 / 100 000 / Gaussian,
+ * 100 / 45x45 / 6 / 400 000 / Gaussian, 200 / 50x50 / 6 / 1 000 000 / Gaussian,
+ * 100 / 64x64 / 8 / 500 000 / Poisson, built by inla_synth_build at the default
+ * theta_true.  Same ownership and errors as inla_synth_build. */
+int inla_synth_grid_model(int32_t cfg_id, uint64_t seed, inla_model_desc *desc, void **owner);
+
+/* Release the arrays of a synthetic workload.  NULL is allowed. */
+void inla_synth_free(void *owner);
+
 /* Free every device resource of the model.  NULL is allowed. */
 void inla_model_destroy(inla_model *model);
 

@@ -232,6 +232,60 @@ def measure_fp32_peak(device=0):
     return v.value
 
 
+class SynthModel:
+    """A synthetic workload built by the library's C generator (inla_synth_build):
+    the model arrays as numpy copies, with the attributes Model() reads."""
+
+    def __init__(self, desc, theta_true, name):
+        n_s, m = desc.n_s, desc.m
+        nnz_g = None
+        self.name = name
+        self.n_t, self.n_b, self.m = desc.n_t, desc.n_b, m
+        self.nx = int(round(n_s ** 0.5))
+        self.lik = "gaussian" if desc.lik == C.INLA_LIK_GAUSSIAN else "poisson"
+        self.tau_b = desc.tau_b
+        arr = np.ctypeslib.as_array
+        self.C_diag = arr(desc.C_diag, (n_s,)).copy()
+        self.G_rowptr = arr(desc.G_rowptr, (n_s + 1,)).copy()
+        nnz_g = int(self.G_rowptr[-1])
+        self.G_col = arr(desc.G_col, (nnz_g,)).copy()
+        self.G_val = arr(desc.G_val, (nnz_g,)).copy()
+        self.A_rowptr = arr(desc.A_rowptr, (m + 1,)).copy()
+        nnz_a = int(self.A_rowptr[-1])
+        self.A_col = arr(desc.A_col, (nnz_a,)).copy()
+        self.A_val = arr(desc.A_val, (nnz_a,)).copy()
+        self.y = arr(desc.y, (m,)).copy()
+        self.E = arr(desc.E, (m,)).copy() if desc.E else None
+        self.prior_mean = np.array(desc.prior_mean[:])
+        self.prior_sd = np.array(desc.prior_sd[:])
+        self.theta_true = np.asarray(theta_true, dtype=float)
+
+    @property
+    def n_s(self):
+        return self.nx * self.nx
+
+    @property
+    def n(self):
+        return self.n_t * self.n_s + self.n_b
+
+
+def synth_build(n_t, nx, n_b, m, lik="gaussian", seed=0, theta_true=None):
+    """Build a synthetic workload with the library's C generator (host code)."""
+    lib = C.load()
+    desc = C.inla_model_desc()
+    owner = c_void_p()
+    liki = C.INLA_LIK_GAUSSIAN if lik == "gaussian" else C.INLA_LIK_POISSON
+    if theta_true is None:
+        theta_true = [1.0, -1.0, 0.0, 1.5] if lik == "gaussian" else [float(np.log(1e-3)), -1.0, 0.0, 1.5]
+    th = (ctypes.c_double * 4)(*theta_true)
+    C.check(lib.inla_synth_build(int(n_t), int(nx), int(n_b), int(m), liki, int(seed),
+                                 ctypes.cast(th, c_void_p), byref(desc), byref(owner)))
+    try:
+        return SynthModel(desc, theta_true, f"synthetic n_t={n_t} {nx}x{nx} n_b={n_b} m={m} {lik}")
+    finally:
+        lib.inla_synth_free(owner)
+
+
 def gemm_tf32x3(X, Y, stream=None):
     """C[b] = X[b] @ Y[b].T on the tensor cores (3xTF32 split product) for CUDA
     float32 tensors X, Y of shape [batch, n, n] (or [n, n]), n a multiple of 128.

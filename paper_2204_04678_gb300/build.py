@@ -14,9 +14,10 @@ CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libinla_gpu.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "probe.cu", "tc_gemm.cu"]
+SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "probe.cu", "tc_gemm.cu",
+           "synth.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE]
 
 
 def _nvcc():
@@ -38,7 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+        o = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
             jobs.append([nvcc, *ARCH, *FLAGS, "-c", s, "-o", o])
 
@@ -52,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OBJDIR, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(OBJDIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
     if jobs or force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + ".tmp"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])

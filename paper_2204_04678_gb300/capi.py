@@ -5,7 +5,7 @@ library.  Loading fails loudly if the library has not been built.
 """
 import ctypes
 import os
-from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
 
 from .build import LIB
 
@@ -83,6 +83,10 @@ SIGNATURES = {
     "inla_measure_fp64_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
     "inla_measure_fp32_peak": (c_int, [c_int, POINTER(c_double)]),
     "inla_gemm_tf32x3": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "inla_synth_build": (c_int, [c_int32, c_int32, c_int32, c_int64, c_int32, c_uint64, c_void_p,
+                                 POINTER(inla_model_desc), POINTER(c_void_p)]),
+    "inla_synth_grid_model": (c_int, [c_int32, c_uint64, POINTER(inla_model_desc), POINTER(c_void_p)]),
+    "inla_synth_free": (None, [c_void_p]),
     "inla_profile_enable": (c_int, [c_void_p, c_int]),
     "inla_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]),
 }
