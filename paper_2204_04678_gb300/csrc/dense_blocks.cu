@@ -20,6 +20,7 @@
 // In FP64 the kernels are bound by the FP64 pipe; all operand traffic is
 // staged through shared memory with conflict-free access (padded rows).
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "inla_internal.cuh"
@@ -439,48 +440,59 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
   }
 }
 
-// FP32 pivot panel (G = 64): C_I = A_IK P for every row tile I != K, split in
-// four 16-row quarters per tile so that a launch has 4 (nt - 1) blocks per
-// point instead of nt - 1 (one 64-row tile per block left most SMs idle).
-// Thread t computes row 16 q + t / 16, columns 4 (t % 16) .. + 3.
-__global__ void __launch_bounds__(256) gj_panel_f32_kernel(const float *A, int64_t sA, int n_p, int K,
-                                                          const float *Pbuf, float *Cbuf, float *Obuf, int64_t sCO,
-                                                          const int *active) {
-  constexpr int G = 64, QR = 16;
+// Pivot panel C_I = A_IK P for every row tile I != K, split in four G/4-row
+// quarters per tile so that a launch has 4 (nt - 1) blocks per point instead
+// of nt - 1 (one tile per block left most SMs idle).  4G threads; thread t
+// computes row (G/4) q + t / 16 and G/16 consecutive columns from 16 (t % 16).
+template <typename R, int G>
+__global__ void __launch_bounds__(4 * G) gj_panel_q_kernel(const R *A, int64_t sA, int n_p, int K, const R *Pbuf,
+                                                          R *Cbuf, R *Obuf, int64_t sCO, const int *active) {
+  constexpr int QR = G / 4, OPT = G / 16, THREADS = 4 * G;
   const int I = blockIdx.x >> 2, q = blockIdx.x & 3, b = blockIdx.y;
   if (I == K || (active && !active[b])) return;
-  __shared__ __align__(16) float As[QR][G];   // rows 16 q .. 16 q + 15 of A_IK
-  __shared__ __align__(16) float Ps[G][G];    // P (symmetric)
-  const float *Ab = A + b * sA;
+  __shared__ __align__(16) R As[QR][G];   // rows QR q .. QR q + QR - 1 of A_IK
+  __shared__ __align__(16) R Ps[G][G];    // P (symmetric)
+  const R *Ab = A + b * sA;
   const int tid = threadIdx.x;
   if (I > K) {
-    const float *src = Ab + (int64_t)(I * G + QR * q) * n_p + K * G;
-    for (int e = tid; e < QR * G; e += 256) As[e >> 6][e & 63] = src[(int64_t)(e >> 6) * n_p + (e & 63)];
+    const R *src = Ab + (int64_t)(I * G + QR * q) * n_p + K * G;
+    for (int e = tid; e < QR * G; e += THREADS) As[e / G][e % G] = src[(int64_t)(e / G) * n_p + (e % G)];
   } else {  // upper tile (I, K) = transpose of the stored lower tile (K, I)
-    const float *src = Ab + (int64_t)(K * G) * n_p + I * G + QR * q;
-    for (int e = tid; e < QR * G; e += 256) {
-      const int c = e >> 4, r = e & 15;
+    const R *src = Ab + (int64_t)(K * G) * n_p + I * G + QR * q;
+    for (int e = tid; e < QR * G; e += THREADS) {
+      const int c = e / QR, r = e % QR;
       As[r][c] = src[(int64_t)c * n_p + r];
     }
   }
-  const float *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G;
-  for (int e = tid; e < G * G / 4; e += 256)
-    reinterpret_cast<float4 *>(&Ps[0][0])[e] = reinterpret_cast<const float4 *>(Pb)[e];
+  const R *Pb = Pbuf + ((int64_t)b * 2 + (K & 1)) * G * G;
+  constexpr int P16 = G * G * (int)sizeof(R) / 16;   // P in 16-byte chunks (slots are 16-byte aligned)
+  for (int e = tid; e < P16; e += THREADS)
+    reinterpret_cast<uint4 *>(&Ps[0][0])[e] = reinterpret_cast<const uint4 *>(Pb)[e];
   __syncthreads();
-  const int r = tid >> 4, c4 = (tid & 15) * 4;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int r = tid / 16, c0 = (tid % 16) * OPT;
+  R acc[OPT];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) acc[o] = R(0);
 #pragma unroll 8
   for (int k = 0; k < G; ++k) {
-    const float a = As[r][k];
-    const float4 pk = *reinterpret_cast<const float4 *>(&Ps[k][c4]);
-    acc.x = fmaf(a, pk.x, acc.x);
-    acc.y = fmaf(a, pk.y, acc.y);
-    acc.z = fmaf(a, pk.z, acc.z);
-    acc.w = fmaf(a, pk.w, acc.w);
+    const R a = As[r][k];
+    R pk[OPT];
+    if constexpr (OPT * sizeof(R) == 16) {   // one 16-byte shared-memory read (the configurations in use)
+      const uint4 u = *reinterpret_cast<const uint4 *>(&Ps[k][c0]);
+      memcpy(pk, &u, 16);
+    } else {
+#pragma unroll
+      for (int o = 0; o < OPT; ++o) pk[o] = Ps[k][c0 + o];
+    }
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) acc[o] = fma(a, pk[o], acc[o]);
   }
-  const int64_t off = (int64_t)(I * G + QR * q + r) * G + c4;
-  *reinterpret_cast<float4 *>(Cbuf + b * sCO + off) = acc;
-  *reinterpret_cast<float4 *>(Obuf + b * sCO + off) = *reinterpret_cast<const float4 *>(&As[r][c4]);
+  const int64_t off = (int64_t)(I * G + QR * q + r) * G + c0;
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    Cbuf[b * sCO + off + o] = acc[o];
+    Obuf[b * sCO + off + o] = As[r][c0 + o];
+  }
 }
 
 // FP32 rank-64 update (G = 64): the same tiles and lookahead as
@@ -818,13 +830,12 @@ void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stri
     }
     if (nt > 1) {
       L.start(KID_GJ_PANEL, (double)P * (nt - 1) * unit);
-      if (sizeof(R) == 4 && G == 64)
-        gj_panel_f32_kernel<<<dim3(4 * nt, P), 256, 0, L.st>>>(
-            reinterpret_cast<const float *>(A), strideA, n_p, K, reinterpret_cast<const float *>(Pb),
-            reinterpret_cast<float *>(Cb), reinterpret_cast<float *>(Ob), sCO, W.active);
-      else
+      if (sizeof(R) == 8 && G == 64)   // 2 x 32 KB of static shared memory would exceed the limit
         gj_panel_kernel<R, G><<<dim3(nt, P), S::THREADS, 2 * G * S::LD * sizeof(R), L.st>>>(
             A, strideA, n_p, K, Pb, Cb, Ob, sCO, W.active);
+      else
+        gj_panel_q_kernel<R, G><<<dim3(4 * nt, P), 4 * G, 0, L.st>>>(A, strideA, n_p, K, Pb, Cb, Ob, sCO,
+                                                                     W.active);
       L.stop();
       L.tick();
     }
