@@ -64,7 +64,11 @@ typedef enum {
   INLA_ERR_UNSUPPORTED = 7      /* option not available in this build          */
 } inla_status;
 
-enum { INLA_LIK_GAUSSIAN = 0, INLA_LIK_POISSON = 1 };
+/* Likelihoods (canonical links): Gaussian y ~ N(eta, 1/tau_y); Poisson
+ * y ~ Pois(E exp(eta)); binomial y ~ Bin(N, 1 / (1 + exp(-eta))) with the
+ * number of trials N in the E array.  The non-Gaussian ones are handled by
+ * the Laplace approximation with a Newton inner loop (Sec. 2.2). */
+enum { INLA_LIK_GAUSSIAN = 0, INLA_LIK_POISSON = 1, INLA_LIK_BINOMIAL = 2 };
 enum { INLA_GRAD_NONE = 0, INLA_GRAD_FD_CENTRAL = 1, INLA_GRAD_ADJOINT = 2 };
 /* How log|Q| and tr(Q^-1 dQ) of the prior are obtained.  KRONECKER uses
  * log|Q_t (x) Q_s| = n_s log|Q_t| + n_t log|Q_s| with one dense n_s x n_s
@@ -92,7 +96,7 @@ typedef struct {
   int32_t n_t;            /* number of time steps (>= 1)                          */
   int32_t n_s;            /* number of mesh vertices (>= 1)                       */
   int32_t n_b;            /* number of fixed effects (>= 0)                       */
-  int32_t lik;            /* INLA_LIK_GAUSSIAN or INLA_LIK_POISSON                */
+  int32_t lik;            /* INLA_LIK_GAUSSIAN, _POISSON or _BINOMIAL             */
   int64_t m;              /* number of observations (>= 1)                        */
   const double *C_diag;   /* [n_s] lumped mass matrix C (all > 0)                 */
   const int32_t *G_rowptr;/* [n_s+1] CSR row pointers of the stiffness matrix G   */
@@ -103,9 +107,12 @@ typedef struct {
                           /* one time block [t n_s, (t+1) n_s) and any number of   */
                           /* fixed-effect entries in [n_t n_s, n)                   */
   const double *A_val;    /* values                                                */
-  const double *y;        /* [m] observations (Poisson: non-negative integers)     */
-  const double *E;        /* [m] exposures (Poisson, > 0); NULL for Gaussian       */
-  double tau_b;           /* fixed-effect prior precision (Gaussian; > 0)          */
+  const double *y;        /* [m] observations (Poisson: non-negative integers;     */
+                          /* binomial: integers 0 <= y <= N)                       */
+  const double *E;        /* [m] Poisson: exposures (> 0); binomial: numbers of    */
+                          /* trials N (positive integers); NULL for Gaussian        */
+  double tau_b;           /* fixed-effect prior precision (Gaussian; > 0; the      */
+                          /* other likelihoods take tau_b = exp(theta_1))          */
   double prior_mean[4];   /* hyperprior: theta_j ~ N(prior_mean[j], prior_sd[j]^2) */
   double prior_sd[4];
 } inla_model_desc;

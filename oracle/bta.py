@@ -257,16 +257,18 @@ def gaussian(model, theta, want_grad=False, want_var=False):
 
 
 def poisson_mode(model, theta, tol=1e-8, max_iter=50):
-    """Newton iteration for x*(theta) (Sec. 2.2) with BTA factorisations."""
+    """Newton iteration for x*(theta) (Sec. 2.2) with BTA factorisations, for a
+    non-Gaussian likelihood (D = diag(weight), right-hand side
+    A^T (y - mean + D eta), both from glm_terms)."""
     A = M.obs_matrix(model)
     Q = M.prior_Q(model, theta)
     x = np.zeros(model.n)
     for k in range(1, max_iter + 1):
         eta = A @ x
-        mu = model.E * np.exp(eta)
-        Qc = (Q + A.T @ sp.diags(mu) @ A).tocsr()
+        mean, wgt, _ = M.glm_terms(model, eta)
+        Qc = (Q + A.T @ sp.diags(wgt) @ A).tocsr()
         L, _ = cholesky(_blocks(model, Qc))
-        xn = solve(L, A.T @ (model.y - mu + mu * eta))
+        xn = solve(L, A.T @ (model.y - mean + wgt * eta))
         step = float(np.linalg.norm(xn - x))
         x = xn
         if step < tol:
@@ -275,24 +277,26 @@ def poisson_mode(model, theta, tol=1e-8, max_iter=50):
 
 
 def poisson(model, theta, want_grad=False, want_var=False, tol=1e-8, max_iter=50):
-    """Laplace f for the Poisson likelihood; Q_c is refactorised at the mode."""
+    """Laplace f for a non-Gaussian likelihood; Q_c is refactorised at the mode.
+    The adjoint gradient adds -lambda^T dQ x* with Q_c lambda = A^T w,
+    w_i = 1/2 (a_i^T Sigma_c a_i) times the derivative of the weight at eta_i."""
     A = M.obs_matrix(model)
     Q = M.prior_Q(model, theta)
     x, iters, ok = poisson_mode(model, theta, tol, max_iter)
     eta = A @ x
-    mu = model.E * np.exp(eta)
-    Qc = (Q + A.T @ sp.diags(mu) @ A).tocsr()
+    _, wgt, third = M.glm_terms(model, eta)
+    Qc = (Q + A.T @ sp.diags(wgt) @ A).tocsr()
     LQ, logdetQ = cholesky(_blocks(model, Q))
     LQc, logdetQc = cholesky(_blocks(model, Qc))
     f = (-M.log_prior(model, theta) - 0.5 * logdetQ + 0.5 * float(x @ (Q @ x))
-         - M.poisson_loglik(model, eta) + 0.5 * logdetQc)
+         - M.glm_loglik(model, eta) + 0.5 * logdetQc)
     out = dict(f=float(f), x=x, logdetQ=logdetQ, logdetQc=logdetQc, iters=iters, converged=ok)
     if want_var or want_grad:
         SQc = selinv(LQc)
         out["var"] = diag_of(SQc)
     if want_grad:
         SQ = selinv(LQ)
-        w = 0.5 * quad_forms_on_pattern(SQc, model, A) * mu
+        w = 0.5 * quad_forms_on_pattern(SQc, model, A) * third
         lam = solve(LQc, A.T @ w)
         dlp = M.dlog_prior(model, theta)
         g = np.zeros(4)

@@ -59,20 +59,20 @@ def gaussian_closed_form(model, theta):
 
 
 def poisson_mode(model, theta, tol=1e-8, max_iter=50, x0=None):
-    """Newton iteration for the mode of pi(x | theta, y), Poisson likelihood.
+    """Newton iteration for the mode of pi(x | theta, y), non-Gaussian likelihood.
 
-    x^{k+1} solves (Q + A^T D A) x = A^T (y - E e^eta + D eta) with
-    eta = A x^k and D = diag(E e^eta); stop when ||x^{k+1} - x^k||_2 < tol.
-    Returns (x*, iterations, converged).
+    x^{k+1} solves (Q + A^T D A) x = A^T (y - b1 + D eta) with eta = A x^k,
+    b1 = the mean and D = diag(weight) from glm_terms (Poisson: both E e^eta);
+    stop when ||x^{k+1} - x^k||_2 < tol.  Returns (x*, iterations, converged).
     """
     Q = M.prior_Q(model, theta).toarray()
     A = M.obs_matrix(model)
     x = np.zeros(model.n) if x0 is None else np.array(x0, dtype=float)
     for k in range(1, max_iter + 1):
         eta = A @ x
-        mu = model.E * np.exp(eta)
-        Qc = Q + (A.T @ (A.multiply(mu[:, None]))).toarray()
-        rhs = A.T @ (model.y - mu + mu * eta)
+        mean, wgt, _ = M.glm_terms(model, eta)
+        Qc = Q + (A.T @ (A.multiply(wgt[:, None]))).toarray()
+        rhs = A.T @ (model.y - mean + wgt * eta)
         xn = sla.cho_solve((np.linalg.cholesky(Qc), True), rhs)
         step = float(np.linalg.norm(xn - x))
         x = xn
@@ -82,17 +82,17 @@ def poisson_mode(model, theta, tol=1e-8, max_iter=50, x0=None):
 
 
 def poisson_eval(model, theta, want_var=True, tol=1e-8, max_iter=50):
-    """Laplace f(theta) for the Poisson likelihood, Q_c refactorised at x*."""
+    """Laplace f(theta) for a non-Gaussian likelihood, Q_c refactorised at x*."""
     Q = M.prior_Q(model, theta).toarray()
     A = M.obs_matrix(model)
     x, iters, ok = poisson_mode(model, theta, tol, max_iter)
     eta = A @ x
-    mu = model.E * np.exp(eta)
-    Qc = Q + (A.T @ (A.multiply(mu[:, None]))).toarray()
+    _, wgt, _ = M.glm_terms(model, eta)
+    Qc = Q + (A.T @ (A.multiply(wgt[:, None]))).toarray()
     _, logdetQ = chol_logdet(Q)
     Lc, logdetQc = chol_logdet(Qc)
     f = (-M.log_prior(model, theta) - 0.5 * logdetQ + 0.5 * x @ Q @ x
-         - M.poisson_loglik(model, eta) + 0.5 * logdetQc)
+         - M.glm_loglik(model, eta) + 0.5 * logdetQc)
     out = dict(f=float(f), x=x, logdetQ=logdetQ, logdetQc=logdetQc, iters=iters, converged=ok)
     if want_var:
         out["var"] = np.diag(sla.cho_solve((Lc, True), np.eye(model.n))).copy()

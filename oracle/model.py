@@ -97,6 +97,36 @@ def poisson_loglik(model, eta):
     return float(np.sum(y * (np.log(E) + eta) - E * np.exp(eta) - gammaln(y + 1.0)))
 
 
+def binomial_loglik(model, eta):
+    """sum_i [log C(N_i, y_i) + y_i log p_i + (N_i - y_i) log(1 - p_i)], p = logistic(eta),
+    N = the numbers of trials (held in model.E)."""
+    from scipy.special import gammaln
+    y, N = model.y, model.E
+    logC = gammaln(N + 1.0) - gammaln(y + 1.0) - gammaln(N - y + 1.0)
+    # log p = -log(1 + e^-eta), log(1 - p) = -log(1 + e^eta)
+    return float(np.sum(logC - y * np.logaddexp(0.0, -eta) - (N - y) * np.logaddexp(0.0, eta)))
+
+
+def glm_loglik(model, eta):
+    """log p(y | eta) of a non-Gaussian likelihood (Poisson or binomial)."""
+    return poisson_loglik(model, eta) if model.lik == "poisson" else binomial_loglik(model, eta)
+
+
+def glm_terms(model, eta):
+    """First, second and third derivatives of b, where log p(y | eta) =
+    y eta - b(eta) + const (canonical link): Poisson b = E e^eta, binomial
+    b = N log(1 + e^eta).  They are the mean, the Newton weight D and the
+    derivative of D (for the adjoint gradient)."""
+    eta = np.asarray(eta, dtype=float)
+    if model.lik == "poisson":
+        mu = model.E * np.exp(eta)
+        return mu, mu, mu
+    p = 1.0 / (1.0 + np.exp(-eta))
+    q = 1.0 / (1.0 + np.exp(eta))
+    N = model.E
+    return N * p, N * p * q, N * p * q * (q - p)
+
+
 def dQ_dtheta(model, theta, j):
     """dQ/dtheta_j as a sparse matrix, differentiating the formulas above.
 

@@ -43,7 +43,8 @@ class Model:
 
     ``data`` provides n_t, n_s, n_b, m, lik ('gaussian' / 'poisson'), C_diag,
     G (CSR: G_rowptr, G_col, G_val), A (CSR: A_rowptr int64, A_col, A_val),
-    y, E (Poisson), tau_b, prior_mean[4], prior_sd[4] (e.g. ``synth.GridModel``).
+    y, E (Poisson exposures / binomial trials), tau_b, prior_mean[4], prior_sd[4]
+    (e.g. ``synth.GridModel``); lik is "gaussian", "poisson" or "binomial".
     """
 
     def __init__(self, data, device: int = 0):
@@ -54,7 +55,8 @@ class Model:
                     Av=arr(data.A_val, np.float64), y=arr(data.y, np.float64))
         d = C.inla_model_desc()
         d.n_t, d.n_s, d.n_b, d.m = int(data.n_t), int(data.n_s), int(data.n_b), int(data.m)
-        d.lik = C.INLA_LIK_GAUSSIAN if data.lik == "gaussian" else C.INLA_LIK_POISSON
+        d.lik = {"gaussian": C.INLA_LIK_GAUSSIAN, "poisson": C.INLA_LIK_POISSON,
+                 "binomial": C.INLA_LIK_BINOMIAL}[data.lik]
         d.C_diag = _ptr(keep["C"], c_double)
         d.G_rowptr = _ptr(keep["Gr"], ctypes.c_int32)
         d.G_col = _ptr(keep["Gc"], ctypes.c_int32)
@@ -242,7 +244,8 @@ class SynthModel:
         self.name = name
         self.n_t, self.n_b, self.m = desc.n_t, desc.n_b, m
         self.nx = int(round(n_s ** 0.5))
-        self.lik = "gaussian" if desc.lik == C.INLA_LIK_GAUSSIAN else "poisson"
+        self.lik = {C.INLA_LIK_GAUSSIAN: "gaussian", C.INLA_LIK_POISSON: "poisson",
+                    C.INLA_LIK_BINOMIAL: "binomial"}[desc.lik]
         self.tau_b = desc.tau_b
         arr = np.ctypeslib.as_array
         self.C_diag = arr(desc.C_diag, (n_s,)).copy()
@@ -274,7 +277,7 @@ def synth_build(n_t, nx, n_b, m, lik="gaussian", seed=0, theta_true=None):
     lib = C.load()
     desc = C.inla_model_desc()
     owner = c_void_p()
-    liki = C.INLA_LIK_GAUSSIAN if lik == "gaussian" else C.INLA_LIK_POISSON
+    liki = {"gaussian": C.INLA_LIK_GAUSSIAN, "poisson": C.INLA_LIK_POISSON, "binomial": C.INLA_LIK_BINOMIAL}[lik]
     if theta_true is None:
         theta_true = [1.0, -1.0, 0.0, 1.5] if lik == "gaussian" else [float(np.log(1e-3)), -1.0, 0.0, 1.5]
     th = (ctypes.c_double * 4)(*theta_true)

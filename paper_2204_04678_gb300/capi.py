@@ -19,6 +19,7 @@ INLA_ERR_TIMEOUT = 6
 INLA_ERR_UNSUPPORTED = 7
 INLA_LIK_GAUSSIAN = 0
 INLA_LIK_POISSON = 1
+INLA_LIK_BINOMIAL = 2
 INLA_GRAD_NONE = 0
 INLA_GRAD_FD_CENTRAL = 1
 INLA_GRAD_ADJOINT = 2

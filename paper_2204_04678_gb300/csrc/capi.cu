@@ -147,10 +147,12 @@ void validate(const inla_model_desc *d) {
   if (d->n_t < 1 || d->n_s < 1) bad("n_t and n_s must be >= 1");
   if (d->n_b < 0 || d->n_b > MAX_NB) bad("n_b must be in [0, 16]");
   if (d->m < 1 || d->m > (int64_t)INT32_MAX) bad("m must be in [1, 2^31)");
-  if (d->lik != INLA_LIK_GAUSSIAN && d->lik != INLA_LIK_POISSON) bad("unknown likelihood");
+  if (d->lik != INLA_LIK_GAUSSIAN && d->lik != INLA_LIK_POISSON && d->lik != INLA_LIK_BINOMIAL)
+    bad("unknown likelihood");
   if (!d->C_diag || !d->G_rowptr || !d->G_col || !d->G_val || !d->A_rowptr || !d->A_col || !d->A_val || !d->y)
     bad("a required array is NULL");
   if (d->lik == INLA_LIK_POISSON && !d->E) bad("Poisson likelihood needs exposures E");
+  if (d->lik == INLA_LIK_BINOMIAL && !d->E) bad("binomial likelihood needs the numbers of trials in E");
   if (d->lik == INLA_LIK_GAUSSIAN && !(d->tau_b > 0.0)) bad("tau_b must be > 0");
   for (int j = 0; j < 4; ++j)
     if (!(d->prior_sd[j] > 0.0) || !std::isfinite(d->prior_mean[j])) bad("hyperprior sd must be > 0");
@@ -188,6 +190,12 @@ void validate(const inla_model_desc *d) {
     if (d->lik == INLA_LIK_POISSON) {
       if (!(d->E[r] > 0.0) || !std::isfinite(d->E[r])) bad("E must be positive");
       if (d->y[r] < 0.0 || d->y[r] != std::floor(d->y[r])) bad("Poisson y must be non-negative integers");
+    }
+    if (d->lik == INLA_LIK_BINOMIAL) {
+      if (!(d->E[r] >= 1.0) || d->E[r] != std::floor(d->E[r]) || d->E[r] > 1e9)
+        bad("binomial numbers of trials must be positive integers");
+      if (d->y[r] < 0.0 || d->y[r] > d->E[r] || d->y[r] != std::floor(d->y[r]))
+        bad("binomial y must be integers in [0, N]");
     }
   }
 }
@@ -237,7 +245,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     for (int64_t r = 0; r < m; ++r) perm[fill[ot[r]]++] = r;
     std::vector<int> s_t(m), s_v(m * MAX_SPATIAL);
     std::vector<double> s_w(m * MAX_SPATIAL), s_z(m * (int64_t)n_b), s_y(m), s_E;
-    if (d->lik == INLA_LIK_POISSON) s_E.resize(m);
+    if (d->lik != INLA_LIK_GAUSSIAN) s_E.resize(m);
     for (int64_t k = 0; k < m; ++k) {
       const int64_t r = perm[k];
       s_t[k] = ot[r];
@@ -450,7 +458,7 @@ Sizes sizes_of(const DevModel &M) {  // element counts per point
   s.part = NPART * PART_W;
   s.tippart = rup((int64_t)M.n_t * (nb * nb + nb), 32) + 32;
   s.ints = 32;
-  if (M.lik == INLA_LIK_POISSON) {
+  if (M.lik != INLA_LIK_GAUSSIAN) {
     s.m = rup(M.m, 32);
     s.AtAp = rup((int64_t)M.n_t * M.nnz, 32);
     s.Arwp = rup((int64_t)M.n_t * nb * M.n_s, 32) + 32;
@@ -463,7 +471,7 @@ int64_t point_bytes(const DevModel &M, int rb) {
   const Sizes s = sizes_of(M);
   int64_t d = s.theta + s.prm + s.qs + s.Rt + 2 * s.Da + 7 * s.vec + s.wv + 3 * s.nbnp + s.sc + s.pt + s.part +
               s.tippart + 4 * s.ints + 1;
-  if (M.lik == INLA_LIK_POISSON) d += 4 * s.m + s.AtAp + s.Arwp;
+  if (M.lik != INLA_LIK_GAUSSIAN) d += 4 * s.m + s.AtAp + s.Arwp;
   d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
   const int64_t dense = s.Dinv + 4 * s.mat;
   return d * 8 + rup(dense * rb, 256) + 64 * 256;   // slack: each array starts on 256 bytes
@@ -508,7 +516,7 @@ Work carve(const DevModel &M, void *base, int Pw, int rb) {
   W.flags = reinterpret_cast<int *>(take(s.ints));
   W.iters = reinterpret_cast<int *>(take(s.ints));
   W.any_active = reinterpret_cast<int *>(take(1));
-  if (M.lik == INLA_LIK_POISSON) {
+  if (M.lik != INLA_LIK_GAUSSIAN) {
     W.eta = take(s.m); W.mu = take(s.m); W.qobs = take(s.m); W.wobs = take(s.m); W.sM = s.m;
     W.AtAp = take(s.AtAp); W.sAtAp = s.AtAp;
     W.Arwp = take(s.Arwp); W.sArwp = s.Arwp;

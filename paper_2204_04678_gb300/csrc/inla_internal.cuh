@@ -109,7 +109,7 @@ struct Work {
   int *iters;            // [P]
   int *any_active;       // [1]
   // Poisson
-  double *eta, *mu, *qobs, *wobs;        // [P][m]
+  double *eta, *mu, *qobs, *wobs;        // [P][m] eta, weight b''(eta), a_i^T Sigma a_i, adjoint weights
   double *AtAp;          // [P][n_t][nnz]
   double *Arwp;          // [P][n_t][n_b][n_s]
   double *Tipp;          // [P][n_b][n_b]
@@ -186,6 +186,30 @@ struct Launch {
     cur_id = -1;
   }
 };
+
+// Canonical-link likelihood terms per observation: y eta - b(eta) is the
+// log-likelihood up to constants, b' the mean, b'' the Newton weight and b''' the
+// derivative of the weight (adjoint gradient).  Poisson: b = E exp(eta) (all
+// three derivatives equal b); binomial: b = N log(1 + exp(eta)), p = logistic(eta),
+// b' = N p, b'' = N p (1 - p), b''' = N p (1 - p) (1 - 2 p).
+struct GlmTerms {
+  double b, mean, weight, third;
+};
+__device__ __forceinline__ GlmTerms glm_terms(int lik, double E, double eta) {
+  GlmTerms g;
+  if (lik == INLA_LIK_BINOMIAL) {
+    const double p = 1.0 / (1.0 + exp(-eta));
+    const double q = 1.0 / (1.0 + exp(eta));   // 1 - p without cancellation
+    g.b = E * (eta > 0.0 ? eta + log1p(exp(-eta)) : log1p(exp(eta)));
+    g.mean = E * p;
+    g.weight = E * p * q;
+    g.third = g.weight * (q - p);
+  } else {
+    const double mu = E * exp(eta);
+    g.b = g.mean = g.weight = g.third = mu;
+  }
+  return g;
+}
 
 // dense_blocks.cu (R = double or float)
 void dense_prepare();   // one-time kernel attributes (call before a stream capture)

@@ -134,7 +134,8 @@ void grid_fem(int nx, Owner &o) {
 
 void build(int n_t, int nx, int n_b, int64_t m, int lik, uint64_t seed, const double theta[4], double tau_b,
            inla_model_desc *d, Owner &o) {
-  if (n_t < 1 || nx < 2 || n_b < 0 || n_b > inla::MAX_NB || m < 1 || (lik != INLA_LIK_GAUSSIAN && lik != INLA_LIK_POISSON))
+  if (n_t < 1 || nx < 2 || n_b < 0 || n_b > inla::MAX_NB || m < 1 ||
+      (lik != INLA_LIK_GAUSSIAN && lik != INLA_LIK_POISSON && lik != INLA_LIK_BINOMIAL))
     throw std::invalid_argument("invalid sizes or likelihood");
   const int n_s = nx * nx;
   grid_fem(nx, o);
@@ -212,8 +213,8 @@ void build(int n_t, int nx, int n_b, int64_t m, int lik, uint64_t seed, const do
     prev.swap(cur);
   }
   std::vector<double> beta = s_beta.normal(n_b);
-  if (lik == INLA_LIK_POISSON)
-    for (double &b : beta) b *= 0.1;
+  if (lik != INLA_LIK_GAUSSIAN)
+    for (double &b : beta) b *= 0.1;   // Poisson and binomial
   std::vector<double> eta(m);
   for (int64_t r = 0; r < m; ++r) {
     double s = 0.0;
@@ -227,6 +228,23 @@ void build(int n_t, int nx, int n_b, int64_t m, int lik, uint64_t seed, const do
     const double tau_y = std::exp(theta[0]);
     const std::vector<double> e = s_noise.normal(m);
     for (int64_t r = 0; r < m; ++r) o.y[r] = eta[r] + e[r] / std::sqrt(tau_y);
+  } else if (lik == INLA_LIK_BINOMIAL) {
+    // N ~ 1 + U{0..9} trials, y ~ Bin(N, logistic(eta)) by inversion (one uniform each)
+    o.E.resize(m);
+    for (int64_t r = 0; r < m; ++r) o.E[r] = (double)(1 + s_exp.integer(10));
+    for (int64_t r = 0; r < m; ++r) {
+      const int64_t n = (int64_t)o.E[r];
+      const double p = 1.0 / (1.0 + std::exp(-eta[r])), q = 1.0 - p;
+      const double u = s_noise.uniform();
+      int64_t k = 0;
+      double pk = std::pow(q, (double)n), cdf = pk;
+      while (u > cdf && k < n) {
+        pk *= (double)(n - k) / ((double)k + 1.0) * (p / q);
+        ++k;
+        cdf += pk;
+      }
+      o.y[r] = (double)k;
+    }
   } else {
     o.E.resize(m);
     for (int64_t r = 0; r < m; ++r) o.E[r] = 0.5 + 1.5 * s_exp.uniform();
@@ -258,13 +276,13 @@ void build(int n_t, int nx, int n_b, int64_t m, int lik, uint64_t seed, const do
   d->A_col = o.A_col.data();
   d->A_val = o.A_val.data();
   d->y = o.y.data();
-  d->E = lik == INLA_LIK_POISSON ? o.E.data() : nullptr;
+  d->E = lik != INLA_LIK_GAUSSIAN ? o.E.data() : nullptr;
   d->tau_b = tau_b;
   for (int j = 0; j < 4; ++j) {
     d->prior_mean[j] = 0.0;
     d->prior_sd[j] = 10.0;
   }
-  if (lik == INLA_LIK_POISSON) d->prior_mean[0] = std::log(1e-3);
+  if (lik != INLA_LIK_GAUSSIAN) d->prior_mean[0] = std::log(1e-3);
 }
 
 }  // namespace
@@ -278,7 +296,7 @@ extern "C" int inla_synth_build(int32_t n_t, int32_t nx, int32_t n_b, int64_t m,
   *owner = nullptr;
   const double gauss[4] = {1.0, -1.0, 0.0, 1.5};
   const double pois[4] = {std::log(1e-3), -1.0, 0.0, 1.5};
-  const double *th = theta_true ? theta_true : (lik == INLA_LIK_POISSON ? pois : gauss);
+  const double *th = theta_true ? theta_true : (lik != INLA_LIK_GAUSSIAN ? pois : gauss);
   try {
     std::unique_ptr<Owner> o(new Owner);
     build(n_t, nx, n_b, m, lik, seed, th, 1e-3, desc, *o);

@@ -15,8 +15,8 @@ random Fourier features and an AR(1) recursion in time, not from any
 precision matrix the method assembles.
 
 Substream ids (seed 0 unless stated): 0 observation times, 1 observation
-locations, 2 covariates, 3 field, 4 beta, 5 noise / Poisson draws,
-6 exposure, 7 hyperparameter batch.
+locations, 2 covariates, 3 field, 4 beta, 5 noise / Poisson / binomial
+draws, 6 exposure / numbers of trials (1..10), 7 hyperparameter batch.
 """
 from dataclasses import dataclass, field
 import numpy as np
@@ -36,7 +36,7 @@ class GridModel:
     nx: int
     n_b: int
     m: int
-    lik: str                      # "gaussian" or "poisson"
+    lik: str                      # "gaussian", "poisson" or "binomial"
     tau_b: float                  # fixed-effect prior precision (Gaussian)
     C_diag: np.ndarray            # [n_s] lumped mass
     G_rowptr: np.ndarray          # CSR of the n_s x n_s stiffness matrix,
@@ -46,7 +46,7 @@ class GridModel:
     A_col: np.ndarray             # int32 column indices
     A_val: np.ndarray
     y: np.ndarray                 # [m]
-    E: np.ndarray = None          # [m] exposure (Poisson only)
+    E: np.ndarray = None          # [m] exposure (Poisson) / number of trials (binomial)
     prior_mean: np.ndarray = field(default_factory=lambda: np.zeros(4))
     prior_sd: np.ndarray = field(default_factory=lambda: np.full(4, 10.0))
     obs_t: np.ndarray = None      # [m] time slice of each observation
@@ -172,7 +172,7 @@ def matern_field(stream: Stream, nx: int, n_t: int, range_: float, sigma: float,
 def build(name: str, n_t: int, nx: int, n_b: int, m: int, lik: str = "gaussian", seed: int = 0,
           theta_true=None, tau_b: float = 1e-3) -> GridModel:
     """Build one workload.  See the module docstring for the recipe."""
-    if lik not in ("gaussian", "poisson"):
+    if lik not in ("gaussian", "poisson", "binomial"):
         raise ValueError(lik)
     theta_true = np.array(theta_true if theta_true is not None else
                           (THETA_TRUE_GAUSSIAN if lik == "gaussian" else THETA_TRUE_POISSON), dtype=float)
@@ -207,9 +207,14 @@ def build(name: str, n_t: int, nx: int, n_b: int, m: int, lik: str = "gaussian",
         tau_y = np.exp(theta_true[0])
         y = eta + s_noise.normal(m) / np.sqrt(tau_y)
         prior_mean = np.zeros(4)
-    else:
+    elif lik == "poisson":
         E = 0.5 + 1.5 * s_exp.uniform(m)
         y = s_noise.poisson(E * np.exp(eta)).astype(np.float64)
+        prior_mean = np.array([np.log(1e-3), 0.0, 0.0, 0.0])
+    else:
+        trials = 1 + s_exp.integers(m, 10)
+        E = trials.astype(np.float64)
+        y = s_noise.binomial(trials, 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
         prior_mean = np.array([np.log(1e-3), 0.0, 0.0, 0.0])
     return GridModel(name=name, n_t=n_t, nx=nx, n_b=n_b, m=m, lik=lik, tau_b=tau_b,
                      C_diag=C, G_rowptr=G_rowptr, G_col=G_col, G_val=G_val,

@@ -11,7 +11,8 @@ and every numpy version.
 Doubles in [0, 1) take the top 53 bits of an output.  Normals use the
 Box-Muller transform.  Poisson counts use sequential-search inversion of
 the cumulative distribution (Devroye, "Non-Uniform Random Variate
-Generation", 1986, Sec. X.3.3), vectorised over the array.
+Generation", 1986, Sec. X.3.3), vectorised over the array; binomial counts
+by the same inversion with the ratio of successive probabilities.
 
 This module only draws numbers; it holds none of the INLA method.
 """
@@ -96,4 +97,22 @@ class Stream:
             cdf[idx] += p[idx]
             # stop when the cdf passes u, or when the tail has vanished in rounding
             active[idx] = (u[idx] > cdf[idx]) & (p[idx] > 0.0)
+        return k
+
+    def binomial(self, trials: np.ndarray, p: np.ndarray) -> np.ndarray:
+        """Binomial counts Bin(trials, p) by CDF inversion, one uniform each."""
+        n = np.asarray(trials, dtype=np.int64)
+        p = np.asarray(p, dtype=np.float64)
+        q = 1.0 - p
+        u = self.uniform(n.size)
+        k = np.zeros(n.size, dtype=np.int64)
+        pk = q ** n
+        cdf = pk.copy()
+        active = (u > cdf) & (k < n)
+        while np.any(active):
+            idx = np.nonzero(active)[0]
+            pk[idx] *= (n[idx] - k[idx]) / (k[idx] + 1.0) * (p[idx] / q[idx])
+            k[idx] += 1
+            cdf[idx] += pk[idx]
+            active[idx] = (u[idx] > cdf[idx]) & (k[idx] < n[idx])
         return k

@@ -78,6 +78,14 @@ def _desc(mdl, keep):
     return d
 
 
+def _binomial(d, m, trials=2.0, y=None):
+    # a binomial description with N = trials everywhere (and y overridden)
+    d.lik = C.INLA_LIK_BINOMIAL
+    m.E = np.full(m.m, float(trials))
+    m.y[:] = np.minimum(np.abs(np.round(m.y)), 2.0) if y is None else y
+    d.E = m.E.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
 def _split_row(m):
     # move the last spatial entry of a row into the next time block (columns stay sorted)
     r = int(np.nonzero(m.obs_t < m.n_t - 1)[0][0])
@@ -93,6 +101,10 @@ def _split_row(m):
     (lambda d, m: m.A_col.__setitem__(0, 10 ** 6), "out of range"),
     (lambda d, m: m.C_diag.__setitem__(3, 0.0), "C_diag"),
     (lambda d, m: _split_row(m), "one time block"),
+    (lambda d, m: setattr(d, "lik", 3), "unknown likelihood"),
+    (lambda d, m: setattr(d, "lik", C.INLA_LIK_BINOMIAL), "trials"),
+    (lambda d, m: _binomial(d, m, trials=2.5), "positive integers"),
+    (lambda d, m: _binomial(d, m, y=3.0), "[0, N]"),
 ])
 def test_invalid_descriptions_are_rejected_before_any_device_work(lib, mutate, needle):
     mdl = build("t", 3, 4, 2, 50)

@@ -75,9 +75,11 @@ def test_gaussian_batch_matches_oracle(pkg, n_t, nx, n_b, m):
             assert abs(float(r["f"][b]) - d["f"]) <= RTOL_F * abs(d["f"])
 
 
-@pytest.mark.parametrize("n_t,nx,n_b,m", [(3, 4, 2, 250), (2, 10, 1, 400), (1, 3, 0, 80)])
-def test_poisson_batch_matches_oracle(pkg, n_t, nx, n_b, m):
-    mdl = build("p", n_t, nx, n_b, m, "poisson", seed=5)
+@pytest.mark.parametrize("lik,n_t,nx,n_b,m", [("poisson", 3, 4, 2, 250), ("poisson", 2, 10, 1, 400),
+                                              ("poisson", 1, 3, 0, 80), ("binomial", 3, 4, 2, 250),
+                                              ("binomial", 2, 10, 1, 400), ("binomial", 1, 3, 0, 80)])
+def test_poisson_batch_matches_oracle(pkg, lik, n_t, nx, n_b, m):
+    mdl = build("p", n_t, nx, n_b, m, lik, seed=5)
     th = thetas(mdl, k=3, seed=1)
     th[:, 0] = np.log(np.array([1e-3, 0.1, 1.0]))
     model = pkg.Model(mdl)
@@ -232,11 +234,12 @@ MIX_F, MIX_G, MIX_X, MIX_V = 1e-6, 1e-5, 1e-9, 5e-5
 
 
 @pytest.mark.parametrize("lik,n_t,nx,n_b,m", [("gaussian", 4, 10, 3, 600), ("gaussian", 6, 13, 2, 1500),
-                                              ("gaussian", 1, 4, 0, 60), ("poisson", 3, 6, 2, 400)])
+                                              ("gaussian", 1, 4, 0, 60), ("poisson", 3, 6, 2, 400),
+                                              ("binomial", 3, 6, 2, 400)])
 def test_mixed_precision_matches_oracle(pkg, lik, n_t, nx, n_b, m):
     mdl = build("mx", n_t, nx, n_b, m, lik, seed=7)
     th = thetas(mdl, 3, seed=3)
-    if lik == "poisson":
+    if lik != "gaussian":
         th[:, 0] = np.log(np.array([1e-3, 0.1, 1.0]))
     model = pkg.Model(mdl)
     r = model.eval(cuda(th), grad="adjoint", want_mode=True, want_marg_var=True, precision="mixed")

@@ -122,7 +122,25 @@ def test_log_prior_and_poisson_loglik_match_scipy():
     assert np.isclose(M.poisson_loglik(mdl, eta), ref, rtol=1e-12)
 
 
-@pytest.mark.parametrize("lik", ["gaussian", "poisson"])
+def test_binomial_loglik_matches_scipy_and_its_derivatives_are_b_prime():
+    mdl = small(lik="binomial")
+    eta = np.linspace(-3, 3, mdl.m)
+    ref = stats.binom.logpmf(mdl.y, mdl.E, 1.0 / (1.0 + np.exp(-eta))).sum()
+    assert np.isclose(M.binomial_loglik(mdl, eta), ref, rtol=1e-12)
+    # b(eta) = N log(1 + e^eta): mean, weight and third derivative by central differences
+    for lik in ("binomial", "poisson"):
+        mdl = small(lik=lik)
+        b = (lambda e: mdl.E * np.logaddexp(0.0, e)) if lik == "binomial" else (lambda e: mdl.E * np.exp(e))
+        h = 1e-4
+        mean, wgt, third = M.glm_terms(mdl, eta)
+        assert np.allclose(mean, (b(eta + h) - b(eta - h)) / (2 * h), rtol=1e-7)
+        assert np.allclose(wgt, (M.glm_terms(mdl, eta + h)[0] - M.glm_terms(mdl, eta - h)[0]) / (2 * h),
+                           rtol=1e-6, atol=1e-9)
+        assert np.allclose(third, (M.glm_terms(mdl, eta + h)[1] - M.glm_terms(mdl, eta - h)[1]) / (2 * h),
+                           rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("lik", ["gaussian", "poisson", "binomial"])
 def test_dQ_matches_finite_difference_of_Q(lik):
     mdl = small(lik=lik)
     th = mdl.theta_true + np.array([0.1, 0.05, -0.1, 0.2])
@@ -291,7 +309,7 @@ def test_gaussian_bta_matches_dense_definition():
     assert np.allclose(d["var"], b["var"], rtol=1e-11)
 
 
-@pytest.mark.parametrize("lik", ["gaussian", "poisson"])
+@pytest.mark.parametrize("lik", ["gaussian", "poisson", "binomial"])
 def test_adjoint_gradient_matches_central_differences(lik):
     mdl = small(n_t=3, nx=4, n_b=2, m=200, lik=lik)
     th = mdl.theta_true + np.array([0.1, -0.1, 0.05, 0.2])
@@ -314,14 +332,17 @@ def test_fd_stencil_layout_and_gradient():
 
 # ---------------------------------------------------------------- Poisson (Laplace, Sec. 2.2)
 
-def test_poisson_mode_is_stationary_and_matches_dense_newton():
-    mdl = small(n_t=3, nx=4, n_b=2, m=250, lik="poisson")
+@pytest.mark.parametrize("lik", ["poisson", "binomial"])
+def test_poisson_mode_is_stationary_and_matches_dense_newton(lik):
+    mdl = small(n_t=3, nx=4, n_b=2, m=250, lik=lik)
     th = mdl.theta_true + np.array([0.5, 0.0, 0.1, 0.0])
     b = bta.poisson(mdl, th, want_var=True)
     d = dense.poisson_eval(mdl, th)
     A = M.obs_matrix(mdl)
     Q = M.prior_Q(mdl, th)
-    grad = Q @ b["x"] - A.T @ (mdl.y - mdl.E * np.exp(A @ b["x"]))
+    eta = A @ b["x"]
+    mean = mdl.E * np.exp(eta) if lik == "poisson" else mdl.E / (1.0 + np.exp(-eta))
+    grad = Q @ b["x"] - A.T @ (mdl.y - mean)
     assert np.abs(grad).max() < 1e-8 * max(1.0, np.abs(A.T @ mdl.y).max())
     assert b["converged"] and d["converged"]
     assert abs(b["f"] - d["f"]) < 1e-11 * abs(d["f"])
@@ -329,29 +350,40 @@ def test_poisson_mode_is_stationary_and_matches_dense_newton():
     assert np.allclose(b["var"], d["var"], rtol=1e-10)
 
 
-def test_poisson_laplace_matches_generic_laplace_formula():
+@pytest.mark.parametrize("lik", ["poisson", "binomial"])
+def test_poisson_laplace_matches_generic_laplace_formula(lik):
     # log p(y|theta) ~ h(x*) + (n/2) log 2 pi - 1/2 log|-h''(x*)|, with
     # h(x) = log pi(x|theta) + log p(y|x, theta), mode from a generic optimiser
     from scipy.optimize import minimize
-    mdl = small(n_t=2, nx=3, n_b=1, m=60, lik="poisson")
+    mdl = small(n_t=2, nx=3, n_b=1, m=60, lik=lik)
     th = mdl.theta_true + np.array([1.0, 0.0, 0.0, 0.0])
     Q = M.prior_Q(mdl, th).toarray()
     A = M.obs_matrix(mdl).toarray()
     n = mdl.n
     logdetQ = np.linalg.slogdet(Q)[1]
 
+    def logp(eta):
+        if lik == "poisson":
+            return stats.poisson.logpmf(mdl.y, mdl.E * np.exp(eta)).sum()
+        return stats.binom.logpmf(mdl.y, mdl.E, 1.0 / (1.0 + np.exp(-eta))).sum()
+
+    def mean_and_weight(eta):
+        if lik == "poisson":
+            mu = mdl.E * np.exp(eta)
+            return mu, mu
+        pr = 1.0 / (1.0 + np.exp(-eta))
+        return mdl.E * pr, mdl.E * pr * (1.0 - pr)
+
     def h(x):
-        eta = A @ x
-        return (-0.5 * n * math.log(2 * math.pi) + 0.5 * logdetQ - 0.5 * x @ Q @ x
-                + stats.poisson.logpmf(mdl.y, mdl.E * np.exp(eta)).sum())
+        return (-0.5 * n * math.log(2 * math.pi) + 0.5 * logdetQ - 0.5 * x @ Q @ x + logp(A @ x))
 
     def dh(x):
-        return -Q @ x + A.T @ (mdl.y - mdl.E * np.exp(A @ x))
+        return -Q @ x + A.T @ (mdl.y - mean_and_weight(A @ x)[0])
 
     res = minimize(lambda x: -h(x), np.zeros(n), jac=lambda x: -dh(x), method="BFGS",
                    options=dict(gtol=1e-11, maxiter=10000))
     xs = res.x
-    Hn = Q + A.T @ np.diag(mdl.E * np.exp(A @ xs)) @ A
+    Hn = Q + A.T @ np.diag(mean_and_weight(A @ xs)[1]) @ A
     laplace = h(xs) + 0.5 * n * math.log(2 * math.pi) - 0.5 * np.linalg.slogdet(Hn)[1]
     expect_f = -M.log_prior(mdl, th) - laplace
     assert abs(bta.poisson(mdl, th)["f"] - expect_f) < 1e-7 * abs(expect_f)

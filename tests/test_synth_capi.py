@@ -15,6 +15,7 @@ def pkg():
 
 
 CASES = [(8, 8, 2, 2000, "gaussian"), (3, 13, 0, 700, "gaussian"), (4, 10, 3, 900, "poisson"),
+         (3, 9, 2, 1500, "binomial"),
          (2, 32, 4, 20000, "gaussian")]
 
 
