@@ -69,7 +69,12 @@ typedef enum {
  * number of trials N in the E array.  The non-Gaussian ones are handled by
  * the Laplace approximation with a Newton inner loop (Sec. 2.2). */
 enum { INLA_LIK_GAUSSIAN = 0, INLA_LIK_POISSON = 1, INLA_LIK_BINOMIAL = 2 };
-enum { INLA_GRAD_NONE = 0, INLA_GRAD_FD_CENTRAL = 1, INLA_GRAD_ADJOINT = 2 };
+/* Gradient of f: none; central differences (Eq. central_diff: 2d + 1 = 9
+ * evaluations per centre); the adjoint (selected-inverse traces, one extra
+ * solve for non-Gaussian data); forward differences (d + 1 = 5 evaluations
+ * per centre, (f(theta + eps e_j) - f(theta)) / eps, first-order accurate: the
+ * cheaper scheme the paper mixes in for later iterations). */
+enum { INLA_GRAD_NONE = 0, INLA_GRAD_FD_CENTRAL = 1, INLA_GRAD_ADJOINT = 2, INLA_GRAD_FD_FORWARD = 3 };
 /* How log|Q| and tr(Q^-1 dQ) of the prior are obtained.  KRONECKER uses
  * log|Q_t (x) Q_s| = n_s log|Q_t| + n_t log|Q_s| with one dense n_s x n_s
  * inversion of Q_s; BTA runs the same block factorisation (and selected

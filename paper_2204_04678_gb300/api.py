@@ -12,7 +12,8 @@ import numpy as np
 
 from . import capi as C
 
-_GRAD = {"none": C.INLA_GRAD_NONE, "fd": C.INLA_GRAD_FD_CENTRAL, "adjoint": C.INLA_GRAD_ADJOINT}
+_GRAD = {"none": C.INLA_GRAD_NONE, "fd": C.INLA_GRAD_FD_CENTRAL, "adjoint": C.INLA_GRAD_ADJOINT,
+         "fd_forward": C.INLA_GRAD_FD_FORWARD}
 _PRIOR = {"kronecker": C.INLA_PRIOR_KRONECKER, "bta": C.INLA_PRIOR_BTA}
 
 

@@ -23,6 +23,7 @@ INLA_LIK_BINOMIAL = 2
 INLA_GRAD_NONE = 0
 INLA_GRAD_FD_CENTRAL = 1
 INLA_GRAD_ADJOINT = 2
+INLA_GRAD_FD_FORWARD = 3
 INLA_PRIOR_KRONECKER = 0
 INLA_PRIOR_BTA = 1
 INLA_FP64 = 0

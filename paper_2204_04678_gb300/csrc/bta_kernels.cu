@@ -999,13 +999,16 @@ __global__ void copy_mode_kernel(DevModel M, Work W, double *x_out, const int *p
   x_out[(int64_t)o * M.n + k] = (W.status[b] == INLA_OK) ? v : NAN;
 }
 
-__global__ void fd_points_kernel(int B, const double *theta, double eps, double *pts) {
+// Difference stencils per centre: central (per = 9) centre, +e_0, -e_0, +e_1, ...;
+// forward (per = 5) centre, +e_0, +e_1, +e_2, +e_3 (steps eps).
+__global__ void fd_points_kernel(int B, int per, const double *theta, double eps, double *pts) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= B * 9) return;
-  const int c = idx / 9, k = idx % 9;
+  if (idx >= B * per) return;
+  const int c = idx / per, k = idx % per;
   for (int j = 0; j < 4; ++j) {
     double v = theta[c * 4 + j];
-    if (k > 0 && (k - 1) / 2 == j) v += ((k - 1) % 2 == 0) ? eps : -eps;
+    if (per == 9 && k > 0 && (k - 1) / 2 == j) v += ((k - 1) % 2 == 0) ? eps : -eps;
+    if (per == 5 && k == j + 1) v += eps;
     pts[idx * 4 + j] = v;
   }
 }
@@ -1025,7 +1028,8 @@ __global__ void outputs_kernel(int B, int per, double eps, int d, const double *
   for (int j = 0; j < d; ++j) {
     double g;
     if (per == 1) g = grad_all ? grad_all[c * d + j] : NAN;
-    else g = (f_all[c * per + 1 + 2 * j] - f_all[c * per + 2 + 2 * j]) / (2.0 * eps);
+    else if (per == 9) g = (f_all[c * per + 1 + 2 * j] - f_all[c * per + 2 + 2 * j]) / (2.0 * eps);
+    else g = (f_all[c * per + 1 + j] - f_all[c * per]) / eps;
     grad[c * d + j] = (st == INLA_OK) ? g : NAN;
   }
 }
@@ -1438,8 +1442,8 @@ void k_copy_mode(Launch &L, const DevModel &M, const Work &W, double *x_out, con
   copy_mode_kernel<<<dim3(blocks(M.n, 256), W.P), 256, 0, L.st>>>(M, W, x_out, point_out, point_base);
   L.tick();
 }
-void k_fd_points(Launch &L, int B, const double *theta, double eps, double *pts) {
-  fd_points_kernel<<<blocks(B * 9, 64), 64, 0, L.st>>>(B, theta, eps, pts);
+void k_fd_points(Launch &L, int B, int per, const double *theta, double eps, double *pts) {
+  fd_points_kernel<<<blocks(B * per, 64), 64, 0, L.st>>>(B, per, theta, eps, pts);
   L.tick();
 }
 void k_outputs(Launch &L, int B, int per, double eps, int d, const double *f_all, const double *grad_all,

@@ -720,7 +720,7 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
   CUDA_OK(cudaMemsetAsync(W.status, 0, sizeof(int) * W.P, L.st));
   CUDA_OK(cudaMemsetAsync(W.iters, 0, sizeof(int) * W.P, L.st));
   CUDA_OK(cudaMemsetAsync(W.rhs, 0, sizeof(double) * W.sVec * W.P, L.st));
-  flags_kernel<<<(W.P + 63) / 64, 64, 0, L.st>>>(W, w0, o.grad == INLA_GRAD_FD_CENTRAL ? 9 : 1, centre_flags);
+  flags_kernel<<<(W.P + 63) / 64, 64, 0, L.st>>>(W, w0, fd_points_per_centre(o.grad), centre_flags);
   L.tick();
   k_set_active(L, W, 0);
   k_params(L, M, W);
@@ -810,7 +810,7 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
                   const inla_eval_out *out, cudaStream_t st) {
   if (!mdl || !opts || !out || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
   if (!out->f_dev || !out->status_dev) throw ApiError(INLA_ERR_ARG, "f_dev and status_dev are required");
-  if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_ADJOINT) throw ApiError(INLA_ERR_ARG, "bad grad mode");
+  if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_FD_FORWARD) throw ApiError(INLA_ERR_ARG, "bad grad mode");
   if (opts->prior_mode != INLA_PRIOR_KRONECKER && opts->prior_mode != INLA_PRIOR_BTA)
     throw ApiError(INLA_ERR_ARG, "bad prior mode");
   if (opts->precision != INLA_FP64 && opts->precision != INLA_MIXED) throw ApiError(INLA_ERR_ARG, "bad precision");
@@ -819,7 +819,7 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   if (opts->want_marg_var && !out->marg_var_dev) throw ApiError(INLA_ERR_ARG, "marg_var_dev required");
   const int rb = opts->precision == INLA_MIXED ? 4 : 8;
   CUDA_OK(cudaSetDevice(mdl->device));
-  const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+  const int per = fd_points_per_centre(opts->grad);
   const int64_t P_total = (int64_t)B * per;
   mdl->launches = 0;
   // the workspace is shared by all calls on this model: order this call after the previous one
@@ -843,12 +843,12 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
 void enqueue_eval(inla_model *mdl, Launch &L, int B, const double *theta_dev, const inla_eval_opts *opts,
                   const inla_eval_out *out, const BatchBufs &bb, int Pw, int rb) {
   cudaStream_t st = L.st;
-  const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+  const int per = fd_points_per_centre(opts->grad);
   const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
   const int64_t P_total = (int64_t)B * per;
   point_out_kernel<<<(unsigned)((P_total + 127) / 128), 128, 0, st>>>((int)P_total, per, bb.point_out);
   L.tick();
-  if (per == 9) k_fd_points(L, B, theta_dev, eps, bb.theta_all);
+  if (per > 1) k_fd_points(L, B, per, theta_dev, eps, bb.theta_all);
   else CUDA_OK(cudaMemcpyAsync(bb.theta_all, theta_dev, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
   int centre_flags = 0;
   if (opts->want_marg_var || opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 1;
@@ -906,7 +906,7 @@ void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_ev
     cudaGraph_t graph = nullptr;
     CUDA_OK(cudaStreamBeginCapture(mdl->stream, cudaStreamCaptureModeThreadLocal));
     try {
-      enqueue_eval(mdl, L, B, e.theta, opts, &so, bb, (int)((int64_t)B * (opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1)),
+      enqueue_eval(mdl, L, B, e.theta, opts, &so, bb, (int)((int64_t)B * (fd_points_per_centre(opts->grad))),
                    rb);
     } catch (...) {
       cudaStreamEndCapture(mdl->stream, &graph);
@@ -989,7 +989,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
                          const inla_eval_out *out, cudaStream_t st) {
   if (!mdl || !opts || !out || !theta_dev || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
   if (!out->f_dev || !out->status_dev) throw ApiError(INLA_ERR_ARG, "f_dev and status_dev are required");
-  if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_ADJOINT) throw ApiError(INLA_ERR_ARG, "bad grad mode");
+  if (opts->grad < INLA_GRAD_NONE || opts->grad > INLA_GRAD_FD_FORWARD) throw ApiError(INLA_ERR_ARG, "bad grad mode");
   if (opts->prior_mode != INLA_PRIOR_KRONECKER && opts->prior_mode != INLA_PRIOR_BTA)
     throw ApiError(INLA_ERR_ARG, "bad prior mode");
   if (opts->precision != INLA_FP64 && opts->precision != INLA_MIXED) throw ApiError(INLA_ERR_ARG, "bad precision");
@@ -997,7 +997,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   if (opts->want_mode && !out->x_mode_dev) throw ApiError(INLA_ERR_ARG, "x_mode_dev required");
   if (opts->want_marg_var && !out->marg_var_dev) throw ApiError(INLA_ERR_ARG, "marg_var_dev required");
   const int rb = opts->precision == INLA_MIXED ? 4 : 8;
-  const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+  const int per = fd_points_per_centre(opts->grad);
   const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
   const int64_t P_total = (int64_t)B * per;
   // the whole batch is one wave: workspace, then the per-point batch arrays
@@ -1025,7 +1025,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   bb.iters_all = reinterpret_cast<int *>(take(4 * P_total));
   point_out_kernel<<<(unsigned)((P_total + 127) / 128), 128, 0, st>>>((int)P_total, per, bb.point_out);
   L.tick();
-  if (per == 9) k_fd_points(L, B, theta_dev, eps, bb.theta_all);
+  if (per > 1) k_fd_points(L, B, per, theta_dev, eps, bb.theta_all);
   else CUDA_OK(cudaMemcpyAsync(bb.theta_all, theta_dev, sizeof(double) * 4 * B, cudaMemcpyDeviceToDevice, st));
   int centre_flags = 0;
   if (opts->want_marg_var || opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 1;
@@ -1059,7 +1059,7 @@ int inla_model_create(const inla_model_desc *desc, int device, inla_model **out)
 int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *opts, size_t *bytes) {
   return guarded([&] {
     if (!model || !opts || !bytes || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
-    const int per = opts->grad == INLA_GRAD_FD_CENTRAL ? 9 : 1;
+    const int per = fd_points_per_centre(opts->grad);
     *bytes = (size_t)point_bytes(model->M, opts->precision == INLA_MIXED ? 4 : 8) * (size_t)B * per;
   });
 }

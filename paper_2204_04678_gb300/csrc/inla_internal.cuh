@@ -272,7 +272,11 @@ void k_finalize(Launch &L, const DevModel &M, const Work &W, int grad_mode, int 
                 double *f_all, double *grad_all, int *status_all, int *iters_all);
 void k_copy_mode(Launch &L, const DevModel &M, const Work &W, double *x_out, const int *point_out,
                  int64_t point_base);
-void k_fd_points(Launch &L, int B, const double *theta, double eps, double *pts);
+void k_fd_points(Launch &L, int B, int per, const double *theta, double eps, double *pts);
+// evaluation points per centre of a gradient mode: 9 (central), 5 (forward), else 1
+inline int fd_points_per_centre(int grad) {
+  return grad == INLA_GRAD_FD_CENTRAL ? 9 : (grad == INLA_GRAD_FD_FORWARD ? 5 : 1);
+}
 void k_outputs(Launch &L, int B, int per, double eps, int d, const double *f_all, const double *grad_all,
                const int *status_all, const int *iters_all, double *f, double *grad, int *status, int *iters);
 void k_poisson_eta(Launch &L, const DevModel &M, const Work &W, const double *x);

@@ -82,7 +82,8 @@ def parallel_line_search(eval_f_batch, theta, f0, d, gamma=1.0, max_shrink=6):
     return step, gamma, pts, fv
 
 
-def bfgs(eval_f_grad, eval_f_batch, theta0, max_iter=50, gtol=1e-3, gamma=1.0, max_step=2.0, ftol=0.0):
+def bfgs(eval_f_grad, eval_f_batch, theta0, max_iter=50, gtol=1e-3, gamma=1.0, max_step=2.0, ftol=0.0,
+         state=None, on_iteration=None):
     """Minimise f with BFGS (inverse-Hessian update, Eq. bfgs_update) and the
     parallel line search.
 
@@ -97,15 +98,31 @@ def bfgs(eval_f_grad, eval_f_batch, theta0, max_iter=50, gtol=1e-3, gamma=1.0, m
     gtol, or when an iteration lowers f by less than ftol |f| (for evaluations
     whose rounding error exceeds what gtol asks).  Returns a dict with the
     final point, f, gradient, iteration count and the history of f.
+
+    Checkpointing: on_iteration(state) is called after every iteration with the
+    optimiser state (theta, f, grad, inverse Hessian, interval length,
+    iteration, history); passing such a state back as `state` resumes the run
+    exactly where it stopped (theta0 is then ignored).  save_state/load_state
+    write and read it as JSON.
     """
-    theta = np.asarray(theta0, dtype=float).copy()
-    dim = theta.size
-    Hinv = np.eye(dim)
-    f, g = eval_f_grad(theta)
-    hist = [f]
-    gam = gamma
-    it = 0
-    for it in range(1, max_iter + 1):
+    if state is not None:
+        theta = np.asarray(state["theta"], dtype=float).copy()
+        f, g = float(state["f"]), np.asarray(state["grad"], dtype=float).copy()
+        Hinv = np.asarray(state["Hinv"], dtype=float).copy()
+        gam = float(state["gamma"])
+        start = int(state["iteration"])
+        hist = list(state["history"])
+        dim = theta.size
+    else:
+        theta = np.asarray(theta0, dtype=float).copy()
+        dim = theta.size
+        Hinv = np.eye(dim)
+        f, g = eval_f_grad(theta)
+        hist = [f]
+        gam = gamma
+        start = 0
+    it = start
+    for it in range(start + 1, max_iter + 1):
         if np.abs(g).max() < gtol:
             it -= 1
             break
@@ -136,9 +153,27 @@ def bfgs(eval_f_grad, eval_f_batch, theta0, max_iter=50, gtol=1e-3, gamma=1.0, m
         done = f - f_new < ftol * abs(f)
         theta, f, g = theta_new, f_new, g_new
         hist.append(f)
+        if on_iteration is not None:
+            on_iteration(dict(theta=theta.copy(), f=f, grad=g.copy(), Hinv=Hinv.copy(), gamma=gam, iteration=it,
+                              history=list(hist)))
         if done:
             break
     return dict(theta=theta, f=f, grad=g, iterations=it, history=np.array(hist))
+
+
+def save_state(path, state):
+    """Write a BFGS state (from on_iteration) as JSON."""
+    import json
+    plain = {k: (np.asarray(v).tolist() if isinstance(v, (np.ndarray, list)) else v) for k, v in state.items()}
+    with open(path, "w") as fh:
+        json.dump(plain, fh)
+
+
+def load_state(path):
+    """Read a BFGS state written by save_state."""
+    import json
+    with open(path) as fh:
+        return json.load(fh)
 
 
 def ccd_unit_design(dim=4):

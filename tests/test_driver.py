@@ -212,3 +212,20 @@ def test_bfgs_and_integration_on_tiny_model_with_the_oracle():
     assert integ["weights"].sum() == pytest.approx(1.0)
     assert np.all(np.linalg.eigvalsh(integ["hessian"]) > 0)
     assert np.all(integ["x_var"] > 0)
+
+
+def test_bfgs_checkpoint_and_resume_reproduce_an_uninterrupted_run(tmp_path):
+    from paper_2204_04678_gb300.driver import load_state, save_state
+    H = np.diag([2e4, 3e3, 50.0, 2.0]) + 0.5
+    mu = np.array([1.0, -1.0, 0.1, 1.5])
+    fg, fb = _quadratic(H, mu)
+    t0 = mu + np.array([0.3, -0.3, 0.2, -0.4])
+    full = bfgs(fg, fb, t0, max_iter=60, gtol=1e-8)
+    path = tmp_path / "bfgs.json"
+    bfgs(fg, fb, t0, max_iter=3, gtol=1e-8, on_iteration=lambda st: save_state(path, st))
+    st = load_state(path)
+    assert st["iteration"] == 3
+    resumed = bfgs(fg, fb, None, max_iter=60, gtol=1e-8, state=st)
+    assert resumed["iterations"] == full["iterations"]
+    np.testing.assert_array_equal(resumed["theta"], full["theta"])
+    np.testing.assert_array_equal(resumed["history"], full["history"])

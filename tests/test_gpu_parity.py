@@ -91,6 +91,22 @@ def test_poisson_batch_matches_oracle(pkg, lik, n_t, nx, n_b, m):
         assert abs(int(r["newton_iters"][b]) - ref["iters"]) <= 1
 
 
+def test_forward_difference_gradient_matches_oracle(pkg):
+    mdl = build("g", 3, 6, 2, 400, "gaussian", seed=9)
+    th = thetas(mdl, 2, seed=4)
+    model = pkg.Model(mdl)
+    r = model.eval(cuda(th), grad="fd_forward")
+    torch.cuda.synchronize()
+    for b in range(th.shape[0]):
+        f = lambda t: bta.gaussian(mdl, t)["f"]
+        ref = fd.forward_gradient(f, th[b], 1e-3)
+        assert int(r["status"][b]) == 0
+        assert abs(float(r["f"][b]) - f(th[b])) <= RTOL_F * abs(f(th[b]))
+        # differences of f values that agree to 1e-10 relative, divided by eps
+        g = r["grad"][b].cpu().numpy()
+        assert np.abs(g - ref).max() <= 1e-10 * abs(f(th[b])) / 1e-3 * 4
+
+
 def test_prior_modes_agree(pkg):
     mdl = build("g", 4, 9, 2, 500, "gaussian", seed=3)
     th = thetas(mdl, 2)

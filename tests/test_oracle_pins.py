@@ -322,6 +322,16 @@ def test_adjoint_gradient_matches_central_differences(lik):
     assert errs[1] < errs[0] / 20.0          # O(eps^2) until round-off
 
 
+def test_forward_differences_are_first_order():
+    f = lambda t: float(np.exp(t[0]) * np.sin(t[1]) + t[2] ** 3 - t[3] * t[0])
+    th = np.array([0.3, 0.7, -0.4, 1.2])
+    exact = np.array([np.exp(th[0]) * np.sin(th[1]) - th[3], np.exp(th[0]) * np.cos(th[1]), 3 * th[2] ** 2, -th[0]])
+    e1 = np.abs(fd.forward_gradient(f, th, 1e-3) - exact).max()
+    e2 = np.abs(fd.forward_gradient(f, th, 1e-4) - exact).max()
+    assert 5.0 < e1 / e2 < 20.0          # O(eps)
+    assert np.abs(fd.central_gradient(f, th, 1e-3) - exact).max() < e2   # central is O(eps^2)
+
+
 def test_fd_stencil_layout_and_gradient():
     th = np.array([0.3, -0.2, 0.1, 1.0])
     pts = fd_stencil(th, 1e-3)
