@@ -301,8 +301,10 @@ const char *inla_last_error(void);
 /* Measurement utility (no counterpart in the paper): sustained FP64 FMA
  * throughput of this GPU in TFLOP/s, timed with CUDA events on a
  * register-resident loop over every SM, so that roofline fractions can be
- * quoted against a measured FP64 peak.  use_tensor != 0 times the
- * warp-level double-precision MMA instruction instead of scalar FMA. */
+ * quoted against a measured FP64 peak.  use_tensor = 1 times the
+ * warp-level double-precision MMA instruction instead of scalar FMA;
+ * use_tensor = 2 runs both at once (half the warps each), which shows whether
+ * the two FP64 paths share one pipe. */
 int inla_measure_fp64_peak(int device, int use_tensor, double *tflops);
 
 /* Measurement utility (no counterpart in the paper): FP32 scalar FMA

@@ -47,6 +47,40 @@ __global__ void __launch_bounds__(256) dmma_probe(int iters, double *sink) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Both FP64 paths at once: even warps run the DFMA chains, odd warps the DMMA
+// chains, to see whether the scalar FP64 pipe and the FP64 tensor path add up.
+__global__ void __launch_bounds__(256) dboth_probe(int iters, double *sink) {
+  const int warp = threadIdx.x >> 5;
+  double s = 0.0;
+  if (warp & 1) {
+    double acc[CHAINS][2];
+    const double av = 1.0 + 1e-9 * threadIdx.x, bv = 1.0 - 1e-9 * blockIdx.x;
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) acc[c][0] = acc[c][1] = 0.25 * c;
+    for (int i = 0; i < iters / 4; ++i) {
+#pragma unroll
+      for (int c = 0; c < CHAINS; ++c)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                     : "+d"(acc[c][0]), "+d"(acc[c][1])
+                     : "d"(av), "d"(bv));
+    }
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) s += acc[c][0] + acc[c][1];
+  } else {
+    double a[CHAINS];
+    const double x = 1.0 + 1e-9 * threadIdx.x, y = 1.0 - 1e-9 * blockIdx.x;
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) a[c] = 0.5 * c;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < CHAINS; ++c) a[c] = fma(a[c], x, y);
+    }
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) s += a[c];
+  }
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(256) ffma_probe(int iters, float *sink) {
   float a[CHAINS];
   const float x = 1.0f + 1e-7f * threadIdx.x, y = 1.0f - 1e-7f * blockIdx.x;
@@ -130,7 +164,8 @@ extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0);
-    if (use_tensor) dmma_probe<<<blocks, threads>>>(iters, sink);
+    if (use_tensor == 2) dboth_probe<<<blocks, threads>>>(1 << 16, sink);
+    else if (use_tensor) dmma_probe<<<blocks, threads>>>(iters, sink);
     else dfma_probe<<<blocks, threads>>>(iters, sink);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
@@ -147,8 +182,14 @@ extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops
     return INLA_ERR_CUDA;
   }
   // scalar: 2 flops per FMA per thread; MMA m8n8k4: 8*8*4 FMAs per warp instruction
-  const double per_iter = use_tensor ? (double)blocks * (threads / 32) * CHAINS * 8 * 8 * 4 * 2
-                                     : (double)blocks * threads * CHAINS * 2;
-  *tflops = per_iter * iters / (best * 1e-3) / 1e12;
+  double flops;
+  if (use_tensor == 2)   // half the warps: 2^16 DFMA steps; the other half: 2^14 DMMA steps
+    flops = (double)blocks * (threads / 2) * CHAINS * 2 * (1 << 16) +
+            (double)blocks * (threads / 64) * CHAINS * 8 * 8 * 4 * 2 * (1 << 14);
+  else if (use_tensor)
+    flops = (double)blocks * (threads / 32) * CHAINS * 8 * 8 * 4 * 2 * iters;
+  else
+    flops = (double)blocks * threads * CHAINS * 2 * iters;
+  *tflops = flops / (best * 1e-3) / 1e12;
   return INLA_OK;
 }
