@@ -131,9 +131,12 @@ typedef struct {
   int32_t max_newton;     /* Poisson: iteration limit (<= 0: 50)                   */
   double newton_tol;      /* Poisson: stop when ||x^{k+1} - x^k||_2 < tol (<= 0: 1e-8) */
   double fd_eps;          /* central-difference step (<= 0: 1e-3)                  */
-  int32_t use_graph;      /* nonzero (Gaussian likelihood, batch in one wave): the  */
-                          /* whole evaluation is captured once per batch size and   */
-                          /* options as a CUDA graph and replayed on later calls    */
+  int32_t use_graph;      /* nonzero (batch in one wave): the whole evaluation is   */
+                          /* captured once per batch size and options as a CUDA    */
+                          /* graph and replayed on later calls; for Poisson and     */
+                          /* binomial data the Newton loop is a conditional while   */
+                          /* node that repeats on the device until every point has  */
+                          /* converged or hit max_newton (no host synchronisation)  */
 } inla_eval_opts;
 
 /* Outputs of inla_eval_batch: DEVICE pointers owned by the caller.  Layout

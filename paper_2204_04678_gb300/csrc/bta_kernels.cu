@@ -1141,9 +1141,11 @@ __global__ void obs_assemble_tip_sum_kernel(DevModel M, const int *active, const
 }
 
 // ||x - xprev||_2 < tol ends the iteration of a point; xprev <- x.
-__global__ void poisson_step_kernel(DevModel M, Work W, double tol, int iter, int max_iter) {
+__global__ void poisson_step_kernel(DevModel M, Work W, double tol, int iter_host, int max_iter,
+                                    const int *iter_dev) {
   const int b = blockIdx.x;
   if (!W.active[b]) return;
+  const int iter = iter_dev ? *iter_dev + 1 : iter_host;   // the graph path counts on the device
   __shared__ double red[32];
   double *x = W.x + b * W.sVec;
   double *xp = W.xprev + b * W.sVec;
@@ -1479,8 +1481,18 @@ void k_obs_assemble(Launch &L, const DevModel &M, int P, const int *active, cons
     L.tick();
   }
 }
-void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter) {
-  poisson_step_kernel<<<W.P, 256, 0, L.st>>>(M, W, tol, iter, max_iter);
+// Newton iterations of a captured evaluation: the while-node's body ends here.
+__global__ void newton_continue_kernel(cudaGraphConditionalHandle h, const int *any_active, int *ctr) {
+  ++*ctr;
+  cudaGraphSetConditional(h, *any_active ? 1u : 0u);
+}
+void k_newton_continue(Launch &L, cudaGraphConditionalHandle h, const int *any_active, int *ctr) {
+  newton_continue_kernel<<<1, 1, 0, L.st>>>(h, any_active, ctr);
+  L.tick();
+}
+void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter,
+                    const int *iter_dev) {
+  poisson_step_kernel<<<W.P, 256, 0, L.st>>>(M, W, tol, iter, max_iter, iter_dev);
   L.tick();
 }
 template <typename R>

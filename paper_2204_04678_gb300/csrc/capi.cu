@@ -91,8 +91,8 @@ struct inla_model {
   int64_t launches = 0;
   Profiler prof;
   struct GraphEntry {
-    int B, grad, prior, precision, want_mode, want_marg_var;
-    double fd_eps;
+    int B, grad, prior, precision, want_mode, want_marg_var, max_newton;
+    double fd_eps, newton_tol;
     void *ws, *bb;                 // workspace the graph was captured on
     cudaGraphExec_t exec = nullptr;
     void *stage = nullptr;         // theta in, outputs out (device)
@@ -755,18 +755,56 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     const double tol = o.newton_tol > 0 ? o.newton_tol : 1e-8;
     CUDA_OK(cudaMemsetAsync(W.x, 0, sizeof(double) * W.sVec * W.P, L.st));
     CUDA_OK(cudaMemsetAsync(W.xprev, 0, sizeof(double) * W.sVec * W.P, L.st));
-    for (int it = 1; it <= max_it; ++it) {
-      k_poisson_eta(L, M, W, W.x);
-      k_obs_assemble(L, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp, W.sArwp,
-                     W.Tipp, W.sNb2, W.rhs, W.sVec, W.tippart);
-      factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC);
-      solve<R>(L, M, W, W.rhs, W.x);
-      CUDA_OK(cudaMemsetAsync(W.any_active, 0, sizeof(int), L.st));
-      k_poisson_step(L, M, W, tol, it, max_it);
-      int any = 0;
-      CUDA_OK(cudaMemcpyAsync(&any, W.any_active, sizeof(int), cudaMemcpyDeviceToHost, L.st));
-      CUDA_OK(cudaStreamSynchronize(L.st));
-      if (!any) break;
+    auto newton_step = [&](Launch &Ls, int it, const int *it_dev) {
+      k_poisson_eta(Ls, M, W, W.x);
+      k_obs_assemble(Ls, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp,
+                     W.sArwp, W.Tipp, W.sNb2, W.rhs, W.sVec, W.tippart);
+      factor<R>(Ls, M, W, ASM_QC, SC_LOGDET_QC);
+      solve<R>(Ls, M, W, W.rhs, W.x);
+      CUDA_OK(cudaMemsetAsync(W.any_active, 0, sizeof(int), Ls.st));
+      k_poisson_step(Ls, M, W, tol, it, max_it, it_dev);
+    };
+    if (L.capturing) {
+      // the Newton loop as a while-node of the graph: its body is one iteration for
+      // every point of the wave, repeated on the device while any point is active
+      int *ctr = W.any_active + 1;   // iterations done (the second int of the slot)
+      CUDA_OK(cudaMemsetAsync(ctr, 0, sizeof(int), L.st));
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t graph = nullptr;
+      const cudaGraphNode_t *deps = nullptr;
+      size_t ndeps = 0;
+      CUDA_OK(cudaStreamGetCaptureInfo(L.st, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+      cudaGraphConditionalHandle h;
+      CUDA_OK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      CUDA_OK(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      cudaStream_t bs;
+      CUDA_OK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+      Launch Lb = L;
+      Lb.st = bs;
+      cudaError_t e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        newton_step(Lb, 0, ctr);
+        k_newton_continue(Lb, h, W.any_active, ctr);
+        e = cudaStreamEndCapture(bs, &body);
+      }
+      cudaStreamDestroy(bs);
+      CUDA_OK(e);
+      CUDA_OK(cudaStreamUpdateCaptureDependencies(L.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    } else {
+      for (int it = 1; it <= max_it; ++it) {
+        newton_step(L, it, nullptr);
+        int any = 0;
+        CUDA_OK(cudaMemcpyAsync(&any, W.any_active, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+        CUDA_OK(cudaStreamSynchronize(L.st));
+        if (!any) break;
+      }
     }
     // refactorise at the mode
     k_set_active(L, W, 0);
@@ -827,7 +865,7 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   const int Pw = wave_points(mdl, P_total, rb);
   ensure_workspace(mdl, Pw, rb);
   BatchBufs bb = batch_buffers(mdl, P_total);
-  if (opts->use_graph && mdl->M.lik == INLA_LIK_GAUSSIAN && Pw == P_total && !mdl->prof.enabled) {
+  if (opts->use_graph && Pw == P_total && !mdl->prof.enabled) {
     replay_graph(mdl, B, theta_dev, opts, out, st, bb, rb);
   } else {
     Launch L{st, &mdl->launches, &mdl->prof};
@@ -877,12 +915,14 @@ void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   for (auto &e : mdl->graphs)
     if (e.B == B && e.grad == opts->grad && e.prior == opts->prior_mode && e.precision == opts->precision &&
         e.want_mode == (opts->want_mode != 0) && e.want_marg_var == (opts->want_marg_var != 0) &&
-        e.fd_eps == opts->fd_eps && e.ws == mdl->ws && e.bb == mdl->bb)
+        e.fd_eps == opts->fd_eps && e.max_newton == opts->max_newton && e.newton_tol == opts->newton_tol &&
+        e.ws == mdl->ws && e.bb == mdl->bb)
       g = &e;
   if (!g) {
     inla_model::GraphEntry e{};
     e.B = B; e.grad = opts->grad; e.prior = opts->prior_mode; e.precision = opts->precision;
     e.want_mode = opts->want_mode != 0; e.want_marg_var = opts->want_marg_var != 0; e.fd_eps = opts->fd_eps;
+    e.max_newton = opts->max_newton; e.newton_tol = opts->newton_tol;
     e.ws = mdl->ws; e.bb = mdl->bb;
     const size_t bytes = rup(32 * B, 256) + rup(8 * B, 256) + rup(32 * B, 256) + 2 * rup(4 * B, 256) +
                          2 * rup(8 * n * B, 256);
@@ -903,6 +943,7 @@ void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_ev
     dense_prepare();
     int64_t count = 0;
     Launch L{mdl->stream, &count, nullptr};
+    L.capturing = true;
     cudaGraph_t graph = nullptr;
     CUDA_OK(cudaStreamBeginCapture(mdl->stream, cudaStreamCaptureModeThreadLocal));
     try {

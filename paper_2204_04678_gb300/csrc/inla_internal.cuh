@@ -165,6 +165,7 @@ struct Launch {
   cudaStream_t st;
   int64_t *counter;
   Profiler *prof = nullptr;
+  bool capturing = false;   // being recorded into a CUDA graph (no host synchronisation allowed)
   int cur_id = -1;
   double cur_units = 0.0;
   cudaEvent_t cur_a = nullptr;
@@ -286,7 +287,10 @@ void k_obs_assemble(Launch &L, const DevModel &M, int P, const int *active, cons
                     const double *r, int64_t sR, bool r_newton, const double *eta, double *AtA, int64_t sAtA,
                     double *Arw, int64_t sArw, double *Tip, int64_t sTip, double *rhs, int64_t sRhs,
                     double *tippart);
-void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter);
+void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter,
+                    const int *iter_dev = nullptr);
+// graph body: count the Newton iteration and continue the while-node while any point is active
+void k_newton_continue(Launch &L, cudaGraphConditionalHandle h, const int *any_active, int *ctr);
 template <typename R>
 void k_poisson_qobs(Launch &L, const DevModel &M, const Work &W, int t);
 void k_poisson_wobs(Launch &L, const DevModel &M, const Work &W);

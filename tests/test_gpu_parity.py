@@ -303,6 +303,30 @@ def test_cuda_graph_replay_matches_eager(pkg):
                     assert torch.equal(eager[key], graph[key]), (kw, k, key)
 
 
+@pytest.mark.parametrize("lik", ["poisson", "binomial"])
+def test_cuda_graph_newton_loop_matches_eager(pkg, lik):
+    # uneven Newton counts in one graph launch: the loop is a conditional while-node
+    mdl = build("p", 3, 6, 2, 400, lik, seed=13)
+    model = pkg.Model(mdl)
+    th = thetas(mdl, 4, seed=2)
+    th[:, 0] = np.log(np.array([1e-3, 0.1, 1.0, 10.0]))
+    for kw in (dict(grad="adjoint", want_mode=True, want_marg_var=True), dict(grad="fd"),
+               dict(grad="adjoint", precision="mixed")):
+        for rep in range(2):    # capture, then replay
+            eager = model.eval(cuda(th), **kw)
+            graph = model.eval(cuda(th), use_graph=True, **kw)
+            torch.cuda.synchronize()
+            for key in ("f", "grad", "x_mode", "marg_var", "status", "newton_iters"):
+                if key in eager:
+                    assert torch.equal(eager[key], graph[key]), (lik, kw, rep, key)
+        it = eager["newton_iters"].cpu().numpy()
+        assert it.min() >= 1
+    # an iteration limit ends the device loop with the status, as on the eager path
+    r = model.eval(cuda(th[:1]), max_newton=1, use_graph=True)
+    torch.cuda.synchronize()
+    assert int(r["status"][0]) == pkg.capi.INLA_ERR_NO_CONVERGENCE
+
+
 def test_autotune_keeps_results(pkg):
     mdl = build("g", 3, 10, 2, 500, "gaussian", seed=21)
     th = thetas(mdl, 2, seed=8)
