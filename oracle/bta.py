@@ -268,7 +268,7 @@ def poisson_mode(model, theta, tol=1e-8, max_iter=50):
         mean, wgt, _ = M.glm_terms(model, eta)
         Qc = (Q + A.T @ sp.diags(wgt) @ A).tocsr()
         L, _ = cholesky(_blocks(model, Qc))
-        xn = solve(L, A.T @ (model.y - mean + wgt * eta))
+        xn = M.capped_step(A, x, solve(L, A.T @ (model.y - mean + wgt * eta)))
         step = float(np.linalg.norm(xn - x))
         x = xn
         if step < tol:

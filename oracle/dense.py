@@ -58,12 +58,18 @@ def gaussian_closed_form(model, theta):
     return float(-M.log_prior(model, theta) + 0.5 * model.m * LOG2PI + 0.5 * logdetS + 0.5 * z @ z)
 
 
+def capped_step(A, x, xn):
+    return M.capped_step(A, x, xn)
+
+
 def poisson_mode(model, theta, tol=1e-8, max_iter=50, x0=None):
     """Newton iteration for the mode of pi(x | theta, y), non-Gaussian likelihood.
 
     x^{k+1} solves (Q + A^T D A) x = A^T (y - b1 + D eta) with eta = A x^k,
-    b1 = the mean and D = diag(weight) from glm_terms (Poisson: both E e^eta);
-    stop when ||x^{k+1} - x^k||_2 < tol.  Returns (x*, iterations, converged).
+    b1 = the mean and D = diag(weight) from glm_terms (Poisson: both E e^eta),
+    the step capped so that no linear predictor moves by more than 2
+    (capped_step); stop when ||x^{k+1} - x^k||_2 < tol.  Returns (x*,
+    iterations, converged).
     """
     Q = M.prior_Q(model, theta).toarray()
     A = M.obs_matrix(model)
@@ -74,6 +80,7 @@ def poisson_mode(model, theta, tol=1e-8, max_iter=50, x0=None):
         Qc = Q + (A.T @ (A.multiply(wgt[:, None]))).toarray()
         rhs = A.T @ (model.y - mean + wgt * eta)
         xn = sla.cho_solve((np.linalg.cholesky(Qc), True), rhs)
+        xn = capped_step(A, x, xn)
         step = float(np.linalg.norm(xn - x))
         x = xn
         if step < tol:

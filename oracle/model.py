@@ -112,6 +112,19 @@ def glm_loglik(model, eta):
     return poisson_loglik(model, eta) if model.lik == "poisson" else binomial_loglik(model, eta)
 
 
+NEWTON_DETA = 2.0
+
+
+def capped_step(A, x, xn, deta=NEWTON_DETA):
+    """Safeguarded Newton update: x + a (xn - x) with a = min(1, deta / max_i |(A (xn - x))_i|),
+    so that no linear predictor moves by more than deta in one step (the full
+    step from x = 0 overshoots exp(eta) by orders of magnitude on Poisson data)."""
+    d = xn - x
+    m = float(np.abs(A @ d).max()) if d.size else 0.0
+    a = deta / m if m > deta else 1.0
+    return x + a * d
+
+
 def glm_terms(model, eta):
     """First, second and third derivatives of b, where log p(y | eta) =
     y eta - b(eta) + const (canonical link): Poisson b = E e^eta, binomial

@@ -1481,6 +1481,62 @@ void k_obs_assemble(Launch &L, const DevModel &M, int P, const int *active, cons
     L.tick();
   }
 }
+// Largest change of the linear predictor a full Newton step would make:
+// max_i |(A x)_i - eta_i| over the observations (eta = A xprev), per point.
+__global__ void __launch_bounds__(256) newton_deta_kernel(DevModel M, Work W) {
+  const int b = blockIdx.y;
+  if (!W.active[b]) return;
+  __shared__ double red[32];
+  const double *xb = W.x + b * W.sVec;
+  double mx = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M.m; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = fabs(obs_eta(M, xb, i) - W.eta[b * W.sM + i]);
+    mx = (d > mx || d != d) ? d : mx;   // a NaN wins, so that it reaches the step test
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = (v > mx || v != v) ? v : mx;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = (red[k] > m || red[k] != red[k]) ? red[k] : m;
+    W.part[((int64_t)b * NPART + blockIdx.x) * PART_W] = m;
+  }
+}
+
+// x <- xprev + a (x - xprev) with a = min(1, NEWTON_DETA / max change); one block per point.
+__global__ void newton_cap_kernel(DevModel M, Work W, int nparts) {
+  const int b = blockIdx.x;
+  if (!W.active[b]) return;
+  __shared__ double s_a;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      const double v = W.part[((int64_t)b * NPART + p) * PART_W];
+      m = (v > m || v != v) ? v : m;
+    }
+    s_a = (m > NEWTON_DETA) ? NEWTON_DETA / m : 1.0;   // a NaN change keeps a = 1 (the step test fails it)
+    W.sc[b * SC_COUNT + SC_DETA] = m;
+  }
+  __syncthreads();
+  const double a = s_a;
+  if (a == 1.0) return;
+  double *x = W.x + b * W.sVec;
+  const double *xp = W.xprev + b * W.sVec;
+  for (int64_t k = threadIdx.x; k < M.nv; k += blockDim.x) x[k] = fma(a, x[k] - xp[k], xp[k]);
+}
+void k_newton_cap(Launch &L, const DevModel &M, const Work &W) {
+  int nparts = (int)blocks(M.m, 256);
+  if (nparts > 64) nparts = 64;
+  newton_deta_kernel<<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W);
+  L.tick();
+  newton_cap_kernel<<<W.P, 256, 0, L.st>>>(M, W, nparts);
+  L.tick();
+}
+
 // Newton iterations of a captured evaluation: the while-node's body ends here.
 __global__ void newton_continue_kernel(cudaGraphConditionalHandle h, const int *any_active, int *ctr) {
   ++*ctr;

@@ -761,6 +761,7 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
                      W.sArwp, W.Tipp, W.sNb2, W.rhs, W.sVec, W.tippart);
       factor<R>(Ls, M, W, ASM_QC, SC_LOGDET_QC);
       solve<R>(Ls, M, W, W.rhs, W.x);
+      k_newton_cap(Ls, M, W);   // no linear predictor moves by more than NEWTON_DETA in one step
       CUDA_OK(cudaMemsetAsync(W.any_active, 0, sizeof(int), Ls.st));
       k_poisson_step(Ls, M, W, tol, it, max_it, it_dev);
     };

@@ -117,7 +117,7 @@ struct Work {
 
 enum {
   SC_LOGDET_QC = 0, SC_LOGDET_Q, SC_LOGDET_QS, SC_TR_QSI_C, SC_TR_QSI_G, SC_TR_QSI_H,
-  SC_RES2, SC_LOGLIK, SC_TIP_XX, SC_TIP_LX, SC_TIP_TRSIG, SC_TIP_ATA, SC_STEP2,
+  SC_RES2, SC_LOGLIK, SC_TIP_XX, SC_TIP_LX, SC_TIP_TRSIG, SC_TIP_ATA, SC_STEP2, SC_DETA,
   SC_COUNT = 16
 };
 enum {
@@ -289,6 +289,9 @@ void k_obs_assemble(Launch &L, const DevModel &M, int P, const int *active, cons
                     double *tippart);
 void k_poisson_step(Launch &L, const DevModel &M, const Work &W, double tol, int iter, int max_iter,
                     const int *iter_dev = nullptr);
+// Newton step cap: x <- xprev + a (x - xprev), a = min(1, NEWTON_DETA / max_i |(A (x - xprev))_i|)
+constexpr double NEWTON_DETA = 2.0;
+void k_newton_cap(Launch &L, const DevModel &M, const Work &W);
 // graph body: count the Newton iteration and continue the while-node while any point is active
 void k_newton_continue(Launch &L, cudaGraphConditionalHandle h, const int *any_active, int *ctr);
 template <typename R>

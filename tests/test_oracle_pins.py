@@ -397,3 +397,28 @@ def test_poisson_laplace_matches_generic_laplace_formula(lik):
     laplace = h(xs) + 0.5 * n * math.log(2 * math.pi) - 0.5 * np.linalg.slogdet(Hn)[1]
     expect_f = -M.log_prior(mdl, th) - laplace
     assert abs(bta.poisson(mdl, th)["f"] - expect_f) < 1e-7 * abs(expect_f)
+
+
+def test_capped_newton_reaches_the_plain_newton_mode_in_fewer_steps():
+    # the full step from x = 0 overshoots exp(eta) on counts; capping |d eta| at 2 per step
+    # reaches the same mode (the stationary point does not depend on the step length)
+    from synth import CONFIGS, theta_batch
+    c = dict(CONFIGS[5]); c["n_t"] = 2; c["m"] = 6000; c["nx"] = 24
+    mdl = build(**c)
+    th = theta_batch(5, mdl)[0]
+    x_cap, it_cap, ok_cap = bta.poisson_mode(mdl, th, max_iter=60)
+    A = M.obs_matrix(mdl)
+    Q = M.prior_Q(mdl, th)
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    x = np.zeros(mdl.n)
+    for it_plain in range(1, 80):
+        eta = A @ x
+        mean, w, _ = M.glm_terms(mdl, eta)
+        xn = spla.spsolve((Q + A.T @ sp.diags(w) @ A).tocsc(), A.T @ (mdl.y - mean + w * eta))
+        done = np.linalg.norm(xn - x) < 1e-8
+        x = xn
+        if done:
+            break
+    assert ok_cap and it_cap < it_plain
+    np.testing.assert_allclose(x_cap, x, atol=1e-8)
