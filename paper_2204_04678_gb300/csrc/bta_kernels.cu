@@ -850,6 +850,45 @@ __global__ void __launch_bounds__(256) obs_reduce_kernel(DevModel M, Work W, int
   if (threadIdx.x == 0) W.part[((int64_t)b * NPART + blockIdx.x) * PART_W] = s;
 }
 
+// Q_s(theta) = tau^2 (kappa^4 C + 2 kappa^2 G + G C^-1 G) depends on theta_2 (the
+// range) through kappa alone and on theta_3 only through the factor tau^2, so
+// points with the same theta_2 have Q_s equal up to a positive factor: a
+// central-difference stencil has three distinct ranges among its nine points, a
+// 25-point central composite design five.  Within each aligned chunk of
+// QS_SHARE_CHUNK points of a wave, the first point with a given theta_2 is the
+// representative; only representatives run the inversion.
+constexpr int QS_SHARE_CHUNK = 256;
+__global__ void qs_share_setup_kernel(Work W) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= W.P) return;
+  const double k = W.theta[4 * b + 1];
+  int r = b;
+  for (int c = (b / QS_SHARE_CHUNK) * QS_SHARE_CHUNK; c < b; ++c)
+    if (W.theta[4 * c + 1] == k) {   // a NaN range matches nothing and stays its own representative
+      r = c;
+      break;
+    }
+  W.qsrep[b] = r;
+  W.active[b] = (r == b) ? 1 : 0;
+}
+
+// For a point that shares the representative r's Q_s with s = tau_b^2 / tau_r^2:
+// log|Q_s,b| = log|Q_s,r| + n_s log s and tr(Q_s,b^-1 X) = tr(Q_s,r^-1 X) / s.
+__global__ void qs_share_kernel(DevModel M, Work W) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= W.P) return;
+  const int r = W.qsrep[b];
+  if (r == b) return;
+  const double s = W.prm[b].aH / W.prm[r].aH;   // aH = tau^2
+  double *sb = W.sc + b * SC_COUNT;
+  const double *sr = W.sc + r * SC_COUNT;
+  sb[SC_LOGDET_QS] = sr[SC_LOGDET_QS] + M.n_s * log(s);
+  sb[SC_TR_QSI_C] = sr[SC_TR_QSI_C] / s;
+  sb[SC_TR_QSI_G] = sr[SC_TR_QSI_G] / s;
+  sb[SC_TR_QSI_H] = sr[SC_TR_QSI_H] / s;
+  if (W.status[r] != INLA_OK) W.status[b] = W.status[r];
+}
+
 // tr(Q_s^-1 X) for X in {C, G, H}, Q_s^-1 in T1.
 __global__ void qs_traces_kernel(DevModel M, Work W) {
   const int b = blockIdx.x;
@@ -1427,6 +1466,14 @@ void k_obs_reduce(Launch &L, const DevModel &M, const Work &W, int kind) {
   L.tick();
   reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, consecutive(1), W.sc + (kind == 0 ? SC_RES2 : SC_LOGLIK),
                                             SC_COUNT);
+  L.tick();
+}
+void k_qs_share_setup(Launch &L, const Work &W) {
+  qs_share_setup_kernel<<<blocks(W.P, 64), 64, 0, L.st>>>(W);
+  L.tick();
+}
+void k_qs_share(Launch &L, const DevModel &M, const Work &W) {
+  qs_share_kernel<<<blocks(W.P, 64), 64, 0, L.st>>>(M, W);
   L.tick();
 }
 void k_qs_traces(Launch &L, const DevModel &M, const Work &W) {

@@ -470,7 +470,7 @@ Sizes sizes_of(const DevModel &M) {  // element counts per point
 int64_t point_bytes(const DevModel &M, int rb) {
   const Sizes s = sizes_of(M);
   int64_t d = s.theta + s.prm + s.qs + s.Rt + 2 * s.Da + 7 * s.vec + s.wv + 3 * s.nbnp + s.sc + s.pt + s.part +
-              s.tippart + 4 * s.ints + 1;
+              s.tippart + 5 * s.ints + 1;
   if (M.lik != INLA_LIK_GAUSSIAN) d += 4 * s.m + s.AtAp + s.Arwp;
   d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
   const int64_t dense = s.Dinv + 4 * s.mat;
@@ -515,6 +515,7 @@ Work carve(const DevModel &M, void *base, int Pw, int rb) {
   W.active = reinterpret_cast<int *>(take(s.ints));
   W.flags = reinterpret_cast<int *>(take(s.ints));
   W.iters = reinterpret_cast<int *>(take(s.ints));
+  W.qsrep = reinterpret_cast<int *>(take(s.ints));
   W.any_active = reinterpret_cast<int *>(take(1));
   if (M.lik != INLA_LIK_GAUSSIAN) {
     W.eta = take(s.m); W.mu = take(s.m); W.qobs = take(s.m); W.wobs = take(s.m); W.sM = s.m;
@@ -727,10 +728,13 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
   k_qs_values(L, M, W);
   // prior log-determinant (and traces for the adjoint)
   if (o.prior_mode == INLA_PRIOR_KRONECKER) {
-    // one n_s x n_s inversion per point: always in FP64
+    // one n_s x n_s inversion per distinct range parameter: always in FP64
+    k_qs_share_setup(L, W);
     k_assemble_diag<double>(L, M, W, 0, ASM_QS, W.QsI, W.sMat, false);
     gj_invert<double>(L, M, W, W.QsI, W.sMat, W.sc + SC_LOGDET_QS, SC_COUNT);
     if (adj) k_qs_traces(L, M, W);
+    k_qs_share(L, M, W);
+    k_set_active(L, W, 0);
   } else {
     factor<R>(L, M, W, ASM_Q, SC_LOGDET_Q);
     if (adj) {

@@ -107,6 +107,7 @@ struct Work {
   int *active;           // [P]  1 = this point takes part in the current pass
   int *flags;            // [P]  bit 0: selected inversion, bit 1: adjoint gradient
   int *iters;            // [P]
+  int *qsrep;            // [P]  earlier point of the wave whose Q_s this point shares (or itself)
   int *any_active;       // [1]
   // Poisson
   double *eta, *mu, *qobs, *wobs;        // [P][m] eta, weight b''(eta), a_i^T Sigma a_i, adjoint weights
@@ -266,6 +267,9 @@ void k_quadforms(Launch &L, const DevModel &M, const Work &W, const double *u, c
 void k_rhs_gaussian(Launch &L, const DevModel &M, const Work &W);
 void k_obs_reduce(Launch &L, const DevModel &M, const Work &W, int kind);
 void k_qs_traces(Launch &L, const DevModel &M, const Work &W);   // tr(Q_s^-1 X) from W.QsI
+// Kronecker prior: points with the same range parameter share one inversion of Q_s
+void k_qs_share_setup(Launch &L, const Work &W);                  // W.qsrep; active = representatives
+void k_qs_share(Launch &L, const DevModel &M, const Work &W);     // log|Q_s| and traces of the others
 // y = Q_c x (mode ASM_QC) in FP64 from the sparse blocks; r = b - y when b != nullptr
 void k_qc_residual(Launch &L, const DevModel &M, const Work &W, const double *x, const double *b, double *r);
 void k_axpy(Launch &L, const DevModel &M, const Work &W, double *x, const double *d);
