@@ -176,7 +176,7 @@ int inla_model_create(const inla_model_desc *desc, int device, inla_model **out)
  * evaluates B * 9 points.  Errors: INLA_ERR_ARG. */
 int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *opts, size_t *bytes);
 
-/* Evaluate B points.  theta_dev: DEVICE [B][4].  out: DEVICE buffers as
+/* Evaluate B >= 1 points (B = 0 is an argument error).  theta_dev: DEVICE [B][4].  out: DEVICE buffers as
  * above.  stream: a cudaStream_t (NULL = legacy default stream).  Work is
  * enqueued on `stream`; the call returns after enqueueing, except for the
  * Poisson likelihood, whose Newton loop reads a convergence flag back to
