@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
     ap.add_argument("--gemm", default=None, choices=["cuda-core", "tensor"],
                     help="FP32 selected-inversion GEMM: 128x128 FP32 FMA tiles or tcgen05 3xTF32")
+    ap.add_argument("--sweep", default=None, choices=["cuda-core", "tensor"],
+                    help="FP32 block-sweep updates: FP32 FMA tiles (the library's default) or tcgen05 3xTF32")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1,
                     help="stencil centres per step (FD mode) / copies of the batch (adjoint mode); profiling only")
@@ -393,8 +395,11 @@ def main():
         mdl = config_model(cfg)
     centre = theta_batch(cfg, mdl)[0] + 0.01 * rank
     model = pkg.Model(mdl, device=local)
-    if args.gemm:
-        model.set_tiles(32, 64, capi.INLA_GEMM_TF32X3 if args.gemm == "tensor" else 128)
+    n_p = -(-mdl.n_s // 64) * 64
+    tensor_sweep = n_p % 128 == 0 and args.sweep == "tensor"
+    if args.gemm or args.sweep:
+        model.set_tiles(32, capi.INLA_SWEEP_TF32X3 if tensor_sweep else 64,
+                        capi.INLA_GEMM_TF32X3 if args.gemm != "cuda-core" else 128)
     stream = torch.cuda.current_stream()
     if args.grad == "fd":
         cen = centre[None, :] + 0.01 * np.arange(args.centres)[:, None]
@@ -447,7 +452,6 @@ def main():
 
     # dominant instrumented kernel: the sweep's tile update or the selected-inversion GEMM
     fp32 = prec == "mixed"
-    n_p = -(-mdl.n_s // 64) * 64
     tensor_gemm = fp32 and n_p % 128 == 0 and args.gemm != "cuda-core"
     upd_id = capi.KERNEL_GJ_UPDATE32 if fp32 else capi.KERNEL_GJ_UPDATE
     kernels = {"gj_update_kernel": model.profile_read(upd_id), "gemm_nn_kernel": model.profile_read(capi.KERNEL_GEMM)}
@@ -462,10 +466,14 @@ def main():
     kms, knl, kunits = kernels[kname]
     avg_s = kms / 1e3 / max(knl, 1)
     achieved = kunits / max(knl, 1) * flop_per_unit / avg_s / 1e12 if knl else None
-    if kname == "gemm_nn_kernel" and tensor_gemm and tf32x3_peak:
-        peak, bound = tf32x3_peak, "tensor"
-        peak_source = ("MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/BF16 ratio / 3 "
-                       "TF32 products per 3xTF32 product, of measured")
+    tf32_source = ("MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/BF16 ratio / 3 "
+                   "TF32 products per 3xTF32 product, of measured")
+    if kname == "gj_update_kernel" and fp32 and tensor_sweep and tf32x3_peak:
+        peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
+        desc = ("rank-64 update of the FP32 block sweep on the tensor cores (tcgen05, 3xTF32, 128x128 tiles, "
+                "K = 64)")
+    elif kname == "gemm_nn_kernel" and tensor_gemm and tf32x3_peak:
+        peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
         desc = "128x128 tile 3xTF32 GEMM of the selected inversion on the tensor cores (tcgen05)"
     else:
         peak, bound = (peak_fp32 if fp32 else peak_fp64), "alu"
@@ -518,7 +526,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
-                "data": "synthetic", "config": config_dict(cfg, world, grad, prec, points), "clocks": clk,
+                "data": "synthetic", "config": dict(config_dict(cfg, world, grad, prec, points),
+                                                    **({"fp32_sweep": "tensor (tcgen05 3xTF32)" if tensor_sweep
+                                                        else "cuda-core", "fp32_gemm": "tensor (tcgen05 3xTF32)"
+                                                        if tensor_gemm else "cuda-core"} if prec == "mixed" else {})),
+                "clocks": clk,
                 "gpu_launches": launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "f_evals_per_s": 9 * value if grad == "fd" else value,

@@ -93,6 +93,14 @@ enum { INLA_FP64 = 0, INLA_MIXED = 1 };
  * with the 3xTF32 split product, used where n_s rounded up to 64 is a
  * multiple of 128 (elsewhere the 128 x 128 CUDA-core GEMM runs). */
 #define INLA_GEMM_TF32X3 3
+/* FP32 block sweep (inla_set_tiles): 32 or 64 = pivot width with the rank-G
+ * tile updates on the CUDA cores; INLA_SWEEP_TF32X3 = 64-wide pivots with the
+ * rank-64 updates of the lower tiles on the tensor cores (tcgen05, kind::tf32,
+ * 3xTF32 split product; the pivot row and column and the next pivot block stay
+ * on the CUDA cores), used where n_s rounded up to 64 is a multiple of 128
+ * (elsewhere the 64-wide CUDA-core sweep runs).  Not the default: with K = 64
+ * per launch it measured slower than the CUDA-core update on GB300. */
+#define INLA_SWEEP_TF32X3 3
 
 /* Model description.  Every pointer is a HOST pointer; the arrays are read
  * (and copied to the device) by inla_model_create and may be freed after it
@@ -221,8 +229,9 @@ int inla_eval_batch_host(inla_model *model, int B, const double *theta, const in
 /* Tile autotuner (the project's own; no counterpart in the paper).  Times
  * full evaluations of this batch (theta_dev: DEVICE [B][4], opts as for
  * inla_eval_batch) for each candidate block-tile shape of the precision in
- * opts -- the sweep's pivot/tile width (32 or 64) and, in INLA_MIXED, the
- * FP32 GEMM (64, 128 or INLA_GEMM_TF32X3) -- keeps the fastest in the model for later
+ * opts -- the sweep's pivot/tile width (32 or 64; in INLA_MIXED also
+ * INLA_SWEEP_TF32X3) and, in INLA_MIXED, the FP32 GEMM (64, 128 or
+ * INLA_GEMM_TF32X3) -- keeps the fastest in the model for later
  * calls, and writes {FP64 sweep width, FP32 sweep width, FP32 GEMM tile} to
  * choice[3] (may be NULL).  Synchronous; allocates and frees its own trial
  * output buffers; drops captured graphs of the model.  Results of every
@@ -230,9 +239,9 @@ int inla_eval_batch_host(inla_model *model, int B, const double *theta, const in
 int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts, int32_t *choice);
 
 /* Set the tile shapes explicitly (e.g. a choice saved from inla_autotune):
- * sweep widths 32 or 64 for FP64 and FP32 blocks; FP32 GEMM 64, 128 or
- * INLA_GEMM_TF32X3.  A new model starts at (32, 64, INLA_GEMM_TF32X3).
- * Errors: INLA_ERR_ARG for other values. */
+ * sweep width 32 or 64 for FP64 blocks; 32, 64 or INLA_SWEEP_TF32X3 for FP32
+ * blocks; FP32 GEMM 64, 128 or INLA_GEMM_TF32X3.  A new model starts at
+ * (32, 64, INLA_GEMM_TF32X3).  Errors: INLA_ERR_ARG for other values. */
 int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_fp32);
 
 /* Latent dimension n = n_t n_s + n_b of a model. */

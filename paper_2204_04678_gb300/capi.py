@@ -29,6 +29,7 @@ INLA_PRIOR_BTA = 1
 INLA_FP64 = 0
 INLA_MIXED = 1
 INLA_GEMM_TF32X3 = 3
+INLA_SWEEP_TF32X3 = 3
 KERNEL_GJ_UPDATE = 0
 KERNEL_GEMM = 1
 KERNEL_GJ_PIVOT = 2

@@ -510,17 +510,26 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
                : "memory");
 }
 
+// special_only: only the lookahead tile and the tiles of the pivot row and
+// column (grid.y = [1 +] nt), while the tensor cores update the other tiles
+// (sweep_update_tf32x3).
 __global__ void __launch_bounds__(256, 3) gj_update_f32_kernel(float *A, int64_t sA, int n_p, int K, int nt,
                                                            float *Pbuf, const float *Cbuf, const float *Obuf,
                                                            int64_t sCO, double *logdet, int ld_stride, int *status,
-                                                           const int *active) {
+                                                           const int *active, int special_only) {
   constexpr int G = 64;
   using S = Sweep<G>;
   const int b = blockIdx.x;   // points fastest: every point's lookahead tile is among the first blocks
   if (active && !active[b]) return;
   const bool look = K + 1 < nt;
   int I, J;
-  if (look) {
+  if (special_only) {
+    const int y = (int)blockIdx.y - (look ? 1 : 0);   // -1: lookahead; then (K, 0..K-1), (K, K), (K+1..nt-1, K)
+    if (y < 0) { I = K + 1; J = K + 1; }
+    else if (y < K) { I = K; J = y; }
+    else if (y == K) { I = K; J = K; }
+    else { I = y; J = K; }
+  } else if (look) {
     const int nxt = (K + 1) * (K + 2) / 2 + (K + 1);   // linear index of tile (K+1, K+1)
     int x = blockIdx.y;
     if (x == 0) x = nxt;
@@ -820,6 +829,7 @@ void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stri
   R *Cb = reinterpret_cast<R *>(W.gjC);
   R *Ob = reinterpret_cast<R *>(W.gjO);
   const double unit = (double)G * G * G / (64.0 * 64.0 * 64.0);   // one tile product in 64^3 units
+  const bool tensor_update = sizeof(R) == 4 && G == 64 && M.sweep_g32 == INLA_SWEEP_TF32X3 && n_p % 128 == 0;
   for (int K = 0; K < nt; ++K) {
     if (K == 0) {
       L.start(KID_GJ_PIVOT, (double)P);
@@ -839,12 +849,27 @@ void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stri
       L.stop();
       L.tick();
     }
+    if (sizeof(R) == 4 && G == 64 && tensor_update) {
+      // the lookahead tile (with the next pivot inversion) and the pivot row and column on the
+      // CUDA cores, then every other lower tile on the tensor cores
+      const int look = K + 1 < nt ? 1 : 0;
+      L.start(KID_GJ_PIVOT, (double)P);
+      gj_update_f32_kernel<<<dim3(P, look + nt), 256, U32_SMEM, L.st>>>(
+          reinterpret_cast<float *>(A), strideA, n_p, K, nt, reinterpret_cast<float *>(Pb),
+          reinterpret_cast<const float *>(Cb), reinterpret_cast<const float *>(Ob), sCO, logdet_out,
+          logdet_slot_stride, W.status, W.active, 1);
+      L.stop();
+      L.tick();
+      sweep_update_tf32x3(L, P, n_p, reinterpret_cast<float *>(A), strideA, reinterpret_cast<const float *>(Cb),
+                          reinterpret_cast<const float *>(Ob), sCO, K, look ? K + 1 : -1, W.active, W.status);
+      continue;
+    }
     L.start(sizeof(R) == 4 ? KID_GJ_UPDATE32 : KID_GJ_UPDATE, (double)P * (ntri - nt) * unit);
     if (sizeof(R) == 4 && G == 64)
       gj_update_f32_kernel<<<dim3(P, ntri), 256, U32_SMEM, L.st>>>(
           reinterpret_cast<float *>(A), strideA, n_p, K, nt, reinterpret_cast<float *>(Pb),
           reinterpret_cast<const float *>(Cb), reinterpret_cast<const float *>(Ob), sCO, logdet_out,
-          logdet_slot_stride, W.status, W.active);
+          logdet_slot_stride, W.status, W.active, 0);
     else
       gj_update_kernel<R, G><<<dim3(P, ntri), S::THREADS, smem_update<R, G>(), L.st>>>(
           A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride, W.status, W.active);
@@ -871,7 +896,7 @@ void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stride
                int logdet_slot_stride) {
   ensure_attrs<R>();
   const int g = sizeof(R) == 4 ? M.sweep_g32 : M.sweep_g64;
-  if (g == 64) gj_invert_g<R, 64>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
+  if (g == 64 || g == INLA_SWEEP_TF32X3) gj_invert_g<R, 64>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
   else gj_invert_g<R, 32>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
 }
 

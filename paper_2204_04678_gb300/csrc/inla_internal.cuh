@@ -228,6 +228,11 @@ void tc_prepare();
 void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const float *Y, int64_t sY, float *C,
                     int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, bool lower_only,
                     const int *active, int *status);
+// A -= C O^T over the lower 64 x 64 sub-tiles of the FP32 block sweep at pivot
+// `pivot` (rank 64, 3xTF32 on the tensor cores; n_p % 128 == 0), leaving out the
+// pivot row and column and the sub-tile (next, next) (next < 0: none).
+void sweep_update_tf32x3(Launch &L, int P, int n_p, float *A, int64_t sA, const float *Cbuf, const float *Obuf,
+                         int64_t sCO, int pivot, int next, const int *active, int *status);
 
 // bta_kernels.cu
 void k_params(Launch &L, const DevModel &M, const Work &W);

@@ -1,6 +1,14 @@
 // Split-product (3xTF32) GEMM on the fifth-generation tensor cores.
 //
-//   C[b] = alpha X[b] Y[b]^T + beta C0[b]      (n x n, row-major FP32, n % 128 == 0)
+//   C[b] = alpha X[b] Y[b]^T + beta C0[b]      (C: n x n, row-major FP32, n % 128 == 0;
+//                                               X, Y: n x K, row stride ldx, K % 32 == 0)
+//
+// It serves two products.  (1) The FP32 selected inversion (K = ldx = n).
+// (2) The rank-64 update of the FP32 block sweep, A_IJ -= C_I O_J^T over the
+// lower tiles (K = ldx = 64, C = C0 = A, alpha = -1, beta = 1), where the
+// 64 x 64 sub-tiles of the pivot row and column, the upper sub-tiles of the
+// diagonal 128-blocks and the next pivot's sub-tile (which another kernel
+// updates and inverts) are computed but not stored.
 //
 // Used by the FP32 selected inversion (the Takahashi products of Eq.
 // sel_inv_cov on n_s x n_s blocks), where both operands are read along their
@@ -137,9 +145,9 @@ __device__ __forceinline__ void split_store(uint8_t *hi, uint8_t *lo, uint32_t o
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    gemm_tf32x3_kernel(int n, const float *__restrict__ X, int64_t sX, const float *__restrict__ Y, int64_t sY,
-                       float *__restrict__ C, int64_t sC, float alpha, const float *__restrict__ C0, int64_t sC0,
-                       float beta, int lower_only, const int *active, int *status) {
+    gemm_tf32x3_kernel(int n, int K, int ldx, const float *__restrict__ X, int64_t sX, const float *__restrict__ Y,
+                       int64_t sY, float *C, int64_t sC, float alpha, const float *C0, int64_t sC0, float beta,
+                       int lower_only, int sweep_pivot, int sweep_next, const int *active, int *status) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   int ti, tj;
@@ -155,8 +163,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tj = blockIdx.x % nt;
   }
   const int i0 = ti * TCM, j0 = tj * TCM;
-  const float *Xb = X + b * sX + (int64_t)i0 * n;
-  const float *Yb = Y + b * sY + (int64_t)j0 * n;
+  const float *Xb = X + b * sX + (int64_t)i0 * ldx;
+  const float *Yb = Y + b * sY + (int64_t)j0 * ldx;
 
   extern __shared__ uint8_t smraw[];
   __shared__ uint64_t mbar[2];
@@ -186,11 +194,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int idx = tid + TC_THREADS * it, r = idx >> 3, q = idx & 7;
-      xv[it] = __ldg(reinterpret_cast<const float4 *>(Xb + (int64_t)r * n + k0 + 4 * q));
-      yv[it] = __ldg(reinterpret_cast<const float4 *>(Yb + (int64_t)r * n + k0 + 4 * q));
+      xv[it] = __ldg(reinterpret_cast<const float4 *>(Xb + (int64_t)r * ldx + k0 + 4 * q));
+      yv[it] = __ldg(reinterpret_cast<const float4 *>(Yb + (int64_t)r * ldx + k0 + 4 * q));
     }
   };
-  const int nch = n / TCK;
+  const int nch = K / TCK;
   // This thread's 64 entries of the C tile: row 32 * quarter + lane, columns
   // 64 * half .. 64 * half + 63 (a warp reads only its own 32-lane quarter of TMEM).
   const int quarter = warp & 3, half = warp >> 2;
@@ -256,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (!aborted) {
     // the last two stages' partial products
-    for (int c = nch - 2; c < nch; ++c) {
+    for (int c = nch >= 2 ? nch - 2 : 0; c < nch; ++c) {
       const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u);
       if (__syncthreads_or(!ok)) {
         aborted = true;
@@ -269,7 +277,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // wait (bounded) for the MMAs in flight before the tensor memory is released
     mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u);
   }
-  if (!aborted) {
+  // sweep update: this thread's 64 columns lie in one 64 x 64 sub-tile (si, sj)
+  const int si = (i0 + 32 * quarter) >> 6, sj = (j0 >> 6) + half;
+  const bool skip = sweep_pivot >= 0 && (si == sweep_pivot || sj == sweep_pivot || si < sj ||
+                                         (si == sweep_next && sj == sweep_next));
+  if (!aborted && !skip) {
     const int row = i0 + 32 * quarter + lane;
     float *crow = C + b * sC + (int64_t)row * n + j0 + half * 64;
     const float *c0row = C0 ? C0 + b * sC0 + (int64_t)row * n + j0 + half * 64 : nullptr;
@@ -285,7 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       *reinterpret_cast<float4 *>(crow + e) = o;
     }
-  } else if (tid == 0 && status) {
+  } else if (aborted && tid == 0 && status) {
     status[b] = INLA_ERR_TIMEOUT;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -312,8 +324,23 @@ void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const f
   const int nt = n / TCM;
   const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
   L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
-  gemm_tf32x3_kernel<<<dim3(tiles, P), TC_THREADS, TC_SMEM, L.st>>>(n, X, sX, Y, sY, C, sC, alpha, C0, sC0, beta,
-                                                                     lower_only ? 1 : 0, active, status);
+  gemm_tf32x3_kernel<<<dim3(tiles, P), TC_THREADS, TC_SMEM, L.st>>>(n, n, n, X, sX, Y, sY, C, sC, alpha, C0, sC0,
+                                                                     beta, lower_only ? 1 : 0, -1, -1, active,
+                                                                     status);
+  L.stop();
+  L.tick();
+}
+
+void sweep_update_tf32x3(Launch &L, int P, int n_p, float *A, int64_t sA, const float *Cbuf, const float *Obuf,
+                         int64_t sCO, int pivot, int next, const int *active, int *status) {
+  tc_prepare();
+  const int nt2 = n_p / TCM, nt = n_p / 64;
+  const int tiles = nt2 * (nt2 + 1) / 2;
+  // stored 64^3 sub-tile products: the lower tiles minus the pivot row and column and the next pivot
+  const double units = (double)P * (nt * (nt + 1) / 2 - nt - (next >= 0 ? 1 : 0));
+  L.start(KID_GJ_UPDATE32, units);
+  gemm_tf32x3_kernel<<<dim3(tiles, P), TC_THREADS, TC_SMEM, L.st>>>(n_p, 64, 64, Cbuf, sCO, Obuf, sCO, A, sA, -1.0f,
+                                                                     A, sA, 1.0f, 1, pivot, next, active, status);
   L.stop();
   L.tick();
 }

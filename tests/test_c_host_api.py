@@ -33,7 +33,7 @@ def test_c_program_compiles_and_links(exe):
 @pytest.mark.gpu
 def test_c_program_matches_oracle(exe):
     theta = np.array([0.9, -1.1, 0.1, 1.4])
-    r = subprocess.run([exe, *map(repr, theta)], capture_output=True, text=True, timeout=300)
+    r = subprocess.run([exe, *(f"{x:.17g}" for x in theta)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     v = r.stdout.split()
     f, g, status = float(v[0]), np.array([float(x) for x in v[1:5]]), int(v[5])

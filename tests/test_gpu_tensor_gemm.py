@@ -68,10 +68,10 @@ def test_invalid_sizes_rejected(pkg):
         pkg.gemm_tf32x3(X, X)
 
 
-def _mixed_vs_oracle(pkg, mdl, th, gemm):
+def _mixed_vs_oracle(pkg, mdl, th, gemm, sweep=64):
     model = pkg.Model(mdl)
     try:
-        model.set_tiles(32, 64, gemm)
+        model.set_tiles(32, sweep, gemm)
         r = model.eval(torch.tensor(th, dtype=torch.float64, device="cuda"), grad="adjoint", precision="mixed",
                        want_mode=True, want_marg_var=True)
         torch.cuda.synchronize()
@@ -114,5 +114,43 @@ def test_mixed_tensor_gemm_full_size_config2(pkg):
         assert np.all(np.abs(fm - fd) <= MIX_F * np.abs(fd))
         gd, gm = d["grad"].cpu().numpy(), m["grad"].cpu().numpy()
         assert np.abs(gm - gd).max() <= MIX_G * max(1.0, np.abs(gd).max())
+    finally:
+        model.close()
+
+
+@pytest.mark.parametrize("lik,nx", [("gaussian", 16), ("poisson", 16), ("binomial", 16), ("gaussian", 23)])
+def test_mixed_with_tensor_sweep_matches_oracle(pkg, lik, nx):
+    """The rank-64 updates of the FP32 block sweep on the tensor cores: n_s = 256
+    gives four 64-wide pivots and two 128-wide tensor tiles per block side (the
+    masks for the pivot row and column and the next pivot cross tile borders);
+    n_s = 529 (n_p = 576, not a multiple of 128) takes the CUDA-core sweep."""
+    from paper_2204_04678_gb300 import capi
+    mdl = build("tcs", 3, nx, 2, 1500, lik, seed=4)
+    th = mdl.theta_true[None, :] + np.array([[0.0, 0.0, 0.0, 0.0], [0.1, -0.1, 0.05, -0.2]])
+    _mixed_vs_oracle(pkg, mdl, th, capi.INLA_GEMM_TF32X3, sweep=capi.INLA_SWEEP_TF32X3)
+
+
+def test_tensor_sweep_full_size_config2(pkg):
+    """n_t = 50, 32 x 32 grid: the mixed path with the tensor-core sweep against
+    the FP64 path and against the mixed path with the CUDA-core sweep."""
+    from paper_2204_04678_gb300 import capi
+    mdl = config_model(2)
+    model = pkg.Model(mdl)
+    try:
+        th = torch.tensor(fd_stencil(theta_batch(2, mdl)[0]), dtype=torch.float64, device="cuda")
+        d = model.eval(th, grad="adjoint", precision="fp64", want_marg_var=True)
+        model.set_tiles(32, capi.INLA_SWEEP_TF32X3, capi.INLA_GEMM_TF32X3)
+        t = model.eval(th, grad="adjoint", precision="mixed", want_marg_var=True)
+        model.set_tiles(32, 64, capi.INLA_GEMM_TF32X3)
+        c = model.eval(th, grad="adjoint", precision="mixed", want_marg_var=True)
+        torch.cuda.synchronize()
+        fd_, ft, fc = (o["f"].cpu().numpy() for o in (d, t, c))
+        assert np.all(t["status"].cpu().numpy() == 0)
+        assert np.all(np.abs(ft - fd_) <= MIX_F * np.abs(fd_))
+        assert np.all(np.abs(ft - fc) <= MIX_F * np.abs(fd_))
+        gd, gt = d["grad"].cpu().numpy(), t["grad"].cpu().numpy()
+        assert np.abs(gt - gd).max() <= MIX_G * max(1.0, np.abs(gd).max())
+        vd, vt = d["marg_var"].cpu().numpy(), t["marg_var"].cpu().numpy()
+        assert np.max(np.abs(vt - vd) / vd) <= MIX_V
     finally:
         model.close()
