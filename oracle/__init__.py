@@ -20,6 +20,7 @@ Modules
   scalar  element-wise recursions on tiny matrices (Cholesky, Eq. backward_solve,
           Eq. sel_inv_cov, Eq. takahashi_recursion)
   fd      central differences (Eq. central_diff)
+  tf32    the TF32 split product of the mixed path's tensor-core products (error model)
 
 Parity status: every function is pinned by tests under tests/ against closed
 forms, brute force and invariants; the Poisson Laplace value is pinned only

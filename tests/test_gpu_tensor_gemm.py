@@ -154,3 +154,27 @@ def test_tensor_sweep_full_size_config2(pkg):
         assert np.max(np.abs(vt - vd) / vd) <= MIX_V
     finally:
         model.close()
+
+
+def test_split_product_matches_the_oracle_emulation(pkg):
+    """Against the oracle's emulation of the 3xTF32 split (oracle.tf32): bit for
+    bit on integer matrices (TF32 values whose partial sums stay below 2^24, so
+    no step of the product rounds), and within FP32 accumulation error of the
+    emulated split product on random FP32 matrices."""
+    from oracle import tf32
+    s = Stream(77, 0)
+    n, batch = 256, 2
+    Xi = (s.integers(batch * n * n, 65) - 32).reshape(batch, n, n).astype(np.float32)
+    Yi = (s.integers(batch * n * n, 65) - 32).reshape(batch, n, n).astype(np.float32)
+    C, st = pkg.gemm_tf32x3(torch.tensor(Xi, device="cuda"), torch.tensor(Yi, device="cuda"))
+    torch.cuda.synchronize()
+    assert int(st.abs().sum()) == 0
+    emu = tf32.product_3xtf32(Xi, Yi)
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), emu)
+    X = s.normal(batch * n * n).reshape(batch, n, n).astype(np.float32)
+    Y = s.normal(batch * n * n).reshape(batch, n, n).astype(np.float32)
+    C, st = pkg.gemm_tf32x3(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"))
+    torch.cuda.synchronize()
+    absprod = np.einsum("bik,bjk->bij", np.abs(X.astype(np.float64)), np.abs(Y.astype(np.float64)))
+    err = np.abs(C.cpu().numpy().astype(np.float64) - tf32.product_3xtf32(X, Y))
+    assert np.all(err <= 2.0 ** -18 * absprod)

@@ -422,3 +422,49 @@ def test_capped_newton_reaches_the_plain_newton_mode_in_fewer_steps():
             break
     assert ok_cap and it_cap < it_plain
     np.testing.assert_allclose(x_cap, x, atol=1e-8)
+
+
+# ---------------------------------------------------------------- TF32 split product (mixed path)
+
+def test_tf32_rounding_is_nearest_ties_away():
+    from oracle import tf32
+    one = np.float32(1.0)
+    ulp = np.float32(2.0 ** -10)                  # TF32 unit in the last place at 1
+    exact = np.array([0.0, 1.0, -0.75, 1.5, 2047.0, -1024.0, 2.0 ** -20, 3.0 * 2 ** 40], dtype=np.float32)
+    assert np.array_equal(tf32.tf32_rna(exact), exact)
+    half = np.float32(one + ulp / 2)              # halfway between 1 and 1 + 2^-10
+    assert tf32.tf32_rna(half) == one + ulp and tf32.tf32_rna(-half) == -(one + ulp)
+    assert tf32.tf32_rna(np.float32(one + ulp / 4)) == one
+    assert tf32.tf32_rna(np.float32(one + 3 * ulp / 4)) == one + ulp
+    x = np.random.default_rng(0).standard_normal(100000).astype(np.float32)
+    r = tf32.tf32_rna(x)
+    assert np.all(r.view(np.uint32) & 0x1FFF == 0)                      # 10 explicit mantissa bits
+    assert np.all(np.abs(r.astype(np.float64) - x) <= 2.0 ** -11 * np.abs(x.astype(np.float64)))
+
+
+def test_tf32_split_recovers_fp32_value():
+    from oracle import tf32
+    x = (np.random.default_rng(1).standard_normal(100000) * 10.0 ** np.random.default_rng(2).integers(
+        -6, 6, 100000)).astype(np.float32)
+    hi, lo = tf32.split(x)
+    assert np.all(hi.view(np.uint32) & 0x1FFF == 0) and np.all(lo.view(np.uint32) & 0x1FFF == 0)
+    err = np.abs(x.astype(np.float64) - hi.astype(np.float64) - lo.astype(np.float64))
+    assert np.all(err <= 2.0 ** -22 * np.abs(x.astype(np.float64)))
+
+
+def test_tf32_split_product_error_model():
+    from oracle import tf32
+    rng = np.random.default_rng(3)
+    # integers of at most 11 significant bits are TF32 values: the split product is exact
+    Xi = rng.integers(-32, 33, (64, 256)).astype(np.float32)
+    Yi = rng.integers(-32, 33, (48, 256)).astype(np.float32)
+    assert np.array_equal(tf32.product_3xtf32(Xi, Yi), Xi.astype(np.float64) @ Yi.astype(np.float64).T)
+    # FP32 inputs: the three kept terms miss lo*lo and the rounding of lo, each below 2^-22 |x||y|
+    X = rng.standard_normal((64, 256)).astype(np.float32)
+    Y = rng.standard_normal((48, 256)).astype(np.float32)
+    exact = X.astype(np.float64) @ Y.astype(np.float64).T
+    bound = 3 * 2.0 ** -22 * (np.abs(X.astype(np.float64)) @ np.abs(Y.astype(np.float64)).T)
+    err = np.abs(tf32.product_3xtf32(X, Y) - exact)
+    assert np.all(err <= bound)
+    single = np.abs(tf32.tf32_rna(X).astype(np.float64) @ tf32.tf32_rna(Y).astype(np.float64).T - exact)
+    assert err.max() < single.max() / 100
