@@ -494,7 +494,8 @@ def main():
                 "K = 64)")
     elif kname == "gemm_nn_kernel" and tensor_gemm and tf32x3_peak:
         peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
-        desc = "128x128 tile 3xTF32 GEMM of the selected inversion on the tensor cores (tcgen05)"
+        desc = ("128x128 tile 3xTF32 GEMM of the selected inversion on the tensor cores (tcgen05, operands "
+                "split once and loaded by TMA)")
     else:
         peak, bound = (peak_fp32 if fp32 else peak_fp64), "alu"
         peak_source = ("measured on this GPU: " + ("FP32" if fp32 else "FP64")

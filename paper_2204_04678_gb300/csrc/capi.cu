@@ -475,7 +475,8 @@ int64_t point_bytes(const DevModel &M, int rb) {
               s.tippart + 5 * s.ints + 1;
   if (M.lik != INLA_LIK_GAUSSIAN) d += 4 * s.m + s.AtAp + s.Arwp;
   d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
-  const int64_t dense = s.Dinv + 4 * s.mat;
+  const int64_t split = (rb == 4 && M.n_p % 128 == 0) ? 6 * s.mat : 0;   // TF32 hi / lo operands
+  const int64_t dense = s.Dinv + 4 * s.mat + split;
   return d * 8 + rup(dense * rb, 256) + 64 * 256;   // slack: each array starts on 256 bytes
 }
 
@@ -506,6 +507,10 @@ Work carve(const DevModel &M, void *base, int Pw, int rb) {
   W.sVec = s.vec;
   W.wv = take(s.wv); W.sWV = s.wv;
   W.T1 = take_r(s.mat); W.S = take_r(s.mat); W.SigN = take_r(s.mat); W.SigC = take_r(s.mat); W.sMat = s.mat;
+  if (rb == 4 && M.n_p % 128 == 0) {
+    float **parts[6] = {&W.Dh, &W.Dl, &W.Sh, &W.Sl, &W.Uh, &W.Ul};
+    for (float **q : parts) *q = static_cast<float *>(take_r(s.mat));
+  }
   W.SigAn = take(s.nbnp); W.SigAc = take(s.nbnp); W.Y = take(s.nbnp); W.sNbNp = s.nbnp;
   W.gjP = take(s.gjP); W.gjC = take(s.gjCO); W.gjO = take(s.gjCO);
   W.QsI = take(s.mat);
@@ -690,13 +695,15 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
     if (M.n_b > 0) k_dinv_apply<R>(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
     if (tensor_gemm<R>(M)) {
       // U = D^-1 S^T (= (S D^-1)^T, D^-1 symmetric), then Sigma_tt = D^-1 U^T + D^-1:
-      // both products read their operands along rows (X Y^T), as the tensor-core kernel wants
+      // both products read their operands along rows (X Y^T), as the tensor-core kernel wants.
+      // D^-1 and S are split into TF32 hi / lo parts once; U is stored split by the first product.
       const float *Df = reinterpret_cast<const float *>(Dt);
-      float *Uf = reinterpret_cast<float *>(T1);
-      gemm_nt_tf32x3(L, W.P, M.n_p, Df, W.sDinv, reinterpret_cast<const float *>(S), W.sMat, Uf, W.sMat, 1.0f,
-                     nullptr, 0, 0.0f, false, W.active, W.status);
-      gemm_nt_tf32x3(L, W.P, M.n_p, Df, W.sDinv, Uf, W.sMat, reinterpret_cast<float *>(SigC), W.sMat, 1.0f, Df,
-                     W.sDinv, 1.0f, true, W.active, W.status);
+      split_tf32(L, W.P, Df, W.sDinv, W.Dh, W.Dl, W.sMat, np2, W.active);
+      split_tf32(L, W.P, reinterpret_cast<const float *>(S), W.sMat, W.Sh, W.Sl, W.sMat, np2, W.active);
+      gemm_nt_tf32x3_split(L, W.P, M.n_p, W.Dh, W.Dl, W.sMat, W.Sh, W.Sl, W.sMat, nullptr, W.sMat, 1.0f, nullptr, 0,
+                           0.0f, W.Uh, W.Ul, false, W.active, W.status);
+      gemm_nt_tf32x3_split(L, W.P, M.n_p, W.Dh, W.Dl, W.sMat, W.Uh, W.Ul, W.sMat, reinterpret_cast<float *>(SigC),
+                           W.sMat, 1.0f, Df, W.sDinv, 1.0f, nullptr, nullptr, true, W.active, W.status);
     } else {
       const int tile = M.gemm_t32 == INLA_GEMM_TF32X3 ? 128 : M.gemm_t32;   // CUDA-core fallback
       gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, tile);

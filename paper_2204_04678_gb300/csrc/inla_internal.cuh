@@ -96,6 +96,8 @@ struct Work {
   double *rvec, *dvec;                   // [P][nv]  refinement residual and correction
   double *wv;            // [P][1+n_b][n_p]  Dinv_t times vectors
   void *T1, *S, *SigN, *SigC;            // [P][n_p][n_p]  (R)
+  float *Dh, *Dl, *Sh, *Sl, *Uh, *Ul;    // [P][n_p][n_p]  TF32 hi / lo parts of the tensor-core products' operands
+                                         //                (FP32 blocks with n_p % 128 == 0 only)
   double *SigAn, *SigAc, *Y;             // [P][n_b][n_p]
   void *gjP, *gjC, *gjO;                 // [P][2][32*32], [P][n_p*32], [P][n_p*32]  (R; sized for double)
   double *QsI;                           // [P][n_p][n_p]  Q_s^-1 (Kronecker prior), always FP64
@@ -228,6 +230,16 @@ void tc_prepare();
 void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const float *Y, int64_t sY, float *C,
                     int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, bool lower_only,
                     const int *active, int *status);
+// The same product with operands already split into TF32 hi / lo parts (P
+// matrices each, sX / sY floats apart), fed by TMA; with Chi != nullptr the
+// result is stored split (Chi / Clo, stride sC) instead of to C.
+void gemm_nt_tf32x3_split(Launch &L, int P, int n, const float *Xh, const float *Xl, int64_t sX, const float *Yh,
+                          const float *Yl, int64_t sY, float *C, int64_t sC, float alpha, const float *C0,
+                          int64_t sC0, float beta, float *Chi, float *Clo, bool lower_only, const int *active,
+                          int *status);
+// hi = tf32(x), lo = tf32(x - hi) for P matrices of `count` floats (count % 4 == 0).
+void split_tf32(Launch &L, int P, const float *src, int64_t ssrc, float *hi, float *lo, int64_t sdst, int64_t count,
+                const int *active);
 // A -= C O^T over the lower 64 x 64 sub-tiles of the FP32 block sweep at pivot
 // `pivot` (rank 64, 3xTF32 on the tensor cores; n_p % 128 == 0), leaving out the
 // pivot row and column and the sub-tile (next, next) (next < 0: none).

@@ -37,9 +37,12 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer); a wait that runs out
 // marks the point INLA_ERR_TIMEOUT, skips the epilogue, releases the tensor
 // memory and returns.
+#include <cuda.h>   // CUtensorMap and the tensor-map encoder's types (the encoder is looked up at run time)
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <stdexcept>
+#include <string>
 
 #include "inla_internal.cuh"
 
@@ -308,13 +311,288 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------------ TMA-fed variant
+//
+// The selected inversion's two products with operands split into TF32 hi / lo
+// parts once in global memory (split_tf32_kernel, and the first product's
+// epilogue for its output), so that each stage's four 128 x 32 slabs arrive
+// by TMA (cp.async.bulk.tensor, 128-byte swizzle: the K-major layout the MMA
+// descriptors read) instead of being loaded, split and stored by the CTA's
+// threads.  Three stages of shared memory; the copies of chunk c + 1 are
+// issued as soon as the MMAs of chunk c - 2 (the stage's previous user) have
+// completed, so that they overlap the MMAs of chunk c - 1 and the drain of
+// chunk c - 2.  The MMAs, accumulators, drains and epilogue are those of
+// gemm_tf32x3_kernel, in the same order, so the results are the same.
+constexpr int TMA_STAGES = 3;
+constexpr int TMA_SMEM = TMA_STAGES * STAGE_BYTES + 1024;
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_slab(uint32_t dst, const CUtensorMap *map, int k0, int row0, int b,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(k0), "r"(row0), "r"(b), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tf32x3_tma_kernel(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+                           const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl, int n,
+                           float *C, int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, float *Chi,
+                           float *Clo, int lower_only, const int *active, int *status) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  int ti, tj;
+  if (lower_only) {
+    const int t = blockIdx.x;
+    ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    tj = t - ti * (ti + 1) / 2;
+  } else {
+    const int nt = n / TCM;
+    ti = blockIdx.x / nt;
+    tj = blockIdx.x % nt;
+  }
+  const int i0 = ti * TCM, j0 = tj * TCM;
+
+  extern __shared__ uint8_t smraw[];
+  __shared__ uint64_t full[TMA_STAGES];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const uint32_t raw = smem_addr(smraw);
+  uint8_t *base = smraw + (((raw + 1023u) & ~1023u) - raw);   // 1024-aligned for the swizzle atoms
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < TMA_STAGES; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[i])), "r"(1u) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1u) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  const int nch = n / TCK;
+  // the four slabs of chunk c into stage c % TMA_STAGES (thread 0)
+  auto issue = [&](int c) {
+    const int s = c % TMA_STAGES;
+    const uint32_t st = smem_addr(base + s * STAGE_BYTES), bar = smem_addr(&full[s]);
+    mbar_expect_tx(bar, (uint32_t)STAGE_BYTES);
+    tma_load_slab(st, &mXh, c * TCK, i0, b, bar);
+    tma_load_slab(st + SLAB_BYTES, &mXl, c * TCK, i0, b, bar);
+    tma_load_slab(st + 2 * SLAB_BYTES, &mYh, c * TCK, j0, b, bar);
+    tma_load_slab(st + 3 * SLAB_BYTES, &mYl, c * TCK, j0, b, bar);
+  };
+  if (tid == 0)
+    for (int c = 0; c < TMA_STAGES && c < nch; ++c) issue(c);
+  int issued = nch < TMA_STAGES ? nch : TMA_STAGES;   // chunks whose copies were issued
+
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
+  float racc[64];
+#pragma unroll
+  for (int e = 0; e < 64; ++e) racc[e] = 0.0f;
+  auto drain = [&](int s) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      uint32_t big[32], small[32];
+      const uint32_t col = (uint32_t)(2 * s * TCM + half * 64 + cc * 32);
+      tmem_ld32(tmem + lane_addr + col, big);
+      tmem_ld32(tmem + lane_addr + col + TCM, small);
+#pragma unroll
+      for (int e = 0; e < 32; ++e) racc[cc * 32 + e] += __uint_as_float(big[e]) + __uint_as_float(small[e]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+  bool aborted = false;
+  int last = -1;     // last chunk whose MMAs were committed
+  int consumed = 0;  // chunks whose copies were waited for
+  for (int c = 0; c < nch; ++c) {
+    const int a = c & 1, s = c % TMA_STAGES;
+    if (c >= 2) {
+      // accumulator pair a and the stage of chunk c - 2 are free once its MMAs completed
+      const bool ok = mbar_wait(smem_addr(&mbar[a]), (uint32_t)((c - 2) >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      if (tid == 0 && c + 1 < nch) issue(c + 1);
+      if (c + 1 < nch) issued = c + 2;
+      drain(a);
+    }
+    const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)(c / TMA_STAGES) & 1u);
+    consumed = c + 1;
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t xh = smem_addr(base + s * STAGE_BYTES), xl = xh + SLAB_BYTES, yh = xh + 2 * SLAB_BYTES,
+                     yl = xh + 3 * SLAB_BYTES;
+      const uint32_t big = tmem + (uint32_t)(2 * a * TCM), small = big + TCM;
+#pragma unroll
+      for (int ks = 0; ks < TCK / 8; ++ks) {   // K = 8 TF32 = 32 bytes per MMA
+        const uint32_t o = 32u * ks, acc = ks > 0 ? 1u : 0u;
+        mma_tf32(small, sw128_desc(xl + o), sw128_desc(yh + o), acc);
+        mma_tf32(small, sw128_desc(xh + o), sw128_desc(yl + o), 1u);
+        mma_tf32(big, sw128_desc(xh + o), sw128_desc(yh + o), acc);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&mbar[a]))
+                   : "memory");
+    }
+    last = c;
+  }
+  if (!aborted) {
+    for (int c = nch >= 2 ? nch - 2 : 0; c < nch; ++c) {
+      const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        aborted = true;
+        break;
+      }
+      drain(c & 1);
+    }
+  }
+  if (aborted) {
+    // wait (bounded) for the copies and the MMAs in flight before the memory is released
+    for (int c = consumed; c < issued; ++c)
+      mbar_wait(smem_addr(&full[c % TMA_STAGES]), (uint32_t)(c / TMA_STAGES) & 1u);
+    if (last >= 0) mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u);
+  }
+  if (!aborted) {
+    const int row = i0 + 32 * quarter + lane;
+    const int64_t off = (int64_t)row * n + j0 + half * 64;
+    const float *c0row = C0 ? C0 + b * sC0 + off : nullptr;
+#pragma unroll
+    for (int e = 0; e < 64; e += 4) {
+      float4 o = make_float4(alpha * racc[e], alpha * racc[e + 1], alpha * racc[e + 2], alpha * racc[e + 3]);
+      if (c0row) {
+        const float4 z = *reinterpret_cast<const float4 *>(c0row + e);
+        o.x += beta * z.x;
+        o.y += beta * z.y;
+        o.z += beta * z.z;
+        o.w += beta * z.w;
+      }
+      if (Chi) {   // the result split for use as the next product's operand
+        uint4 h, l;
+        h.x = tf32_rna(o.x);
+        h.y = tf32_rna(o.y);
+        h.z = tf32_rna(o.z);
+        h.w = tf32_rna(o.w);
+        l.x = tf32_rna(o.x - __uint_as_float(h.x));
+        l.y = tf32_rna(o.y - __uint_as_float(h.y));
+        l.z = tf32_rna(o.z - __uint_as_float(h.z));
+        l.w = tf32_rna(o.w - __uint_as_float(h.w));
+        *reinterpret_cast<uint4 *>(Chi + b * sC + off + e) = h;
+        *reinterpret_cast<uint4 *>(Clo + b * sC + off + e) = l;
+      } else {
+        *reinterpret_cast<float4 *>(C + b * sC + off + e) = o;
+      }
+    }
+  } else if (tid == 0 && status) {
+    status[b] = INLA_ERR_TIMEOUT;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// hi = tf32(x), lo = tf32(x - hi) for every entry of P matrices of `count` floats.
+__global__ void split_tf32_kernel(const float *__restrict__ src, int64_t ssrc, float *__restrict__ hi,
+                                  float *__restrict__ lo, int64_t sdst, int64_t count, const int *active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (q >= count) return;
+  const float4 v = *reinterpret_cast<const float4 *>(src + b * ssrc + q);
+  split_store(reinterpret_cast<uint8_t *>(hi + b * sdst + q), reinterpret_cast<uint8_t *>(lo + b * sdst + q), 0u,
+              v);
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+      throw std::runtime_error("the driver does not provide cuTensorMapEncodeTiled");
+    fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// P row-major n x n FP32 matrices, `point_stride` floats apart; one box is a
+// 128-row x 32-float slab (128 bytes per row, 128-byte swizzle).
+CUtensorMap slab_map(const float *base, int n, int P, int64_t point_stride) {
+  CUtensorMap m;
+  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)P};
+  const cuuint64_t strides[2] = {(cuuint64_t)n * 4u, (cuuint64_t)point_stride * 4u};
+  const cuuint32_t box[3] = {(cuuint32_t)TCK, (cuuint32_t)TCM, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
 }  // namespace
 
 void tc_prepare() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  cudaFuncSetAttribute(gemm_tf32x3_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM);
   done = true;
+}
+
+void split_tf32(Launch &L, int P, const float *src, int64_t ssrc, float *hi, float *lo, int64_t sdst, int64_t count,
+                const int *active) {
+  const int64_t quads = count / 4;
+  split_tf32_kernel<<<dim3((unsigned)((quads + 255) / 256), P), 256, 0, L.st>>>(src, ssrc, hi, lo, sdst, count,
+                                                                                 active);
+  L.tick();
+}
+
+void gemm_nt_tf32x3_split(Launch &L, int P, int n, const float *Xh, const float *Xl, int64_t sX, const float *Yh,
+                          const float *Yl, int64_t sY, float *C, int64_t sC, float alpha, const float *C0,
+                          int64_t sC0, float beta, float *Chi, float *Clo, bool lower_only, const int *active,
+                          int *status) {
+  tc_prepare();
+  const CUtensorMap mXh = slab_map(Xh, n, P, sX), mXl = slab_map(Xl, n, P, sX);
+  const CUtensorMap mYh = slab_map(Yh, n, P, sY), mYl = slab_map(Yl, n, P, sY);
+  const int nt = n / TCM;
+  const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
+  L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
+  gemm_tf32x3_tma_kernel<<<dim3(tiles, P), TC_THREADS, TMA_SMEM, L.st>>>(
+      mXh, mXl, mYh, mYl, n, C, sC, alpha, C0, sC0, beta, Chi, Clo, lower_only ? 1 : 0, active, status);
+  L.stop();
+  L.tick();
 }
 
 void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const float *Y, int64_t sY, float *C,
