@@ -21,6 +21,7 @@
 // staged through shared memory with conflict-free access (padded rows).
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "inla_internal.cuh"
@@ -800,10 +801,16 @@ constexpr size_t smem_update() {
 template <typename R, int G>
 constexpr size_t smem_pivot() { return Sweep<G>::SMEM_ELEMS * sizeof(R); }
 
+// Kernel attributes belong to the device's context: they are set once for
+// every device the process uses (the first call with that device current).
 template <typename R>
 void ensure_attrs() {
-  static bool done = false;
-  if (done) return;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
   cudaFuncSetAttribute(gemm_nn_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gemm<R>());
   // 64-wide FP64 tiles need more than the default 48 KB of dynamic shared memory
   cudaFuncSetAttribute(gj_update_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -813,7 +820,7 @@ void ensure_attrs() {
   cudaFuncSetAttribute(gj_pivot_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pivot<R, 64>());
   if (sizeof(R) == 4)
     cudaFuncSetAttribute(gj_update_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, U32_SMEM);
-  done = true;
+  done[dev] = true;
 }
 
 // Block sweep inversion with G x G pivots (see the kernels above).

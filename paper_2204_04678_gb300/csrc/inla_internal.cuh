@@ -140,6 +140,7 @@ enum {
 enum { ASM_QC = 0, ASM_Q = 1, ASM_QS = 2 };
 
 // Optional CUDA-event timing of selected kernels (inla_profile_*).
+constexpr int kMaxDevices = 256;   // device indices the per-device caches cover
 enum { KID_GJ_UPDATE = 0, KID_GEMM = 1, KID_GJ_PIVOT = 2, KID_GJ_PANEL = 3, KID_GJ_UPDATE32 = 4, KID_COUNT = 5 };
 struct Profiler {
   int enabled = 0;      // 0 = off, k >= 1: time every k-th launch of each kernel

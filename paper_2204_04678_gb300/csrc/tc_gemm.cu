@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 
@@ -533,16 +534,17 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+EncodeTiled lookup_encoder() {
+  void *p = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+    throw std::runtime_error("the driver does not provide cuTensorMapEncodeTiled");
+  return reinterpret_cast<EncodeTiled>(p);
+}
+
 EncodeTiled encoder() {
-  static EncodeTiled fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
-      throw std::runtime_error("the driver does not provide cuTensorMapEncodeTiled");
-    fn = reinterpret_cast<EncodeTiled>(p);
-  }
+  static const EncodeTiled fn = lookup_encoder();   // initialised once, thread-safe
   return fn;
 }
 
@@ -563,12 +565,17 @@ CUtensorMap slab_map(const float *base, int n, int P, int64_t point_stride) {
 
 }  // namespace
 
+// Kernel attributes belong to the device's context: set once per device.
 void tc_prepare() {
-  static bool done = false;
-  if (done) return;
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
   cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   cudaFuncSetAttribute(gemm_tf32x3_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM);
-  done = true;
+  done[dev] = true;
 }
 
 void split_tf32(Launch &L, int P, const float *src, int64_t ssrc, float *hi, float *lo, int64_t sdst, int64_t count,
