@@ -10,7 +10,7 @@
  *     pi~(theta|y) = pi(theta) pi(x|theta) pi(y|x,theta) / pi_G(x|theta,y) at x = x*(theta),
  *   together with its gradient (central differences, Eq. central_diff, or
  *   an adjoint of the same formula), the latent mode x*(theta) (Sec. 2.2;
- *   Newton iteration for a Poisson likelihood), and the marginal variances
+ *   Newton iteration for Poisson and binomial data), and the marginal variances
  *   diag(Q_c(theta)^-1) by selected inversion (Sec. 2.3, Sec. 2.4.2,
  *   Eq. sel_inv_cov / Eq. takahashi_recursion).
  *
@@ -18,12 +18,13 @@
  *   Q(theta)   = Q_t(rho) (x) Q_s(kappa, tau) (+) tau_b I_{n_b},
  *   Q_s        = tau^2 (kappa^4 C + 2 kappa^2 G + G C^-1 G)   (SPDE, alpha = 2),
  *   Q_t        = stationary AR(1) precision, unit marginal variance,
- *   Q_c(theta) = Q(theta) + A^T D A,  D = tau_y I (Gaussian) or diag(E e^eta) (Poisson),
+ *   Q_c(theta) = Q(theta) + A^T D A,  D = tau_y I (Gaussian) or diag(b''(eta)) at the
+ *   current latent field (Poisson: E e^eta; binomial: N p (1 - p)),
  * latent vector ordered time-major with the n_b fixed effects last, so
  * Q and Q_c are block tridiagonal with an arrowhead (Fig. arrowhead_matrices).
  * theta = (theta_1..theta_4): Gaussian: (log tau_y, log range, log sigma,
  * logit rho) with kappa = sqrt(8)/range, tau^2 = 1/(4 pi kappa^2 sigma^2) and
- * tau_b fixed by the model; Poisson: theta_1 = log tau_b instead of log tau_y.
+ * tau_b fixed by the model; Poisson and binomial data: theta_1 = log tau_b instead of log tau_y.
  * The prior pi(theta) is a product of independent normals.
  *
  * Conventions
@@ -136,8 +137,8 @@ typedef struct {
   int32_t precision;      /* INLA_FP64 or INLA_MIXED                               */
   int32_t want_mode;      /* nonzero: write x*(theta) to out->x_mode               */
   int32_t want_marg_var;  /* nonzero: write diag(Q_c^-1) to out->marg_var          */
-  int32_t max_newton;     /* Poisson: iteration limit (<= 0: 50)                   */
-  double newton_tol;      /* Poisson: stop when ||x^{k+1} - x^k||_2 < tol (<= 0: 1e-8) */
+  int32_t max_newton;     /* Poisson/binomial: iteration limit (<= 0: 50)          */
+  double newton_tol;      /* Poisson/binomial: stop when ||x^{k+1} - x^k||_2 < tol (<= 0: 1e-8) */
   double fd_eps;          /* central-difference step (<= 0: 1e-3)                  */
   int32_t use_graph;      /* nonzero (batch in one wave): the whole evaluation is   */
                           /* captured once per batch size and options as a CUDA    */
@@ -156,7 +157,7 @@ typedef struct {
   double *x_mode_dev;     /* [B][n] latent mode x*(theta_b)                        */
   double *marg_var_dev;   /* [B][n] diag(Q_c(theta_b)^-1), latent order            */
   int32_t *status_dev;    /* [B]    per-point inla_status (required)               */
-  int32_t *newton_iters_dev; /* [B] Newton iterations (Poisson), 0 for Gaussian     */
+  int32_t *newton_iters_dev; /* [B] Newton iterations (Poisson/binomial), 0 for Gaussian */
 } inla_eval_out;
 
 /* Host-buffer twin of inla_eval_out (all HOST pointers, same layout). */
@@ -186,9 +187,10 @@ int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *o
 
 /* Evaluate B >= 1 points (B = 0 is an argument error).  theta_dev: DEVICE [B][4].  out: DEVICE buffers as
  * above.  stream: a cudaStream_t (NULL = legacy default stream).  Work is
- * enqueued on `stream`; the call returns after enqueueing, except for the
- * Poisson likelihood, whose Newton loop reads a convergence flag back to
- * the host once per iteration.  The workspace grows on first use (device
+ * enqueued on `stream`; the call returns after enqueueing, except for
+ * Poisson and binomial data without use_graph, whose Newton loop reads a
+ * convergence flag back to the host once per iteration (with use_graph the
+ * loop runs on the device).  The workspace grows on first use (device
  * allocation), so the first call with a larger B may allocate.
  * With opts->grad == INLA_GRAD_FD_CENTRAL each point is the centre of a
  * 2d+1 = 9 point stencil (Eq. central_diff); f, x_mode and marg_var are
