@@ -172,7 +172,9 @@ typedef struct {
 
 typedef struct inla_model inla_model;
 
-/* Build a model on CUDA device `device`: validates the description, sorts
+/* Build a model on CUDA device `device` (the latent Gaussian model of Sec. 2.1:
+ * the spatial SPDE and temporal AR(1) precisions, the fixed effects and the
+ * observation matrix A of the linear predictor): validates the description, sorts
  * the observations by time, builds the index structures on the host and
  * computes every theta-free value (G C^-1 G, A^T A, A^T y, ...) with device
  * kernels.  On success *out owns all device memory of the model.
@@ -181,8 +183,11 @@ typedef struct inla_model inla_model;
 int inla_model_create(const inla_model_desc *desc, int device, inla_model **out);
 
 /* Bytes of device workspace that inla_eval_batch allocates (and keeps in
- * the model for reuse) for a batch of B points with these options.  FD mode
- * evaluates B * 9 points.  Errors: INLA_ERR_ARG. */
+ * the model for reuse) for a batch of B points with these options: per point
+ * the block factorisation of Sec. 2.4 (n_t inverted n_s x n_s Schur blocks)
+ * and two live blocks of the selected inversion (Sec. 2.4.2).  Central
+ * differences (Eq. central_diff) evaluate B * 9 points.  model and opts are
+ * HOST pointers, *bytes is written on success.  Errors: INLA_ERR_ARG. */
 int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *opts, size_t *bytes);
 
 /* Evaluate B >= 1 points (B = 0 is an argument error).  theta_dev: DEVICE [B][4].  out: DEVICE buffers as
@@ -205,19 +210,27 @@ int inla_eval_batch(inla_model *model, int B, const double *theta_dev, const inl
  * after start-up, or a plugin inside a host framework whose own caching
  * allocator owns the device memory, so that a raw cudaMalloc could fail or
  * fragment that pool.  Its workspace is one array of INLA_STATIC_SCRATCH_BYTES
- * (64 MiB) that the library reserves in device memory on every GPU that
- * loads it, until the process exits; the model itself (inla_model_create)
- * still allocates, so create models at start-up.
- * Arguments, outputs and results are those of inla_eval_batch.  The whole
- * batch must fit in the array in one pass: inla_workspace_bytes() plus
- * about 96 bytes per point (B points, or 9 B with central differences) up
- * to 64 MiB; a larger batch returns INLA_ERR_ARG and does nothing.
- * The first call on a device looks up the array's device address with that
- * device current (no allocation); make that first call before any stream
- * capture.  All calls on a device share the array, which keeps the last
- * call's contents (every call clears what it needs); calls on one model are
- * ordered like inla_eval_batch, but calls from two models that overlap on
- * the GPU race on the array.  Errors as for inla_eval_batch. */
+ * (64 MiB), a file-scope __device__ array of the library.  The array is
+ * committed on a device, and its device address looked up with that device
+ * current, by the first inla_model_create on that device; from then on every
+ * GPU that has a model holds it until the process exits.  The model itself
+ * (inla_model_create) allocates, so create models at start-up.  Kernel code
+ * is loaded on first use under the CUDA runtime's default lazy module
+ * loading, which the driver backs with a little device memory; callers that
+ * need the very first call to touch no new device memory either set
+ * CUDA_MODULE_LOADING=EAGER or make one warm-up call at start-up.
+ * Arguments, outputs and results are those of inla_eval_batch, with two
+ * differences: opts->use_graph is ignored (the call always launches its
+ * kernels directly), and for Poisson and binomial data the call reads a
+ * convergence flag back to the host once per Newton iteration, as
+ * inla_eval_batch does without use_graph.  The whole batch must fit in the
+ * array in one pass: inla_workspace_bytes() plus about 96 bytes per point
+ * (B points, or 9 B with central differences) up to 64 MiB; a larger batch
+ * returns INLA_ERR_ARG and does nothing.  All calls on a device share the
+ * array, which keeps the last call's contents (every call clears what it
+ * needs); calls on one model are ordered like inla_eval_batch, but calls from
+ * two models that overlap on the GPU race on the array.  Errors as for
+ * inla_eval_batch. */
 #define INLA_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 int inla_eval_batch_static(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts,
                            const inla_eval_out *out, void *stream);
@@ -245,6 +258,18 @@ int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_
  * blocks; FP32 GEMM 64, 128 or INLA_GEMM_TF32X3.  A new model starts at
  * (32, 64, INLA_GEMM_TF32X3).  Errors: INLA_ERR_ARG for other values. */
 int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_fp32);
+
+/* Bound on each wait of the tensor-core kernels for their own asynchronous
+ * copies and matrix products (no counterpart in the paper; the library's
+ * failure detection).  Process-wide; seconds in (0, 2], default 2; below
+ * 1e-6 every wait is a single non-blocking test of completion.  A wait
+ * that runs out marks its evaluation point INLA_ERR_TIMEOUT (f = +inf, NaN in
+ * the point's other outputs) -- or, in inla_gemm_tf32x3, its batch entry --
+ * and the kernel then waits, with the full 2 s bound, for the work it has in
+ * flight before it releases its shared and tensor memory and returns.  Takes
+ * effect for kernels launched after the call; a CUDA graph keeps the limit it
+ * was captured with.  Errors: INLA_ERR_ARG. */
+int inla_set_wait_limit(double seconds);
 
 /* Latent dimension n = n_t n_s + n_b of a model. */
 int64_t inla_model_latent_dim(const inla_model *model);
@@ -306,25 +331,15 @@ int inla_synth_grid_model(int32_t cfg_id, uint64_t seed, inla_model_desc *desc, 
 /* Release the arrays of a synthetic workload.  NULL is allowed. */
 void inla_synth_free(void *owner);
 
-/* Free every device resource of the model.  NULL is allowed. */
+/* Free every device resource of the model built by inla_model_create (the
+ * device copy of the Sec. 2.1 model, the workspace, captured graphs).
+ * Synchronises the model's work first.  NULL is allowed. */
 void inla_model_destroy(inla_model *model);
 
-/* Message of the last non-OK return on this thread ("" if none). */
+/* Message of the last non-OK return on this thread ("" if none); the string
+ * is owned by the library and valid until the thread's next call.  No
+ * counterpart in the paper (error reporting of the C ABI). */
 const char *inla_last_error(void);
-
-/* Measurement utility (no counterpart in the paper): sustained FP64 FMA
- * throughput of this GPU in TFLOP/s, timed with CUDA events on a
- * register-resident loop over every SM, so that roofline fractions can be
- * quoted against a measured FP64 peak.  use_tensor = 1 times the
- * warp-level double-precision MMA instruction instead of scalar FMA;
- * use_tensor = 2 runs both at once (half the warps each), which shows whether
- * the two FP64 paths share one pipe. */
-int inla_measure_fp64_peak(int device, int use_tensor, double *tflops);
-
-/* Measurement utility (no counterpart in the paper): FP32 scalar FMA
- * throughput of this GPU in TFLOP/s (the denominator of the mixed-precision
- * rooflines), measured like inla_measure_fp64_peak. */
-int inla_measure_fp32_peak(int device, double *tflops);
 
 #ifdef __cplusplus
 }

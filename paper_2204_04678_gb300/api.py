@@ -164,24 +164,26 @@ class Model:
         return out
 
     def eval_static(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False,
-                    max_newton=50, newton_tol=1e-8, fd_eps=1e-3, stream=None):
+                    max_newton=50, newton_tol=1e-8, fd_eps=1e-3, stream=None, out=None, precision="fp64"):
         """Same as eval() through inla_eval_batch_static: the library's fixed
         device array serves as the workspace, so the call allocates no device
-        memory (the output tensors are allocated here, by torch)."""
+        memory.  Pass ``out`` (the dict eval() returns) to reuse output tensors;
+        otherwise they are allocated here, by torch."""
         import torch
         theta = theta.contiguous()
         B = theta.shape[0]
         dev = theta.device
-        out = dict(f=torch.empty(B, dtype=torch.float64, device=dev),
-                   status=torch.empty(B, dtype=torch.int32, device=dev),
-                   newton_iters=torch.empty(B, dtype=torch.int32, device=dev))
-        if grad != "none":
-            out["grad"] = torch.empty(B, 4, dtype=torch.float64, device=dev)
-        if want_mode:
-            out["x_mode"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
-        if want_marg_var:
-            out["marg_var"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
-        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps)
+        if out is None:
+            out = dict(f=torch.empty(B, dtype=torch.float64, device=dev),
+                       status=torch.empty(B, dtype=torch.int32, device=dev),
+                       newton_iters=torch.empty(B, dtype=torch.int32, device=dev))
+            if grad != "none":
+                out["grad"] = torch.empty(B, 4, dtype=torch.float64, device=dev)
+            if want_mode:
+                out["x_mode"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
+            if want_marg_var:
+                out["marg_var"] = torch.empty(B, self.n, dtype=torch.float64, device=dev)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision)
         so = C.inla_eval_out()
         so.f_dev = out["f"].data_ptr()
         so.status_dev = out["status"].data_ptr()
@@ -219,19 +221,25 @@ class Model:
         return res
 
 
+def _probe_check(code):
+    if code != C.INLA_OK:
+        raise C.InlaError(code, C.load_probe().inla_probe_last_error().decode())
+
+
 def measure_fp64_peak(device=0, tensor=False):
-    """Measured FP64 throughput (TFLOP/s) of scalar FMA or the DMMA instruction."""
-    lib = C.load()
+    """Measured FP64 throughput (TFLOP/s) of scalar FMA or the DMMA instruction
+    (libinla_probe.so, a benchmark utility)."""
+    lib = C.load_probe()
     v = c_double()
-    C.check(lib.inla_measure_fp64_peak(int(device), int(bool(tensor)), byref(v)))
+    _probe_check(lib.inla_measure_fp64_peak(int(device), int(bool(tensor)), byref(v)))
     return v.value
 
 
 def measure_fp32_peak(device=0):
-    """Measured FP32 scalar FMA throughput (TFLOP/s)."""
-    lib = C.load()
+    """Measured FP32 scalar FMA throughput (TFLOP/s) (libinla_probe.so)."""
+    lib = C.load_probe()
     v = c_double()
-    C.check(lib.inla_measure_fp32_peak(int(device), byref(v)))
+    _probe_check(lib.inla_measure_fp32_peak(int(device), byref(v)))
     return v.value
 
 

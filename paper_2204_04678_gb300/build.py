@@ -1,8 +1,10 @@
-"""Build the in-tree shared library ``libinla_gpu.so`` for sm_103a with nvcc.
+"""Build the in-tree shared libraries for sm_103a with nvcc.
 
-Each translation unit under ``csrc/`` is compiled in parallel into
-``_build/`` and linked into ``paper_2204_04678_gb300/libinla_gpu.so``
-(both git-ignored).  Objects are rebuilt when a source or a header is newer.
+``libinla_gpu.so`` is the evaluation library (include/inla_gpu.h);
+``libinla_probe.so`` holds the benchmark's throughput probes
+(include/inla_probe.h).  Each translation unit under ``csrc/`` is compiled in
+parallel into ``_build/`` and linked in-tree (both git-ignored).  Objects are
+rebuilt when a source or a header is newer.
 """
 import os
 import subprocess
@@ -13,9 +15,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libinla_gpu.so")
+PROBE_LIB = os.path.join(PKG, "libinla_probe.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "probe.cu", "tc_gemm.cu",
-           "synth.cpp"]
+SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "tc_gemm.cu", "synth.cpp"]
+PROBE_SOURCES = ["probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE]
 
@@ -37,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     hdr = _headers_mtime()
     jobs = []
-    for src in SOURCES:
+    for src in SOURCES + PROBE_SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
@@ -51,13 +54,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed for {cmd[-3]}:\n{r.stdout}\n{r.stderr}")
         return r
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + len(PROBE_SOURCES)) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OBJDIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
-    if jobs or force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
+    for lib, srcs in ((LIB, SOURCES), (PROBE_LIB, PROBE_SOURCES)):
+        objs = [os.path.join(OBJDIR, os.path.splitext(s)[0] + ".o") for s in srcs]
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+            tmp = lib + ".tmp"
+            run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+            os.replace(tmp, lib)
     return LIB
 
 

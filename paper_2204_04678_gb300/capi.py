@@ -7,7 +7,7 @@ import ctypes
 import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
 
-from .build import LIB
+from .build import LIB, PROBE_LIB
 
 INLA_OK = 0
 INLA_ERR_ARG = 1
@@ -79,12 +79,11 @@ SIGNATURES = {
                                      POINTER(inla_eval_out_host)]),
     "inla_autotune": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts), POINTER(c_int32)]),
     "inla_set_tiles": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "inla_set_wait_limit": (c_int, [c_double]),
     "inla_model_latent_dim": (c_int64, [c_void_p]),
     "inla_last_launch_count": (c_int64, [c_void_p]),
     "inla_model_destroy": (None, [c_void_p]),
     "inla_last_error": (c_char_p, []),
-    "inla_measure_fp64_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
-    "inla_measure_fp32_peak": (c_int, [c_int, POINTER(c_double)]),
     "inla_gemm_tf32x3": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "inla_synth_build": (c_int, [c_int32, c_int32, c_int32, c_int64, c_int32, c_uint64, c_void_p,
                                  POINTER(inla_model_desc), POINTER(c_void_p)]),
@@ -94,7 +93,31 @@ SIGNATURES = {
     "inla_profile_read": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_int64), POINTER(c_double)]),
 }
 
+# include/inla_probe.h (libinla_probe.so, the benchmark's throughput probes)
+PROBE_SIGNATURES = {
+    "inla_measure_fp64_peak": (c_int, [c_int, c_int, POINTER(c_double)]),
+    "inla_measure_fp32_peak": (c_int, [c_int, POINTER(c_double)]),
+    "inla_probe_last_error": (c_char_p, []),
+}
+
 _lib = None
+_probe = None
+
+
+def load_probe(path: str = PROBE_LIB):
+    """Load the probe library (measurement utilities, not the evaluation path)."""
+    global _probe
+    if _probe is not None:
+        return _probe
+    if not os.path.exists(path):
+        raise RuntimeError(f"libinla_probe.so not found at {path}: build it first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in PROBE_SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _probe = lib
+    return lib
 
 
 def load(path: str = LIB):

@@ -69,6 +69,17 @@ __global__ void flags_kernel(Work W, int64_t w0, int per, int centre_flags) {
   W.flags[b] = (per == 1 || g % per == 0) ? centre_flags : 0;
 }
 
+// A point whose status is not OK gets NaN marginal variances (its selected
+// inverse may be incomplete, e.g. after a timed-out tensor-core product).
+__global__ void mask_failed_kernel(Work W, int64_t n, double *mv, const int *point_out, int64_t point_base) {
+  const int b = blockIdx.y;
+  if (W.status[b] == INLA_OK) return;
+  const int o = point_out[point_base + b];
+  if (o < 0) return;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    mv[(int64_t)o * n + k] = NAN;
+}
+
 __global__ void zero_slot_kernel(Work W, int slot) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < W.P) W.sc[b * SC_COUNT + slot] = 0.0;
@@ -123,6 +134,7 @@ struct inla_model {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(device);
+    if (done && done_valid) cudaEventSynchronize(done);   // the last evaluation has finished
     for (void *p : allocs) cudaFree(p);
     if (ws) cudaFree(ws);
     if (bb) cudaFree(bb);
@@ -138,6 +150,8 @@ struct inla_model {
 };
 
 namespace {
+
+void *static_scratch(int device);   // the no-allocation entry point's array (defined below)
 
 // ------------------------------------------------------------------ model construction
 
@@ -420,6 +434,11 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     }
     CUDA_OK(cudaGetLastError());
     CUDA_OK(cudaStreamSynchronize(mdl->stream));
+    // Commit the no-allocation entry point's static array on this device now: with lazy
+    // module loading its device memory is only backed when the address is first taken,
+    // which must not happen inside inla_eval_batch_static.
+    static_scratch(device);
+    dense_prepare();
     return mdl;
   } catch (...) {
     delete mdl;
@@ -845,6 +864,10 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
   }
   if (x_out) k_copy_mode(L, M, W, x_out, bb.point_out, w0);
   k_finalize(L, M, W, o.grad, o.prior_mode, w0, bb.f_all, bb.grad_all, bb.status_all, bb.iters_all);
+  if (mv_out && need_sel) {
+    mask_failed_kernel<<<dim3(64, W.P), 256, 0, L.st>>>(W, M.n, mv_out, bb.point_out, w0);
+    L.tick();
+  }
 }
 
 void run_wave(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts &o, int64_t w0,
@@ -1018,10 +1041,13 @@ int guarded(F &&f) {
 // ------------------------------------------------------------------ no-allocation variant
 //
 // inla_eval_batch_static runs the same evaluation with its workspace in this
-// fixed array instead of memory from cudaMalloc.  Every GPU that loads the
-// library holds the array until the process exits.  Host code must not use
-// the symbol as an address: the device address comes from
-// cudaGetSymbolAddress, looked up once per device with that device current.
+// fixed array instead of memory from cudaMalloc.  Host code must not use the
+// symbol as an address: the device address comes from cudaGetSymbolAddress,
+// looked up once per device with that device current -- by inla_model_create,
+// which thereby also makes the runtime back the array on that device (under
+// lazy module loading that happens at the first use of the symbol), so that
+// the entry point itself never triggers it.  Every GPU with a model holds the
+// array until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[INLA_STATIC_SCRATCH_BYTES];
 
 namespace {
@@ -1300,6 +1326,14 @@ int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *
     *total_ms = ms;
     *launches = n;
     *units = u;
+  });
+}
+
+int inla_set_wait_limit(double seconds) {
+  return guarded([&] {
+    if (!(seconds > 0.0) || !(seconds <= 2.0))
+      throw ApiError(INLA_ERR_ARG, "the wait limit must be in (0, 2] seconds");
+    set_wait_limit_ns((uint64_t)(seconds * 1e9));
   });
 }
 

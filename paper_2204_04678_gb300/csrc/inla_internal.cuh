@@ -228,6 +228,9 @@ void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active);
 
 // tc_gemm.cu: C = alpha X Y^T + beta C0 in 3xTF32 on the tensor cores (n % 128 == 0)
 void tc_prepare();
+// bound (ns of %globaltimer) on one mbarrier wait of the tensor-core kernels
+uint64_t wait_limit_ns();
+void set_wait_limit_ns(uint64_t ns);
 void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const float *Y, int64_t sY, float *C,
                     int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, bool lower_only,
                     const int *active, int *status);

@@ -1,4 +1,6 @@
-// Throughput probes (measurement utilities; no counterpart in the paper).
+// Throughput probes (measurement utilities for the benchmark's roofline
+// denominators; no counterpart in the paper).  Built as libinla_probe.so,
+// separate from the product library; declared in include/inla_probe.h.
 // Every SM runs register-resident chains of independent fused multiply-adds
 // (FP64 scalar FMA, the warp-level m8n8k4 double-precision MMA instruction,
 // or FP32 scalar FMA) for a fixed number of iterations; the rate is
@@ -6,9 +8,14 @@
 // one store per thread at the end (so the compiler cannot drop them).
 #include <cuda_runtime.h>
 
-#include "inla_internal.cuh"
+#include <string>
+
+#include "../../include/inla_probe.h"
 
 namespace {
+
+thread_local std::string g_probe_err;
+void set_error(const char *msg) { g_probe_err = msg; }
 
 constexpr int CHAINS = 8;
 
@@ -98,13 +105,15 @@ __global__ void __launch_bounds__(256) ffma_probe(int iters, float *sink) {
 
 }  // namespace
 
+extern "C" const char *inla_probe_last_error(void) { return g_probe_err.c_str(); }
+
 extern "C" int inla_measure_fp32_peak(int device, double *tflops) {
   if (!tflops) {
-    inla::set_error("tflops is NULL");
+    set_error("tflops is NULL");
     return INLA_ERR_ARG;
   }
   if (cudaSetDevice(device) != cudaSuccess) {
-    inla::set_error("cudaSetDevice failed");
+    set_error("cudaSetDevice failed");
     return INLA_ERR_CUDA;
   }
   cudaDeviceProp prop;
@@ -112,7 +121,7 @@ extern "C" int inla_measure_fp32_peak(int device, double *tflops) {
   const int blocks = prop.multiProcessorCount * 8, threads = 256, iters = 1 << 16;
   float *sink = nullptr;
   if (cudaMalloc(&sink, sizeof(float) * blocks * threads) != cudaSuccess) {
-    inla::set_error("cudaMalloc failed");
+    set_error("cudaMalloc failed");
     return INLA_ERR_OOM;
   }
   cudaEvent_t e0, e1;
@@ -133,7 +142,7 @@ extern "C" int inla_measure_fp32_peak(int device, double *tflops) {
   cudaEventDestroy(e1);
   cudaFree(sink);
   if (err != cudaSuccess) {
-    inla::set_error(cudaGetErrorString(err));
+    set_error(cudaGetErrorString(err));
     return INLA_ERR_CUDA;
   }
   *tflops = (double)blocks * threads * CHAINS * 2 * iters / (best * 1e-3) / 1e12;
@@ -142,11 +151,11 @@ extern "C" int inla_measure_fp32_peak(int device, double *tflops) {
 
 extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops) {
   if (!tflops) {
-    inla::set_error("tflops is NULL");
+    set_error("tflops is NULL");
     return INLA_ERR_ARG;
   }
   if (cudaSetDevice(device) != cudaSuccess) {
-    inla::set_error("cudaSetDevice failed");
+    set_error("cudaSetDevice failed");
     return INLA_ERR_CUDA;
   }
   cudaDeviceProp prop;
@@ -155,7 +164,7 @@ extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops
   const int iters = use_tensor ? (1 << 14) : (1 << 16);
   double *sink = nullptr;
   if (cudaMalloc(&sink, sizeof(double) * blocks * threads) != cudaSuccess) {
-    inla::set_error("cudaMalloc failed");
+    set_error("cudaMalloc failed");
     return INLA_ERR_OOM;
   }
   cudaEvent_t e0, e1;
@@ -178,7 +187,7 @@ extern "C" int inla_measure_fp64_peak(int device, int use_tensor, double *tflops
   cudaEventDestroy(e1);
   cudaFree(sink);
   if (err != cudaSuccess) {
-    inla::set_error(cudaGetErrorString(err));
+    set_error(cudaGetErrorString(err));
     return INLA_ERR_CUDA;
   }
   // scalar: 2 flops per FMA per thread; MMA m8n8k4: 8*8*4 FMAs per warp instruction

@@ -34,12 +34,15 @@
 //     K = 1024 when one accumulator took the whole sum), so the large hi*hi
 //     partial takes only the 4 MMAs of one 32-deep stage, the small cross
 //     terms never round it, and the sum over stages runs in FP32 arithmetic.
-// Every mbarrier wait is bounded (2 s of %globaltimer); a wait that runs out
-// marks the point INLA_ERR_TIMEOUT, skips the epilogue, releases the tensor
-// memory and returns.
+// Every mbarrier wait is bounded (2 s of %globaltimer by default; the limit is
+// a kernel argument, set process-wide by inla_set_wait_limit); a wait that runs
+// out marks the point INLA_ERR_TIMEOUT, skips the epilogue, waits with the full
+// 2 s bound for its own copies and MMAs in flight, releases the tensor memory
+// and returns.
 #include <cuda.h>   // CUtensorMap and the tensor-map encoder's types (the encoder is looked up at run time)
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <stdexcept>
@@ -57,7 +60,7 @@ constexpr int SLAB_BYTES = TCM * TCK * 4;             // 16 KB per operand slab
 constexpr int STAGE_BYTES = 4 * SLAB_BYTES;           // X_hi, X_lo, Y_hi, Y_lo
 constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024;       // two stages + alignment slack
 constexpr uint32_t TMEM_COLS = 512;                   // 2 stages x {hi*hi, cross terms} x 128 columns
-constexpr uint64_t WAIT_NS = 2000000000ull;           // bound on one mbarrier wait
+constexpr uint64_t WAIT_NS = 2000000000ull;           // bound on the waits for work in flight before an exit
 
 // Instruction descriptor of kind::tf32: D in F32 (bits 4-5 = 1), A and B in
 // TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N / 8 in
@@ -91,8 +94,20 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait until the mbarrier phase of the given parity has completed; false if
-// the bound ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// the bound (limit_ns of %globaltimer, at most 2^26 polls) ran out.  A limit
+// below 1 us makes the wait a single non-blocking test.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns < 1000) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+  }
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < (1u << 26); ++it) {
     uint32_t done;
@@ -104,7 +119,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > WAIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -151,7 +166,8 @@ __device__ __forceinline__ void split_store(uint8_t *hi, uint8_t *lo, uint32_t o
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tf32x3_kernel(int n, int K, int ldx, const float *__restrict__ X, int64_t sX, const float *__restrict__ Y,
                        int64_t sY, float *C, int64_t sC, float alpha, const float *C0, int64_t sC0, float beta,
-                       int lower_only, int sweep_pivot, int sweep_next, const int *active, int *status) {
+                       int lower_only, int sweep_pivot, int sweep_next, const int *active, int *status,
+                       uint64_t wait_ns) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   int ti, tj;
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int s = c & 1;
     if (c >= 2) {
       // stage s and accumulator s are free once the MMAs of chunk c - 2 completed
-      const bool ok = mbar_wait(smem_addr(&mbar[s]), (uint32_t)((c - 2) >> 1) & 1u);
+      const bool ok = mbar_wait(smem_addr(&mbar[s]), (uint32_t)((c - 2) >> 1) & 1u, wait_ns);
       if (__syncthreads_or(!ok)) {
         aborted = true;
         break;
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (!aborted) {
     // the last two stages' partial products
     for (int c = nch >= 2 ? nch - 2 : 0; c < nch; ++c) {
-      const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u);
+      const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u, wait_ns);
       if (__syncthreads_or(!ok)) {
         aborted = true;
         break;
@@ -278,8 +294,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   }
   if (aborted && last >= 0) {
-    // wait (bounded) for the MMAs in flight before the tensor memory is released
-    mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u);
+    // wait (with the full bound, whatever the caller's limit) for the MMAs in flight
+    // before the tensor memory is released
+    mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u, WAIT_NS);
   }
   // sweep update: this thread's 64 columns lie in one 64 x 64 sub-tile (si, sj)
   const int si = (i0 + 32 * quarter) >> 6, sj = (j0 >> 6) + half;
@@ -344,7 +361,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tf32x3_tma_kernel(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
                            const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl, int n,
                            float *C, int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, float *Chi,
-                           float *Clo, int lower_only, const int *active, int *status) {
+                           float *Clo, int lower_only, const int *active, int *status, uint64_t wait_ns) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   int ti, tj;
@@ -428,7 +445,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int a = c & 1, s = c % TMA_STAGES;
     if (c >= 2) {
       // accumulator pair a and the stage of chunk c - 2 are free once its MMAs completed
-      const bool ok = mbar_wait(smem_addr(&mbar[a]), (uint32_t)((c - 2) >> 1) & 1u);
+      const bool ok = mbar_wait(smem_addr(&mbar[a]), (uint32_t)((c - 2) >> 1) & 1u, wait_ns);
       if (__syncthreads_or(!ok)) {
         aborted = true;
         break;
@@ -437,12 +454,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (c + 1 < nch) issued = c + 2;
       drain(a);
     }
-    const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)(c / TMA_STAGES) & 1u);
-    consumed = c + 1;
+    const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)(c / TMA_STAGES) & 1u, wait_ns);
     if (__syncthreads_or(!ok)) {
       aborted = true;
       break;
     }
+    consumed = c + 1;   // only once the copies of chunk c have landed
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t xh = smem_addr(base + s * STAGE_BYTES), xl = xh + SLAB_BYTES, yh = xh + 2 * SLAB_BYTES,
@@ -463,7 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (!aborted) {
     for (int c = nch >= 2 ? nch - 2 : 0; c < nch; ++c) {
-      const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u);
+      const bool ok = mbar_wait(smem_addr(&mbar[c & 1]), (uint32_t)(c >> 1) & 1u, wait_ns);
       if (__syncthreads_or(!ok)) {
         aborted = true;
         break;
@@ -472,10 +489,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   }
   if (aborted) {
-    // wait (bounded) for the copies and the MMAs in flight before the memory is released
+    // wait (with the full bound, whatever the caller's limit) for the copies and the
+    // MMAs in flight before the shared and tensor memory are released
     for (int c = consumed; c < issued; ++c)
-      mbar_wait(smem_addr(&full[c % TMA_STAGES]), (uint32_t)(c / TMA_STAGES) & 1u);
-    if (last >= 0) mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u);
+      mbar_wait(smem_addr(&full[c % TMA_STAGES]), (uint32_t)(c / TMA_STAGES) & 1u, WAIT_NS);
+    if (last >= 0) mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)(last >> 1) & 1u, WAIT_NS);
   }
   if (!aborted) {
     const int row = i0 + 32 * quarter + lane;
@@ -565,6 +583,12 @@ CUtensorMap slab_map(const float *base, int n, int P, int64_t point_stride) {
 
 }  // namespace
 
+// Bound on one mbarrier wait of the tensor-core kernels (inla_set_wait_limit),
+// read at each launch and passed to the kernel.
+static std::atomic<uint64_t> g_wait_ns{WAIT_NS};
+uint64_t wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+void set_wait_limit_ns(uint64_t ns) { g_wait_ns.store(ns, std::memory_order_relaxed); }
+
 // Kernel attributes belong to the device's context: set once per device.
 void tc_prepare() {
   static std::mutex mu;
@@ -597,7 +621,8 @@ void gemm_nt_tf32x3_split(Launch &L, int P, int n, const float *Xh, const float 
   const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
   L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
   gemm_tf32x3_tma_kernel<<<dim3(tiles, P), TC_THREADS, TMA_SMEM, L.st>>>(
-      mXh, mXl, mYh, mYl, n, C, sC, alpha, C0, sC0, beta, Chi, Clo, lower_only ? 1 : 0, active, status);
+      mXh, mXl, mYh, mYl, n, C, sC, alpha, C0, sC0, beta, Chi, Clo, lower_only ? 1 : 0, active, status,
+      wait_limit_ns());
   L.stop();
   L.tick();
 }
@@ -611,7 +636,7 @@ void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const f
   L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
   gemm_tf32x3_kernel<<<dim3(tiles, P), TC_THREADS, TC_SMEM, L.st>>>(n, n, n, X, sX, Y, sY, C, sC, alpha, C0, sC0,
                                                                      beta, lower_only ? 1 : 0, -1, -1, active,
-                                                                     status);
+                                                                     status, wait_limit_ns());
   L.stop();
   L.tick();
 }
@@ -625,7 +650,8 @@ void sweep_update_tf32x3(Launch &L, int P, int n_p, float *A, int64_t sA, const 
   const double units = (double)P * (nt * (nt + 1) / 2 - nt - (next >= 0 ? 1 : 0));
   L.start(KID_GJ_UPDATE32, units);
   gemm_tf32x3_kernel<<<dim3(tiles, P), TC_THREADS, TC_SMEM, L.st>>>(n_p, 64, 64, Cbuf, sCO, Obuf, sCO, A, sA, -1.0f,
-                                                                     A, sA, 1.0f, 1, pivot, next, active, status);
+                                                                     A, sA, 1.0f, 1, pivot, next, active, status,
+                                                                     wait_limit_ns());
   L.stop();
   L.tick();
 }

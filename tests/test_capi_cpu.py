@@ -21,8 +21,8 @@ def lib():
     return C.load()
 
 
-def header_functions():
-    src = open(os.path.join(ROOT, "include", "inla_gpu.h")).read()
+def header_functions(header="inla_gpu.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(inla_[a-z0-9_]+)\s*\(", src)))
 
@@ -34,6 +34,17 @@ def test_every_declared_function_is_exported_and_bound(lib):
         assert hasattr(lib, n), n
         assert n in C.SIGNATURES, n
     assert set(C.SIGNATURES) == set(names)
+
+
+def test_probe_library_is_separate_and_complete(lib):
+    # the benchmark's throughput probes live in their own library, not in the product
+    probe = C.load_probe()
+    names = header_functions("inla_probe.h")
+    assert "inla_measure_fp64_peak" in names
+    for n in names:
+        assert hasattr(probe, n), n
+        assert not hasattr(lib, n), n
+    assert set(C.PROBE_SIGNATURES) == set(names)
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
@@ -125,5 +136,6 @@ def test_null_arguments(lib):
     assert lib.inla_workspace_bytes(None, 1, ctypes.byref(o), ctypes.byref(out)) == C.INLA_ERR_ARG
     assert lib.inla_eval_batch(None, 1, None, None, None, None) == C.INLA_ERR_ARG
     v = ctypes.c_double()
-    assert lib.inla_measure_fp64_peak(0, 0, None) == C.INLA_ERR_ARG
+    assert C.load_probe().inla_measure_fp64_peak(0, 0, None) == C.INLA_ERR_ARG
+    assert lib.inla_set_wait_limit(0.0) == C.INLA_ERR_ARG
     lib.inla_model_destroy(None)

@@ -51,6 +51,49 @@ def test_static_scratch_matches_allocating_entry_point(pkg, lik):
             assert close(got["marg_var"], ref["marg_var"], RTOL_V)
 
 
+@pytest.mark.parametrize("case", ["mixed", "bta_prior"])
+def test_static_scratch_other_layouts(pkg, case):
+    # mixed precision on a block size that is a multiple of 128 carves the FP32
+    # blocks and the TF32 hi / lo operand arrays of the tensor-core products out
+    # of the static array; the BTA prior mode runs a second factorisation on it
+    mdl = build("s", 3, 16 if case == "mixed" else 6, 2, 600, "gaussian", seed=4)
+    th = torch.tensor(mdl.theta_true[None, :] + 0.05 * np.arange(3)[:, None], dtype=torch.float64, device="cuda")
+    model = pkg.Model(mdl)
+    kw = dict(grad="adjoint", want_mode=True, want_marg_var=True)
+    kw.update(precision="mixed" if case == "mixed" else "fp64", prior="bta" if case == "bta_prior" else "kronecker")
+    ref = model.eval(th, **kw)
+    for _ in range(2):
+        got = model.eval_static(th, **kw)
+        torch.cuda.synchronize()
+        assert torch.equal(got["status"], ref["status"]) and int(ref["status"].abs().sum()) == 0
+        assert close(got["f"], ref["f"], RTOL_F)
+        assert close(got["grad"], ref["grad"], RTOL_G)
+        assert close(got["x_mode"], ref["x_mode"], RTOL_X)
+        assert close(got["marg_var"], ref["marg_var"], RTOL_V)
+
+
+def test_static_scratch_first_call_on_a_fresh_model_allocates_nothing(pkg):
+    mdl = build("s", 3, 6, 2, 400, "gaussian", seed=6)
+    th = torch.tensor(mdl.theta_true[None, :] + 0.05 * np.arange(2)[:, None], dtype=torch.float64, device="cuda")
+    kw = dict(grad="adjoint", want_mode=True, want_marg_var=True)
+    warm = pkg.Model(mdl)            # loads the kernels' code (lazy module loading) once per process
+    out = warm.eval_static(th, **kw)
+    torch.cuda.synchronize()
+    warm.close()
+    model = pkg.Model(mdl)           # the fresh model: its first evaluation is the static entry point
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    got = model.eval_static(th, out=out, **kw)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    ref = model.eval(th, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(got["status"], ref["status"]) and int(ref["status"].abs().sum()) == 0
+    assert close(got["f"], ref["f"], RTOL_F)
+    assert close(got["marg_var"], ref["marg_var"], RTOL_V)
+
+
 def test_static_scratch_rejects_a_batch_that_does_not_fit(pkg):
     mdl = build("big", 40, 32, 2, 5000, "gaussian")      # ~340 MB of workspace per point
     model = pkg.Model(mdl)
