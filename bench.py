@@ -69,70 +69,117 @@ def parse():
     ap.add_argument("--theta-iter", action="store_true",
                     help="time theta-iterations (gradient + 16-point line search) in the FD/FP64 form and "
                          "the adjoint/mixed form on the same workload, and run BFGS to the mode with both")
-    ap.add_argument("--no-errors", action="store_true", help="skip the mixed-vs-FP64 accuracy check")
+    ap.add_argument("--no-errors", action="store_true", help="skip the accuracy checks against the oracle")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the extra legs (mode + variances, adjoint FP64 / mixed, theta-iterations)")
     ap.add_argument("--no-bfgs", action="store_true", help="with --theta-iter: skip the runs to the mode")
     ap.add_argument("--bfgs-iters", type=int, default=30, help="with --theta-iter: BFGS iteration limit")
-    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--evals", type=int, default=1, help=argparse.SUPPRESS)
-    ap.add_argument("--nt-sample", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--with-grad", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ CPU oracle timing
+#
+# The oracle (numpy/scipy FP64, test infrastructure) timed on the host cores as
+# a reported baseline: one theta per worker process with single-threaded BLAS,
+# the paper's level-1 parallelism over the stencil points (Sec. 3.1).  The
+# pool uses the spawn start method (no fork after CUDA initialisation).
 
-def oracle_sample(cfg, evals, nt_sample, with_grad):
-    """Time `evals` oracle evaluations at the first point of the workload (child process).
+_WORKER = {}
+BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
-    For the large workloads the model is built with n_t = nt_sample time steps
-    (same grid, observations and batch) and the time is scaled by n_t / nt_sample:
-    the block algorithms cost the same per time step.
-    """
+
+def _oracle_init(cfg, threads):
+    for v in BLAS_ENV:
+        os.environ[v] = str(threads)
+    os.environ["CUDA_VISIBLE_DEVICES"] = ""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from synth import config_model
+    _WORKER["mdl"] = config_model(cfg)
+
+
+def _oracle_eval(args):
+    import numpy as np
     from oracle import bta
-    from synth import CONFIGS, build, theta_batch, config_model
-    c = dict(CONFIGS[cfg])
-    scale = 1.0
-    if nt_sample and nt_sample < c["n_t"]:
-        scale = c["n_t"] / nt_sample
-        c["n_t"] = nt_sample
-    mdl = build(**c)
-    th = theta_batch(cfg, config_model(1) if cfg == 1 else mdl)
+    theta, want = args
     t0 = time.perf_counter()
-    for k in range(evals):
-        bta.evaluate(mdl, th[k % th.shape[0]], want_grad=with_grad)
-    dt = (time.perf_counter() - t0) * scale
-    print(json.dumps({"seconds_per_f": dt / evals, "evals": evals, "scale": scale}))
+    r = bta.evaluate(_WORKER["mdl"], np.asarray(theta, dtype=float), want_grad=want, want_var=want)
+    out = {"f": r["f"], "seconds": time.perf_counter() - t0}
+    if want:
+        out.update(grad=r["grad"].tolist(), x=r["x"], var=r["var"])
+    return out
 
 
-def run_oracle_child(cfg, evals, nt_sample=0, with_grad=False):
-    cores = os.cpu_count() or 1
-    env = dict(os.environ)
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = str(cores)
-    env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--config", str(cfg),
-                        "--evals", str(evals), "--nt-sample", str(nt_sample)] + (["--with-grad"] if with_grad else []),
-                       capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])["seconds_per_f"], cores
+def cpu_model_name():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
-NT_SAMPLE = {1: 0, 2: 0, 3: 4, 4: 2, 5: 2}
+class OraclePool:
+    """Worker processes holding the workload's model, one theta per task."""
+
+    def __init__(self, cfg, workers, threads=1):
+        import multiprocessing as mp
+        self.workers, self.threads = workers, threads
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_oracle_init, initargs=(cfg, threads))
+
+    def map(self, thetas, want=False):
+        return self.pool.map(_oracle_eval, [(list(map(float, t)), want) for t in thetas], chunksize=1)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
 
 
-def cpu_baseline(cfg, grad):
-    if grad == "fd":
-        sec, cores = run_oracle_child(cfg, 1 if cfg == 2 else 9, NT_SAMPLE[cfg])
-        per_grad = 9 * sec   # one f + grad f by central differences = 9 f evaluations
-        what = f"oracle f at the stencil centre, {sec:.3f} s per f; 9 f per f+grad f"
-    else:
-        per_grad, cores = run_oracle_child(cfg, 1, NT_SAMPLE[cfg], with_grad=True)
-        what = f"oracle f + adjoint gradient at one point, {per_grad:.3f} s"
-    if NT_SAMPLE[cfg]:
-        what += f" (built with n_t = {NT_SAMPLE[cfg]}, time scaled linearly to the workload's n_t)"
-    return {"value": 1.0 / per_grad, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": what + f"; {cores} host threads (numpy BLAS)"}
+def oracle_stencil_step(pool, centre):
+    """One f + grad f by central differences on the oracle: the 9 stencil points
+    in parallel (one per worker).  Returns (seconds, f values, oracle FD gradient)."""
+    import numpy as np
+    from synth import fd_stencil
+    pts = fd_stencil(np.asarray(centre))
+    t0 = time.perf_counter()
+    res = pool.map(pts)
+    sec = time.perf_counter() - t0
+    f = np.array([r["f"] for r in res])
+    g = np.array([(f[1 + 2 * j] - f[2 + 2 * j]) / (pts[1 + 2 * j][j] - pts[2 + 2 * j][j]) for j in range(4)])
+    return sec, f, g
+
+
+def one_core_f(cfg, centre):
+    """Seconds for one oracle f on one core (one worker, single-threaded BLAS)."""
+    pool = OraclePool(cfg, 1, 1)
+    try:
+        pool.map([centre])                      # warm-up: imports and model in the worker
+        return pool.map([centre])[0]["seconds"]
+    finally:
+        pool.close()
+
+
+def cpu_baseline(cfg, centre):
+    """The oracle on the host cores: the workload's 9-point stencil with one theta
+    per single-threaded worker (timed in full, one step), and one f on one core."""
+    nproc = os.cpu_count() or 1
+    workers = min(9, nproc)
+    pool = OraclePool(cfg, workers, 1)
+    try:
+        pool.map([centre] * workers)            # warm-up: imports and model in every worker
+        sec, f, g = oracle_stencil_step(pool, centre)
+    finally:
+        pool.close()
+    sec1 = one_core_f(cfg, centre)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"one full step: the 9-point central-difference stencil, one theta per worker process "
+                      f"({workers} workers, single-threaded numpy/scipy BLAS each), {sec:.2f} s",
+            "nproc": nproc, "cpu_model": cpu_model_name(),
+            "one_core": {"seconds_per_f": sec1, "value": 1.0 / (9 * sec1), "unit": UNIT,
+                         "sample": "one oracle f on one core, 9 f per f + grad f"}}, f, g
 
 
 # ------------------------------------------------------------------ clocks
@@ -188,35 +235,49 @@ class Clocks:
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
 
 def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on this arm's workload: each
+    step is the full 9-point central-difference stencil (one f + grad f), one
+    theta per single-threaded worker process.  Warm-up steps start the workers
+    and build the model in each (the oracle has no other warm-up state)."""
     if rank != 0:
         return
     cfg = args.config
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; every step below is a fresh evaluation
-    times = []
-    cores = None
-    fd = args.grad == "fd"
-    for _ in range(args.steps):
-        sec, cores = run_oracle_child(cfg, 1, NT_SAMPLE[cfg], with_grad=not fd)
-        times.append(sec)
-    t = sum(times) / len(times)
-    per = 9 * t if fd else t
-    value = 1.0 / per
+    from synth import config_model, theta_batch
+    if args.grad != "fd":
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the central-difference "
+                          "form of the workload; run it with --grad fd"}))
+        return
+    mdl = config_model(cfg)
+    centre = theta_batch(cfg, mdl)[0]
+    nproc = os.cpu_count() or 1
+    workers = min(9, nproc)
+    pool = OraclePool(cfg, workers, 1)
+    try:
+        for _ in range(args.warmup):
+            pool.map([centre] * workers)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle_stencil_step(pool, centre)
+        elapsed = time.perf_counter() - t0
+    finally:
+        pool.close()
+    value = args.steps / elapsed
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * per, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_dict(cfg, world, args.grad, args.precision, l2="CPU oracle: not applicable"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": ("each step: one oracle f evaluation at the stencil centre; "
-                                        "f + grad f = 9 such evaluations") if fd else
-                                       "each step: one oracle f + adjoint gradient at one point"
-                                       + (f" (n_t = {NT_SAMPLE[cfg]}, scaled to the workload's n_t)"
-                                          if NT_SAMPLE[cfg] else "")},
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(cfg, world, args.grad, args.precision,
+                                  l2=L2_NOTE_FLUSH if cfg in SMALL_WORKSPACE_CONFIGS else L2_NOTE_LARGE),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"every step: the full 9-point stencil, one theta per worker process "
+                                       f"({workers} workers, single-threaded BLAS each); warm-up steps start the "
+                                       f"workers and build the model in each",
+                             "nproc": nproc, "cpu_model": cpu_model_name()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 L2_BYTES = 129 * 2 ** 20
+SMALL_WORKSPACE_CONFIGS = (1,)   # workloads whose GPU workspace is below twice the L2 (timed after a flush)
 L2_NOTE_LARGE = "working set (GBs of factor storage per step) exceeds L2; no flush"
 L2_NOTE_FLUSH = "working set below 2x L2: a 512 MiB buffer is rewritten before each timed step (outside its events)"
 
@@ -351,11 +412,95 @@ def theta_iterations(args, local):
 
 # ------------------------------------------------------------------ our arm
 
+def timed_calls(model, theta, kw, steps, stream, flush=None):
+    """Device seconds of `steps` evaluations (CUDA events on the launch stream)
+    and the kernel launches they issued.  With `flush` (a buffer larger than L2)
+    each call is timed alone after the buffer has been rewritten."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches, elapsed = 0, 0.0
+    if flush is not None:
+        for _ in range(steps):
+            flush.fill_(1)
+            e0.record(stream)
+            model.eval(theta, **kw)
+            e1.record(stream)
+            launches += model.last_launch_count()
+            torch.cuda.synchronize()
+            elapsed += e0.elapsed_time(e1) / 1e3
+        return elapsed, launches
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        model.eval(theta, **kw)
+        launches += model.last_launch_count()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, launches
+
+
+def rel_errors(f, ref_f, grad=None, ref_grad=None, x=None, ref_x=None, v=None, ref_v=None):
+    """The parity metrics: |df| / |f|, max |dg| / max(1, |g|), ||dx||_inf / ||x||_inf, max |dv| / v."""
+    import numpy as np
+    e = {"f_rel": float(abs(f - ref_f) / abs(ref_f))}
+    if grad is not None:
+        e["grad_rel"] = float(np.max(np.abs(grad - ref_grad)) / max(1.0, np.max(np.abs(ref_grad))))
+    if x is not None:
+        e["x_rel"] = float(np.max(np.abs(x - ref_x)) / np.max(np.abs(ref_x)))
+    if v is not None:
+        e["var_rel"] = float(np.max(np.abs(v - ref_v) / ref_v))
+    return e
+
+
+def extra_forms(model, centre, stream, steps, dist_world):
+    """The workload's other forms, timed on the same model (each after one untimed
+    call): FD with the mode and the marginal variances (selected inversion at the
+    centre); the 9 stencil points each with an adjoint gradient in FP64 and in
+    mixed precision; and theta-iterations (gradient at the centre + one 16-point
+    line-search batch, Sec. 3.2) in the FD/FP64 and the adjoint/mixed forms."""
+    import numpy as np
+    import torch
+    from synth import fd_stencil, line_points
+    cen = torch.tensor(centre[None], dtype=torch.float64, device="cuda")
+    st9 = torch.tensor(fd_stencil(centre), dtype=torch.float64, device="cuda")
+    forms, outs = {}, {}
+    legs = {"fd_fp64_mode_var": (cen, 1, dict(grad="fd", want_mode=True, want_marg_var=True)),
+            "adjoint_fp64": (st9, 9, dict(grad="adjoint")),
+            "adjoint_mixed": (st9, 9, dict(grad="adjoint", precision="mixed"))}
+    for name, (th, per, kw) in legs.items():
+        outs[name] = model.eval(th, **kw)
+        sec, nl = timed_calls(model, th, kw, steps, stream)
+        assert int(outs[name]["status"].abs().sum()) == 0, name
+        forms[name] = {"value": per * steps / sec, "unit": UNIT, "ms_per_step": 1e3 * sec / steps,
+                       "f_grad_per_step": per, "gpu_launches_per_step": nl / steps}
+    outs["mixed_centre"] = model.eval(cen, grad="adjoint", want_mode=True, want_marg_var=True, precision="mixed")
+    g = outs["adjoint_fp64"]["grad"][0].cpu().numpy()
+    lsp = torch.tensor(line_points(centre, -g, 0.5), dtype=torch.float64, device="cuda")
+    its = {}
+    for name, (gk, prec) in {"fd_fp64": ("fd", "fp64"), "adjoint_mixed": ("adjoint", "mixed")}.items():
+        kw_g = dict(grad=gk, precision=prec)
+        kw_l = dict(grad="none", precision=prec)
+        model.eval(cen, **kw_g)
+        model.eval(lsp, **kw_l)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            model.eval(cen, **kw_g)
+            model.eval(lsp, **kw_l)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / steps
+        its[name] = {"theta_iterations_per_s": 1.0 / sec, "ms_per_iteration": 1e3 * sec}
+    forms["theta_iterations"] = dict(its, speedup_adjoint_mixed_over_fd_fp64=its["adjoint_mixed"][
+        "theta_iterations_per_s"] / its["fd_fp64"]["theta_iterations_per_s"],
+        definition="gradient at the stencil centre + one 16-point line-search batch (f only), each form in "
+                   "its own precision")
+    return forms, outs
+
+
 def main():
     args = parse()
-    if args.oracle_sample:
-        oracle_sample(args.config, args.evals, args.nt_sample, args.with_grad)
-        return
     if args.grad is None:
         args.grad = MODES[args.config][0]
     if args.precision is None:
@@ -422,46 +567,22 @@ def main():
     grad = args.grad
     prec = args.precision
     out = model.eval(theta, grad=grad, precision=prec)
-    for w in range(max(args.warmup, 1)):
-        if w == args.warmup - 1:
-            model.profile_enable(PROFILE_EVERY)   # creates the event pool outside the timed region
-        model.eval(theta, grad=grad, out=out, precision=prec)
+    kw = dict(grad=grad, out=out, precision=prec, use_graph=args.graph)
+    for _ in range(max(args.warmup, 1)):
+        model.eval(theta, **kw)
     torch.cuda.synchronize()
     assert int(out["status"].abs().sum()) == 0, "evaluation failed"
-    model.profile_enable(PROFILE_EVERY)
-
-    if args.graph:
-        model.profile_enable(0)          # event timing and graph replay exclude each other
-        model.eval(theta, grad=grad, out=out, precision=prec, use_graph=True)   # capture
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     # a working set below twice the L2 would stay cache-resident from step to step: then each
     # step is timed alone, after a buffer larger than L2 has been rewritten
     flush = model.workspace_bytes(theta.shape[0], grad=grad, precision=prec) < 2 * L2_BYTES
     scratch = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda") if flush else None
+
+    # ---- the headline: K steps, no instrumentation
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = 0
-    elapsed = 0.0
-    if flush:
-        for _ in range(args.steps):
-            scratch.fill_(1)
-            e0.record(stream)
-            model.eval(theta, grad=grad, out=out, precision=prec, use_graph=args.graph)
-            e1.record(stream)
-            launches += model.last_launch_count()
-            torch.cuda.synchronize()
-            elapsed += e0.elapsed_time(e1) / 1e3
-    else:
-        e0.record(stream)
-        for _ in range(args.steps):
-            model.eval(theta, grad=grad, out=out, precision=prec, use_graph=args.graph)
-            launches += model.last_launch_count()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        elapsed = e0.elapsed_time(e1) / 1e3
+    elapsed, launches = timed_calls(model, theta, kw, args.steps, stream, scratch)
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -470,7 +591,11 @@ def main():
         elapsed = max_over_ranks(elapsed)
     value = world * args.steps * per_step / elapsed
 
-    # dominant instrumented kernel: the sweep's tile update or the selected-inversion GEMM
+    # ---- roofline of the dominant kernel: a second pass of K steps with every
+    # PROFILE_EVERY-th launch of the instrumented kernels bracketed by events
+    model.profile_enable(PROFILE_EVERY)
+    kwp = dict(kw, use_graph=False)
+    elapsed_p, _ = timed_calls(model, theta, kwp, args.steps, stream, scratch)
     fp32 = prec == "mixed"
     tensor_gemm = fp32 and n_p % 128 == 0 and args.gemm != "cuda-core"
     upd_id = capi.KERNEL_GJ_UPDATE32 if fp32 else capi.KERNEL_GJ_UPDATE
@@ -499,7 +624,7 @@ def main():
     else:
         peak, bound = (peak_fp32 if fp32 else peak_fp64), "alu"
         peak_source = ("measured on this GPU: " + ("FP32" if fp32 else "FP64")
-                       + " FMA loop over all SMs (inla_measure_fp32/fp64_peak), of measured")
+                       + " FMA loop over all SMs (libinla_probe.so), of measured")
         desc = {"gj_update_kernel": ("FP32" if fp32 else "FP64") + " tile update of the block sweep inversion",
                 "gemm_nn_kernel": ("FP32" if fp32 else "FP64") + " tile GEMM of the selected inversion"}[kname]
     traffic = None
@@ -511,9 +636,10 @@ def main():
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": f"{kname} ({desc})", "timed_every": PROFILE_EVERY, "peak_source": peak_source,
-                "launches_timed": knl, "share_of_step": PROFILE_EVERY * kms / 1e3 / elapsed if elapsed else None}
+                "launches_timed": knl, "share_of_step": PROFILE_EVERY * kms / 1e3 / elapsed_p if elapsed_p else None,
+                "timed_in": "a second pass of the same steps with event instrumentation (the headline pass has none)"}
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
         th_host = theta.cpu().numpy().copy()
@@ -529,18 +655,44 @@ def main():
         e2e = {"value": world * per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * nb,
                "d2h_bytes_per_step": nb * (8 + 4 * 8 + 4 + 4)}
 
-    # accuracy of the mixed path against the FP64 path (which matches the oracle
-    # to 1e-10 on f): the first point of the batch, with marginal variances
-    errors = None
-    if prec == "mixed" and not args.no_errors:
-        errors = mixed_errors(model, theta[:1], grad)
+    # ---- the workload's other forms (x* and variances, adjoint FP64 / mixed, theta-iterations)
+    forms, fouts = None, None
+    base_case = cfg in (1, 2) and grad == "fd" and not (args.nt or args.centres != 1)
+    if base_case and world == 1 and not args.no_forms:
+        forms, fouts = extra_forms(model, centre, stream, 3, world)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # ---- the oracle on the host cores, and the errors against it at the stencil centre
+    cpu, errors = None, None
+    if rank == 0 and world == 1 and base_case and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(cfg, grad)
+            cpu, f_or, g_or = cpu_baseline(cfg, centre)
         except Exception as e:  # reported, not fatal
-            cpu = {"value": None, "error": str(e)[:200]}
+            cpu, f_or = {"value": None, "error": str(e)[:200]}, None
+        if f_or is not None and not args.no_errors:
+            errors = {"reference": "oracle/ (FP64 CPU), at the stencil centre; gradients: central differences "
+                                   "of oracle f for the FD form, the oracle's adjoint for the adjoint forms"}
+            errors["fd_fp64"] = rel_errors(float(out["f"][0]), f_or[0], out["grad"][0].cpu().numpy(), g_or)
+            if fouts is not None:
+                pool = OraclePool(cfg, 1, os.cpu_count() or 1)
+                try:
+                    ref = pool.map([centre], want=True)[0]
+                finally:
+                    pool.close()
+                o = fouts["fd_fp64_mode_var"]
+                errors["fd_fp64"].update(rel_errors(float(o["f"][0]), ref["f"], x=o["x_mode"][0].cpu().numpy(),
+                                                    ref_x=ref["x"], v=o["marg_var"][0].cpu().numpy(),
+                                                    ref_v=ref["var"]))
+                errors["fd_fp64"].pop("f_rel")
+                errors["fd_fp64"]["f_rel"] = rel_errors(float(o["f"][0]), ref["f"])["f_rel"]
+                a = fouts["adjoint_fp64"]
+                errors["adjoint_fp64"] = rel_errors(float(a["f"][0]), ref["f"], a["grad"][0].cpu().numpy(),
+                                                    np.array(ref["grad"]))
+                mc = fouts["mixed_centre"]
+                errors["adjoint_mixed"] = rel_errors(float(mc["f"][0]), ref["f"], mc["grad"][0].cpu().numpy(),
+                                                     np.array(ref["grad"]), mc["x_mode"][0].cpu().numpy(), ref["x"],
+                                                     mc["marg_var"][0].cpu().numpy(), ref["var"])
+    elif prec == "mixed" and not args.no_errors and world == 1:
+        errors = {"vs_fp64_path": mixed_errors(model, theta[:1], grad)}
 
     line = {}
     if rank == 0:
@@ -557,17 +709,16 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "f_evals_per_s": 9 * value if grad == "fd" else value,
                 "grad_mode": grad,
-                "errors_vs_fp64": errors,
+                "errors_vs_oracle": errors,
+                "forms": forms,
                 "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32,
                                           "tf32x3_tensor_from_bf16_sustained": tf32x3_peak},
                 "kernels": {k: {"ms_sampled": v[0], "launches_sampled": v[1],
                                 "tflops": v[2] * flop_per_unit / (v[0] / 1e3) / 1e12 if v[0] else None}
                             for k, v in kernels.items()}}
-        if not (args.nt or args.centres != 1):
-            print(json.dumps(line))
-    if args.nt or args.centres != 1:
-        line["config"]["workload"] = f"profiling case: n_t={mdl.n_t}, {args.centres} stencil centres per step"
-        print(json.dumps(line)) if rank == 0 else None
+        if args.nt or args.centres != 1:
+            line["config"]["workload"] = f"profiling case: n_t={mdl.n_t}, {args.centres} stencil centres per step"
+        print(json.dumps(line))
     model.close()
     if dist:
         dist.destroy_process_group()

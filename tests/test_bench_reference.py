@@ -25,3 +25,8 @@ def test_reference_arm_prints_one_contract_line():
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"].startswith("st-spde-ar1 n_t=8 grid=8x8")
     assert abs(line["ms_per_step"] - 1e3 / line["value"]) <= 1e-6 * line["ms_per_step"]
+    # both arms describe the workload with the same config dict
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.config_dict(1, 1, "fd", "fp64", l2=bench.L2_NOTE_FLUSH)
+    assert line["cpu_baseline"]["nproc"] >= 1 and line["cpu_baseline"]["cpu_model"]

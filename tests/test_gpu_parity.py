@@ -212,32 +212,6 @@ def test_autograd_function(pkg):
     assert torch.allclose(th.grad, w[:, None] * r["grad"], rtol=0, atol=0)
 
 
-def test_config2_full_size_sampled(pkg):
-    """The benchmark workload at full size: f, x* and sampled variances at the centre."""
-    mdl = config_model(2)
-    th = theta_batch(2, mdl)
-    model = pkg.Model(mdl)
-    r = model.eval(cuda(th[:1]), grad="fd", want_mode=True, want_marg_var=True)
-    torch.cuda.synchronize()
-    ref = bta.gaussian(mdl, th[0])
-    assert int(r["status"][0]) == 0
-    assert abs(float(r["f"][0]) - ref["f"]) <= RTOL_F * abs(ref["f"])
-    x = r["x_mode"][0].cpu().numpy()
-    assert np.abs(x - ref["x"]).max() <= RTOL_X * np.abs(ref["x"]).max()
-    # marginal variances one by one: v_i = e_i^T Q_c^-1 e_i with the oracle's factor
-    import oracle.model as M
-    A = M.obs_matrix(mdl)
-    tau_y = math.exp(th[0, 0])
-    Qc = (M.prior_Q(mdl, th[0]) + tau_y * (A.T @ A)).tocsr()
-    L, _ = bta.cholesky(bta.from_sparse(Qc, mdl.n_t, mdl.n_s, mdl.n_b)[0])
-    v = r["marg_var"][0].cpu().numpy()
-    for i in (0, 517, mdl.n_s * 25 + 300, mdl.n_t * mdl.n_s - 1, mdl.n - 1):
-        e = np.zeros(mdl.n)
-        e[i] = 1.0
-        vi = bta.solve(L, e)[i]
-        assert abs(v[i] - vi) <= RTOL_V * vi
-
-
 # ---------------------------------------------------------------- mixed precision
 # Dense blocks in FP32, pivots' log-determinants accumulated in FP64, the mode
 # refined with FP64 residuals, and every FP32 block update summed before it is
@@ -270,22 +244,6 @@ def test_mixed_precision_matches_oracle(pkg, lik, n_t, nx, n_b, m):
         assert np.abs(x - ref["x"]).max() <= MIX_X * np.abs(ref["x"]).max()
         v = r["marg_var"][b].cpu().numpy()
         assert np.max(np.abs(v - ref["var"]) / ref["var"]) <= MIX_V
-
-
-def test_mixed_precision_full_size_config2(pkg):
-    mdl = config_model(2)
-    th = theta_batch(2, mdl)[:2]
-    model = pkg.Model(mdl)
-    r = model.eval(cuda(th), grad="adjoint", want_mode=True, precision="mixed")
-    d = model.eval(cuda(th), grad="adjoint", want_mode=True)
-    torch.cuda.synchronize()
-    ref = bta.gaussian(mdl, th[0])
-    assert abs(float(r["f"][0]) - ref["f"]) <= MIX_F * abs(ref["f"])
-    assert np.all(np.abs(r["f"].cpu().numpy() - d["f"].cpu().numpy()) <= MIX_F * np.abs(d["f"].cpu().numpy()))
-    gd, gm = d["grad"].cpu().numpy(), r["grad"].cpu().numpy()
-    assert np.abs(gm - gd).max() <= MIX_G * max(1.0, np.abs(gd).max())
-    x = r["x_mode"][0].cpu().numpy()
-    assert np.abs(x - ref["x"]).max() <= MIX_X * np.abs(ref["x"]).max()
 
 
 def test_cuda_graph_replay_matches_eager(pkg):
