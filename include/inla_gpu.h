@@ -271,6 +271,14 @@ int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_f
  * was captured with.  Errors: INLA_ERR_ARG. */
 int inla_set_wait_limit(double seconds);
 
+/* Where the FP64 path's selected-inversion products run (Eq. sel_inv_cov on
+ * the n_s x n_s blocks, 3 n_s^3 flops per time step): tensor = 1 (the default)
+ * on the BF16 tensor cores through error-free digit splitting (as
+ * inla_gemm_f64), used where n_s rounded up to 64 is a multiple of 128;
+ * tensor = 0 with FP64 FMA on the CUDA cores.  Both meet the FP64 tolerances;
+ * results differ in rounding.  Drops captured graphs.  Errors: INLA_ERR_ARG. */
+int inla_set_fp64_products(inla_model *model, int tensor);
+
 /* Latent dimension n = n_t n_s + n_b of a model. */
 int64_t inla_model_latent_dim(const inla_model *model);
 
@@ -303,6 +311,28 @@ int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *
  * cudaStream_t; NULL = legacy default stream).  Errors: INLA_ERR_ARG
  * (sizes, NULL or unaligned pointers), INLA_ERR_CUDA. */
 int inla_gemm_tf32x3(int n, int batch, const float *X, const float *Y, float *C, int32_t *status, void *stream);
+
+/* C[b] = X[b] Y[b]^T for b < batch: n x n row-major FP64 matrices (DEVICE,
+ * contiguous one after another; n a positive multiple of 128) -- the product
+ * the FP64 selected inversion uses (Eq. sel_inv_cov on n_s x n_s blocks),
+ * computed on the BF16 tensor cores by error-free splitting (the Ozaki scheme):
+ * each row of X and of Y is scaled by the power of two 2^e above its largest
+ * magnitude and written as 8 integer digits of 7 bits (|digit| <= 64, exact in
+ * BF16) plus a rounding error below 2^(e-56); the 36 digit products of
+ * combined weight >= 2^-49 run on the tensor cores (tcgen05, kind::f16,
+ * FP32 accumulation that is exact for the leading four weights), and their
+ * sum is formed in 64-bit integer and FP64 arithmetic.  Error per entry
+ * within K 2^(e_r + e_c - 50) + 2^-52 |C_rc| (e_r, e_c the row and column
+ * exponents); integer matrices whose products fit 53 bits are multiplied
+ * exactly.  work: DEVICE scratch of inla_gemm_f64_workspace_bytes(n, batch)
+ * bytes, 256-byte aligned, owned by the caller.  status (DEVICE [batch], may
+ * be NULL) receives INLA_OK, or INLA_ERR_TIMEOUT where a bounded wait ran out
+ * (C is then incomplete).  Asynchronous on `stream` (a cudaStream_t; NULL =
+ * legacy default stream).  Errors: INLA_ERR_ARG, INLA_ERR_CUDA. */
+int inla_gemm_f64(int n, int batch, const double *X, const double *Y, double *C, void *work, size_t work_bytes,
+                  int32_t *status, void *stream);
+/* Scratch bytes inla_gemm_f64 needs (0 for invalid sizes). */
+size_t inla_gemm_f64_workspace_bytes(int n, int batch);
 
 /* Synthetic workload (host helper, not on the hot path; no counterpart in the
  * paper): fills *desc with a spatio-temporal SPDE x AR(1) model on an nx x nx

@@ -110,6 +110,11 @@ class Model:
     def set_tiles(self, sweep_fp64=32, sweep_fp32=64, gemm_fp32=128):
         C.check(self.lib.inla_set_tiles(self.handle, int(sweep_fp64), int(sweep_fp32), int(gemm_fp32)))
 
+    def set_fp64_products(self, tensor=True):
+        """FP64 selected-inversion products on the BF16 tensor cores (digit
+        splitting; the default) or with FP64 FMA on the CUDA cores."""
+        C.check(self.lib.inla_set_fp64_products(self.handle, int(bool(tensor))))
+
     def last_launch_count(self):
         return int(self.lib.inla_last_launch_count(self.handle))
 
@@ -316,6 +321,31 @@ def gemm_tf32x3(X, Y, stream=None):
         stream = torch.cuda.current_stream(X.device)
     C.check(lib.inla_gemm_tf32x3(int(n), int(batch), c_void_p(X.data_ptr()), c_void_p(Y.data_ptr()),
                                  c_void_p(Cm.data_ptr()), c_void_p(status.data_ptr()), c_void_p(stream.cuda_stream)))
+    return (Cm[0] if squeeze else Cm), status
+
+
+def gemm_f64(X, Y, stream=None):
+    """C[b] = X[b] @ Y[b].T in FP64 on the BF16 tensor cores (error-free digit
+    splitting) for CUDA float64 tensors of shape [batch, n, n] (or [n, n]), n a
+    multiple of 128.  Returns (C, status) with status [batch] int32."""
+    import torch
+    lib = C.load()
+    squeeze = X.dim() == 2
+    X = (X[None] if squeeze else X).contiguous()
+    Y = (Y[None] if squeeze else Y).contiguous()
+    if X.dtype != torch.float64 or Y.dtype != torch.float64 or not X.is_cuda or X.shape != Y.shape:
+        raise TypeError("X and Y must be CUDA float64 tensors of the same shape")
+    batch, n = X.shape[0], X.shape[1]
+    Cm = torch.empty_like(X)
+    status = torch.empty(batch, dtype=torch.int32, device=X.device)
+    nbytes = int(lib.inla_gemm_f64_workspace_bytes(int(n), int(batch)))
+    work = torch.empty(nbytes + 256, dtype=torch.uint8, device=X.device)
+    wptr = (work.data_ptr() + 255) // 256 * 256
+    if stream is None:
+        stream = torch.cuda.current_stream(X.device)
+    C.check(lib.inla_gemm_f64(int(n), int(batch), c_void_p(X.data_ptr()), c_void_p(Y.data_ptr()),
+                              c_void_p(Cm.data_ptr()), c_void_p(wptr), nbytes, c_void_p(status.data_ptr()),
+                              c_void_p(stream.cuda_stream)))
     return (Cm[0] if squeeze else Cm), status
 
 

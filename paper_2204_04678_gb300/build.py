@@ -17,7 +17,7 @@ OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libinla_gpu.so")
 PROBE_LIB = os.path.join(PKG, "libinla_probe.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "tc_gemm.cu", "synth.cpp"]
+SOURCES = ["dense_blocks.cu", "bta_kernels.cu", "setup_kernels.cu", "capi.cu", "tc_gemm.cu", "ozaki.cu", "synth.cpp"]
 PROBE_SOURCES = ["probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE]

@@ -80,11 +80,14 @@ SIGNATURES = {
     "inla_autotune": (c_int, [c_void_p, c_int, c_void_p, POINTER(inla_eval_opts), POINTER(c_int32)]),
     "inla_set_tiles": (c_int, [c_void_p, c_int, c_int, c_int]),
     "inla_set_wait_limit": (c_int, [c_double]),
+    "inla_set_fp64_products": (c_int, [c_void_p, c_int]),
     "inla_model_latent_dim": (c_int64, [c_void_p]),
     "inla_last_launch_count": (c_int64, [c_void_p]),
     "inla_model_destroy": (None, [c_void_p]),
     "inla_last_error": (c_char_p, []),
     "inla_gemm_tf32x3": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "inla_gemm_f64": (c_int, [c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
+    "inla_gemm_f64_workspace_bytes": (c_size_t, [c_int, c_int]),
     "inla_synth_build": (c_int, [c_int32, c_int32, c_int32, c_int64, c_int32, c_uint64, c_void_p,
                                  POINTER(inla_model_desc), POINTER(c_void_p)]),
     "inla_synth_grid_model": (c_int, [c_int32, c_uint64, POINTER(inla_model_desc), POINTER(c_void_p)]),

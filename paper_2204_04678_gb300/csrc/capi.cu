@@ -313,6 +313,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     // 29.4 vs 22.9 TFLOP/s at n_p = 2560, 33.0 vs 27.6 at n_p = 4096
     M.sweep_g32 = 64;
     M.gemm_t32 = INLA_GEMM_TF32X3;   // tensor cores where n_p % 128 == 0, else 128-wide CUDA-core tiles
+    M.f64_tensor = 1;                // FP64 selected inversion through BF16 digit slices where n_p % 128 == 0
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);
@@ -496,7 +497,9 @@ int64_t point_bytes(const DevModel &M, int rb) {
   d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
   const int64_t split = (rb == 4 && M.n_p % 128 == 0) ? 6 * s.mat : 0;   // TF32 hi / lo operands
   const int64_t dense = s.Dinv + 4 * s.mat + split;
-  return d * 8 + rup(dense * rb, 256) + 64 * 256;   // slack: each array starts on 256 bytes
+  // BF16 digit slices and row exponents of the FP64 tensor-core products' two operands
+  const int64_t digits = (rb == 8 && M.n_p % 128 == 0) ? 2 * (OZ_SLICES * s.mat * 2 + 4 * (int64_t)M.n_p) : 0;
+  return d * 8 + rup(dense * rb, 256) + digits + 64 * 256;   // slack: each array starts on 256 bytes
 }
 
 Work carve(const DevModel &M, void *base, int Pw, int rb) {
@@ -529,6 +532,19 @@ Work carve(const DevModel &M, void *base, int Pw, int rb) {
   if (rb == 4 && M.n_p % 128 == 0) {
     float **parts[6] = {&W.Dh, &W.Dl, &W.Sh, &W.Sl, &W.Uh, &W.Ul};
     for (float **q : parts) *q = static_cast<float *>(take_r(s.mat));
+  }
+  if (rb == 8 && M.n_p % 128 == 0) {
+    auto take_b = [&](int64_t bytes) {   // bytes per point
+      char *r = p;
+      p += rup(bytes * Pw, 256);
+      return static_cast<void *>(r);
+    };
+    W.sZ = OZ_SLICES * s.mat;
+    W.sE = M.n_p;
+    W.Zd = static_cast<uint16_t *>(take_b(W.sZ * 2));
+    W.Zs = static_cast<uint16_t *>(take_b(W.sZ * 2));
+    W.Ed = static_cast<int32_t *>(take_b(W.sE * 4));
+    W.Es = static_cast<int32_t *>(take_b(W.sE * 4));
   }
   W.SigAn = take(s.nbnp); W.SigAc = take(s.nbnp); W.Y = take(s.nbnp); W.sNbNp = s.nbnp;
   W.gjP = take(s.gjP); W.gjC = take(s.gjCO); W.gjO = take(s.gjCO);
@@ -690,6 +706,13 @@ bool tensor_gemm(const DevModel &M) {
   return sizeof(R) == sizeof(float) && M.gemm_t32 == INLA_GEMM_TF32X3 && M.n_p % 128 == 0;
 }
 
+// The FP64 selected-inversion products run on the BF16 tensor cores (digit
+// splitting, ozaki.cu) when enabled and the padded block size is a multiple of 128.
+template <typename R>
+bool digit_gemm(const DevModel &M) {
+  return sizeof(R) == sizeof(double) && M.f64_tensor && M.n_p % 128 == 0;
+}
+
 // Block Takahashi recursion from the last time block to the first.
 template <typename R>
 void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contractions, double *marg_var,
@@ -723,6 +746,19 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
                            0.0f, W.Uh, W.Ul, false, W.active, W.status);
       gemm_nt_tf32x3_split(L, W.P, M.n_p, W.Dh, W.Dl, W.sMat, W.Uh, W.Ul, W.sMat, reinterpret_cast<float *>(SigC),
                            W.sMat, 1.0f, Df, W.sDinv, 1.0f, nullptr, nullptr, true, W.active, W.status);
+    } else if (digit_gemm<R>(M)) {
+      // the same two products in FP64 through BF16 digit slices: U = D^-1 S^T into T1, then
+      // Sigma_tt = D^-1 U^T + D^-1; D^-1 is split once, S's slices are replaced by U's
+      const double *Dd = reinterpret_cast<const double *>(Dt);
+      double *Ud = reinterpret_cast<double *>(T1);
+      const int n = M.n_p;
+      ozaki_split(L, W.P, n, n, Dd, n, W.sDinv, W.Zd, W.sZ, W.Ed, W.sE, W.active);
+      ozaki_split(L, W.P, n, n, reinterpret_cast<const double *>(S), n, W.sMat, W.Zs, W.sZ, W.Es, W.sE, W.active);
+      gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE, Ud, n, W.sMat, 1.0, nullptr, 0,
+                    0, 0.0, false, W.active, W.status);
+      ozaki_split(L, W.P, n, n, Ud, n, W.sMat, W.Zs, W.sZ, W.Es, W.sE, W.active);
+      gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE,
+                    reinterpret_cast<double *>(SigC), n, W.sMat, 1.0, Dd, n, W.sDinv, 1.0, true, W.active, W.status);
     } else {
       const int tile = M.gemm_t32 == INLA_GEMM_TF32X3 ? 128 : M.gemm_t32;   // CUDA-core fallback
       gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, tile);
@@ -1326,6 +1362,20 @@ int inla_profile_read(inla_model *model, int kernel, double *total_ms, int64_t *
     *total_ms = ms;
     *launches = n;
     *units = u;
+  });
+}
+
+int inla_set_fp64_products(inla_model *model, int tensor) {
+  return guarded([&] {
+    if (!model || (tensor != 0 && tensor != 1)) throw ApiError(INLA_ERR_ARG, "model is NULL or tensor not 0 / 1");
+    CUDA_OK(cudaSetDevice(model->device));
+    CUDA_OK(cudaDeviceSynchronize());
+    model->M.f64_tensor = tensor;
+    for (auto &g : model->graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.stage) cudaFree(g.stage);
+    }
+    model->graphs.clear();
   });
 }
 

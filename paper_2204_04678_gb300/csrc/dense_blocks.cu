@@ -893,6 +893,7 @@ void dense_prepare() {
   ensure_attrs<double>();
   ensure_attrs<float>();
   tc_prepare();
+  ozaki_prepare();
 }
 
 // Tile width per precision from the model (defaults: 32 for FP64, where short

@@ -53,6 +53,7 @@ struct DevModel {
   int pmax;                      // longest pattern row
   int sweep_g64, sweep_g32;      // sweep tile width for FP64 / FP32 blocks (32 or 64; autotuned)
   int gemm_t32;                  // FP32 GEMM tile (64 or 128; autotuned)
+  int f64_tensor;                // FP64 selected-inversion products on the BF16 tensor cores (n_p % 128 == 0)
   int64_t m, n, nv;              // nv = n_t*n_p + n_b (padded latent length)
   const int *prow, *pcol;        // union pattern, CSR [n_s+1], [nnz]
   const int *prow_of;            // [nnz] row of each pattern entry
@@ -98,6 +99,10 @@ struct Work {
   void *T1, *S, *SigN, *SigC;            // [P][n_p][n_p]  (R)
   float *Dh, *Dl, *Sh, *Sl, *Uh, *Ul;    // [P][n_p][n_p]  TF32 hi / lo parts of the tensor-core products' operands
                                          //                (FP32 blocks with n_p % 128 == 0 only)
+  uint16_t *Zd, *Zs;                     // [P][OZ_SLICES][n_p][n_p]  BF16 digit slices of the FP64 tensor-core
+  int32_t *Ed, *Es;                      // [P][n_p]  products' operands and their row exponents
+                                         //           (FP64 blocks with n_p % 128 == 0 only)
+  int64_t sZ, sE;
   double *SigAn, *SigAc, *Y;             // [P][n_b][n_p]
   void *gjP, *gjC, *gjO;                 // [P][2][32*32], [P][n_p*32], [P][n_p*32]  (R; sized for double)
   double *QsI;                           // [P][n_p][n_p]  Q_s^-1 (Kronecker prior), always FP64
@@ -228,6 +233,21 @@ void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active);
 
 // tc_gemm.cu: C = alpha X Y^T + beta C0 in 3xTF32 on the tensor cores (n % 128 == 0)
 void tc_prepare();
+// ozaki.cu: FP64 products C = alpha X Y^T + beta C0 on the BF16 tensor cores by
+// error-free splitting into OZ_SLICES digit slices per entry (X: M x K, Y: N x K;
+// M % 128, N % 64, K % 32 == 0).  ozaki_split writes the slices of P row blocks
+// (S[b][a][r][k] BF16, point stride sS = OZ_SLICES rows K) and their exponents
+// (E[b][r], point stride sE).
+constexpr int OZ_SLICES = 8;   // digit slices per FP64 entry
+constexpr int OZ_LEVELS = 8;   // digit products s_a t_b with a + b < OZ_LEVELS
+void ozaki_prepare();
+void ozaki_split(Launch &L, int P, int rows, int K, const double *X, int64_t ldx, int64_t sX, uint16_t *S,
+                 int64_t sS, int32_t *E, int64_t sE, const int *active);
+void gemm_nt_ozaki(Launch &L, int P, int M, int N, int K, const uint16_t *Xs, int64_t sXs, const int32_t *Xe,
+                   int64_t sXe, const uint16_t *Ys, int64_t sYs, const int32_t *Ye, int64_t sYe, double *C,
+                   int64_t ldc, int64_t sC, double alpha, const double *C0, int64_t ldc0, int64_t sC0, double beta,
+                   bool lower_only, const int *active, int *status);
+
 // bound (ns of %globaltimer) on one mbarrier wait of the tensor-core kernels
 uint64_t wait_limit_ns();
 void set_wait_limit_ns(uint64_t ns);

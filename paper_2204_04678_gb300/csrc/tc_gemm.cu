@@ -39,9 +39,6 @@
 // out marks the point INLA_ERR_TIMEOUT, skips the epilogue, waits with the full
 // 2 s bound for its own copies and MMAs in flight, releases the tensor memory
 // and returns.
-#include <cuda.h>   // CUtensorMap and the tensor-map encoder's types (the encoder is looked up at run time)
-#include <cuda_runtime.h>
-
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -49,9 +46,17 @@
 #include <string>
 
 #include "inla_internal.cuh"
+#include "tc_common.cuh"
 
 namespace inla {
 namespace {
+
+using tc::global_ns;
+using tc::mbar_expect_tx;
+using tc::mbar_wait;
+using tc::smem_addr;
+using tc::tmem_ld32;
+using tc::WAIT_NS;
 
 constexpr int TCM = 128;                              // tile rows = tile columns
 constexpr int TCK = 32;                               // K per stage (one 128-byte swizzle row)
@@ -60,17 +65,12 @@ constexpr int SLAB_BYTES = TCM * TCK * 4;             // 16 KB per operand slab
 constexpr int STAGE_BYTES = 4 * SLAB_BYTES;           // X_hi, X_lo, Y_hi, Y_lo
 constexpr int TC_SMEM = 2 * STAGE_BYTES + 1024;       // two stages + alignment slack
 constexpr uint32_t TMEM_COLS = 512;                   // 2 stages x {hi*hi, cross terms} x 128 columns
-constexpr uint64_t WAIT_NS = 2000000000ull;           // bound on the waits for work in flight before an exit
 
 // Instruction descriptor of kind::tf32: D in F32 (bits 4-5 = 1), A and B in
 // TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N / 8 in
 // bits 17-22, M / 16 in bits 24-28.
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TCM >> 3) << 17) |
                            ((uint32_t)(TCM >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading
 // byte offset / 16 (bits 16-29; unused by swizzled K-major operands, set to
@@ -87,43 +87,6 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait until the mbarrier phase of the given parity has completed; false if
-// the bound (limit_ns of %globaltimer, at most 2^26 polls) ran out.  A limit
-// below 1 us makes the wait a single non-blocking test.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-  if (limit_ns < 1000) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-  }
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < (1u << 26); ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-  return false;
-}
-
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -132,19 +95,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       :
       : "r"(tmem), "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
       : "memory");
-}
-
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Split four FP32 values into TF32 hi / lo parts and store them at byte
@@ -343,10 +293,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // gemm_tf32x3_kernel, in the same order, so the results are the same.
 constexpr int TMA_STAGES = 3;
 constexpr int TMA_SMEM = TMA_STAGES * STAGE_BYTES + 1024;
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ void tma_load_slab(uint32_t dst, const CUtensorMap *map, int k0, int row0, int b,
                                               uint32_t bar) {
@@ -548,10 +494,24 @@ __global__ void split_tf32_kernel(const float *__restrict__ src, int64_t ssrc, f
               v);
 }
 
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// P row-major n x n FP32 matrices, `point_stride` floats apart; one box is a
+// 128-row x 32-float slab (128 bytes per row, 128-byte swizzle).
+CUtensorMap slab_map(const float *base, int n, int P, int64_t point_stride) {
+  CUtensorMap m;
+  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)P};
+  const cuuint64_t strides[2] = {(cuuint64_t)n * 4u, (cuuint64_t)point_stride * 4u};
+  const cuuint32_t box[3] = {(cuuint32_t)TCK, (cuuint32_t)TCM, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUresult r = tc::encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
 
+}  // namespace
+
+namespace tc {
 EncodeTiled lookup_encoder() {
   void *p = nullptr;
   cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
@@ -565,27 +525,11 @@ EncodeTiled encoder() {
   static const EncodeTiled fn = lookup_encoder();   // initialised once, thread-safe
   return fn;
 }
-
-// P row-major n x n FP32 matrices, `point_stride` floats apart; one box is a
-// 128-row x 32-float slab (128 bytes per row, 128-byte swizzle).
-CUtensorMap slab_map(const float *base, int n, int P, int64_t point_stride) {
-  CUtensorMap m;
-  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)P};
-  const cuuint64_t strides[2] = {(cuuint64_t)n * 4u, (cuuint64_t)point_stride * 4u};
-  const cuuint32_t box[3] = {(cuuint32_t)TCK, (cuuint32_t)TCM, 1u};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
-  const CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
-                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-  return m;
-}
-
-}  // namespace
+}  // namespace tc
 
 // Bound on one mbarrier wait of the tensor-core kernels (inla_set_wait_limit),
 // read at each launch and passed to the kernel.
-static std::atomic<uint64_t> g_wait_ns{WAIT_NS};
+static std::atomic<uint64_t> g_wait_ns{tc::WAIT_NS};
 uint64_t wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 void set_wait_limit_ns(uint64_t ns) { g_wait_ns.store(ns, std::memory_order_relaxed); }
 

@@ -285,6 +285,27 @@ def test_cuda_graph_newton_loop_matches_eager(pkg, lik):
     assert int(r["status"][0]) == pkg.capi.INLA_ERR_NO_CONVERGENCE
 
 
+@pytest.mark.parametrize("nx", [16, 23])
+def test_fp64_selinv_products_tensor_cores_match_oracle(pkg, nx):
+    # n_s = 256 and 529 (padded to 256 and 640, multiples of 128): the FP64 selected
+    # inversion's products through BF16 digit slices on the tensor cores, against the
+    # oracle and against the same products with FP64 FMA on the CUDA cores
+    mdl = build("z", 3, nx, 2, 800, "gaussian", seed=nx)
+    th = thetas(mdl, 2, seed=5)
+    model = pkg.Model(mdl)
+    kw = dict(grad="adjoint", want_mode=True, want_marg_var=True)
+    t = model.eval(cuda(th), **kw)
+    model.set_fp64_products(False)
+    c = model.eval(cuda(th), **kw)
+    torch.cuda.synchronize()
+    for b in range(th.shape[0]):
+        ref = bta.gaussian(mdl, th[b], want_grad=True, want_var=True)
+        check_point(t, b, ref, mdl.n)
+        check_point(c, b, ref, mdl.n)
+    vt, vc = t["marg_var"].cpu().numpy(), c["marg_var"].cpu().numpy()
+    assert np.max(np.abs(vt - vc) / vc) <= 1e-11
+
+
 def test_autotune_keeps_results(pkg):
     mdl = build("g", 3, 10, 2, 500, "gaussian", seed=21)
     th = thetas(mdl, 2, seed=8)
