@@ -613,14 +613,24 @@ def main():
     achieved = kunits / max(knl, 1) * flop_per_unit / avg_s / 1e12 if knl else None
     tf32_source = ("MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/BF16 ratio / 3 "
                    "TF32 products per 3xTF32 product, of measured")
-    if kname == "gj_update_kernel" and fp32 and tensor_sweep and tf32x3_peak:
+    bf16_peak = peaks.get("bf16_tflops")
+    digit_products = (not fp32) and n_p % 128 == 0 and n_p > 128
+    if kname == "gemm_nn_kernel" and digit_products and bf16_peak:
+        # FP64 products through 36 BF16 digit-slice products on the tensor cores: the FP64-equivalent
+        # peak is the measured BF16 dense peak / 36
+        peak, bound = bf16_peak / 36.0, "tensor"
+        peak_source = ("MEASURED_PEAKS.json bf16_tflops (burst, the kernel timed alone) / 36 BF16 digit products "
+                       "per FP64 product, of measured")
+        desc = ("FP64 products of the blocked inversion on the BF16 tensor cores (tcgen05 kind::f16, 8 digit "
+                "slices of 7 bits per entry, 128x64 tiles)")
+    elif kname == "gj_update_kernel" and fp32 and tensor_sweep and tf32x3_peak:
         peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
         desc = ("rank-64 update of the FP32 block sweep on the tensor cores (tcgen05, 3xTF32, 128x128 tiles, "
                 "K = 64)")
     elif kname == "gemm_nn_kernel" and tensor_gemm and tf32x3_peak:
         peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
-        desc = ("128x128 tile 3xTF32 GEMM of the selected inversion on the tensor cores (tcgen05, operands "
-                "split once and loaded by TMA)")
+        desc = ("128x128 tile 3xTF32 products of the blocked inversion and the selected inversion on the tensor "
+                "cores (tcgen05, operands split once and loaded by TMA)")
     else:
         peak, bound = (peak_fp32 if fp32 else peak_fp64), "alu"
         peak_source = ("measured on this GPU: " + ("FP32" if fp32 else "FP64")

@@ -82,7 +82,7 @@ __global__ void mask_failed_kernel(Work W, int64_t n, double *mv, const int *poi
 
 __global__ void zero_slot_kernel(Work W, int slot) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < W.P) W.sc[b * SC_COUNT + slot] = 0.0;
+  if (b < W.P && W.active[b]) W.sc[b * SC_COUNT + slot] = 0.0;
 }
 
 }  // namespace
@@ -488,21 +488,23 @@ Sizes sizes_of(const DevModel &M) {  // element counts per point
   return s;
 }
 
-// rb: bytes per element of the dense blocks (8 = FP64, 4 = mixed precision)
-int64_t point_bytes(const DevModel &M, int rb) {
+// rb: bytes per element of the dense blocks' storage (8 = FP64, 4 = mixed
+// precision; 8 also for mixed precision with an FP64 selected inversion);
+// mixed: the TF32 hi / lo operand arrays of the FP32 tensor-core products exist.
+int64_t point_bytes(const DevModel &M, int rb, bool mixed) {
   const Sizes s = sizes_of(M);
   int64_t d = s.theta + s.prm + s.qs + s.Rt + 2 * s.Da + 7 * s.vec + s.wv + 3 * s.nbnp + s.sc + s.pt + s.part +
               s.tippart + 5 * s.ints + 1;
   if (M.lik != INLA_LIK_GAUSSIAN) d += 4 * s.m + s.AtAp + s.Arwp;
   d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
-  const int64_t split = (rb == 4 && M.n_p % 128 == 0) ? 6 * s.mat : 0;   // TF32 hi / lo operands
-  const int64_t dense = s.Dinv + 4 * s.mat + split;
+  const int64_t split = (mixed && M.n_p % 128 == 0) ? 6 * s.mat * 4 : 0;   // TF32 hi / lo operands (bytes)
+  const int64_t dense = s.Dinv + 4 * s.mat;
   // BF16 digit slices and row exponents of the FP64 tensor-core products' two operands
   const int64_t digits = (rb == 8 && M.n_p % 128 == 0) ? 2 * (OZ_SLICES * s.mat * 2 + 4 * (int64_t)M.n_p) : 0;
-  return d * 8 + rup(dense * rb, 256) + digits + 64 * 256;   // slack: each array starts on 256 bytes
+  return d * 8 + rup(dense * rb, 256) + split + digits + 64 * 256;   // slack: each array starts on 256 bytes
 }
 
-Work carve(const DevModel &M, void *base, int Pw, int rb) {
+Work carve(const DevModel &M, void *base, int Pw, int rb, bool mixed) {
   const Sizes s = sizes_of(M);
   Work W{};
   W.rb = rb;
@@ -529,9 +531,12 @@ Work carve(const DevModel &M, void *base, int Pw, int rb) {
   W.sVec = s.vec;
   W.wv = take(s.wv); W.sWV = s.wv;
   W.T1 = take_r(s.mat); W.S = take_r(s.mat); W.SigN = take_r(s.mat); W.SigC = take_r(s.mat); W.sMat = s.mat;
-  if (rb == 4 && M.n_p % 128 == 0) {
+  if (mixed && M.n_p % 128 == 0) {
     float **parts[6] = {&W.Dh, &W.Dl, &W.Sh, &W.Sl, &W.Uh, &W.Ul};
-    for (float **q : parts) *q = static_cast<float *>(take_r(s.mat));
+    for (float **q : parts) {
+      *q = reinterpret_cast<float *>(p);
+      p += rup((int64_t)s.mat * Pw * 4, 256);
+    }
   }
   if (rb == 8 && M.n_p % 128 == 0) {
     auto take_b = [&](int64_t bytes) {   // bytes per point
@@ -572,8 +577,10 @@ Work carve(const DevModel &M, void *base, int Pw, int rb) {
 // stride of point b is the count; sc, pt and Tipp use fixed strides.
 static_assert(SC_COUNT <= 32, "sc slots");
 
-int wave_points(inla_model *mdl, int64_t P_total, int rb) {
-  const int64_t per = point_bytes(mdl->M, rb);
+int64_t point_bytes_for(const DevModel &M, const inla_eval_opts &o);
+
+int wave_points(inla_model *mdl, int64_t P_total, const inla_eval_opts &o) {
+  const int64_t per = point_bytes_for(mdl->M, o);
   size_t free_b = 0, total_b = 0;
   CUDA_OK(cudaMemGetInfo(&free_b, &total_b));
   const int64_t avail = (int64_t)free_b + (int64_t)mdl->ws_bytes - (int64_t)(2ll << 30);
@@ -582,8 +589,8 @@ int wave_points(inla_model *mdl, int64_t P_total, int rb) {
   return (int)std::min<int64_t>(P_total, std::min<int64_t>(cap, 65535));
 }
 
-void ensure_workspace(inla_model *mdl, int Pw, int rb) {
-  const size_t need = (size_t)point_bytes(mdl->M, rb) * Pw;
+void ensure_workspace(inla_model *mdl, int Pw, const inla_eval_opts &o) {
+  const size_t need = (size_t)point_bytes_for(mdl->M, o) * Pw;
   if (mdl->ws && mdl->ws_bytes >= need) return;
   if (mdl->ws) {
     CUDA_OK(cudaStreamSynchronize(mdl->stream));
@@ -706,6 +713,34 @@ bool tensor_gemm(const DevModel &M) {
   return sizeof(R) == sizeof(float) && M.gemm_t32 == INLA_GEMM_TF32X3 && M.n_p % 128 == 0;
 }
 
+// INLA_MIXED on meshes finer than this: the selected inversion (marginal
+// variances, the adjoint's traces) runs on an FP64 factorisation at the mode,
+// and the workspace is carved for FP64 blocks.  FP32 blocks carry errors of
+// order kappa(D_t) 2^-24, and kappa(Q_s) of the alpha = 2 SPDE grows like h^-4:
+// on the 64 x 64 mesh the FP32 selected inverse missed the mixed form's budget
+// (gradient 3.4e-4, variances 1e-4) while f and the refined mode kept theirs.
+constexpr int MIXED_FP64_SELINV_NS = 3000;
+
+bool mixed_fp64_selinv(const DevModel &M, const inla_eval_opts &o) {
+  return o.precision == INLA_MIXED && (o.want_marg_var || o.grad == INLA_GRAD_ADJOINT) &&
+         M.n_s > MIXED_FP64_SELINV_NS;
+}
+
+// Bytes per element of the workspace's dense blocks for these options.
+int workspace_rb(const DevModel &M, const inla_eval_opts &o) {
+  return (o.precision == INLA_MIXED && !mixed_fp64_selinv(M, o)) ? 4 : 8;
+}
+
+int64_t point_bytes_for(const DevModel &M, const inla_eval_opts &o) {
+  return point_bytes(M, workspace_rb(M, o), o.precision == INLA_MIXED);
+}
+
+Work carve_for(const DevModel &M, void *base, int Pw, const inla_eval_opts &o) {
+  Work W = carve(M, base, Pw, workspace_rb(M, o), o.precision == INLA_MIXED);
+  W.rb = o.precision == INLA_MIXED ? 4 : 8;   // the dense blocks' arithmetic (an FP64-sized workspace may hold FP32 blocks)
+  return W;
+}
+
 // The FP64 selected-inversion products run on the BF16 tensor cores (digit
 // splitting, ozaki.cu) when enabled and the padded block size is a multiple of 128.
 template <typename R>
@@ -742,10 +777,11 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
       const float *Df = reinterpret_cast<const float *>(Dt);
       split_tf32(L, W.P, Df, W.sDinv, W.Dh, W.Dl, W.sMat, np2, W.active);
       split_tf32(L, W.P, reinterpret_cast<const float *>(S), W.sMat, W.Sh, W.Sl, W.sMat, np2, W.active);
-      gemm_nt_tf32x3_split(L, W.P, M.n_p, W.Dh, W.Dl, W.sMat, W.Sh, W.Sl, W.sMat, nullptr, W.sMat, 1.0f, nullptr, 0,
-                           0.0f, W.Uh, W.Ul, false, W.active, W.status);
-      gemm_nt_tf32x3_split(L, W.P, M.n_p, W.Dh, W.Dl, W.sMat, W.Uh, W.Ul, W.sMat, reinterpret_cast<float *>(SigC),
-                           W.sMat, 1.0f, Df, W.sDinv, 1.0f, nullptr, nullptr, true, W.active, W.status);
+      const int n = M.n_p;
+      gemm_nt_tf32x3_split(L, W.P, n, n, n, W.Dh, W.Dl, W.sMat, W.Sh, W.Sl, W.sMat, nullptr, n, W.sMat, 1.0f, nullptr,
+                           n, 0, 0.0f, W.Uh, W.Ul, false, W.active, W.status);
+      gemm_nt_tf32x3_split(L, W.P, n, n, n, W.Dh, W.Dl, W.sMat, W.Uh, W.Ul, W.sMat, reinterpret_cast<float *>(SigC), n,
+                           W.sMat, 1.0f, Df, n, W.sDinv, 1.0f, nullptr, nullptr, true, W.active, W.status);
     } else if (digit_gemm<R>(M)) {
       // the same two products in FP64 through BF16 digit slices: U = D^-1 S^T into T1, then
       // Sigma_tt = D^-1 U^T + D^-1; D^-1 is split once, S's slices are replaced by U's
@@ -780,6 +816,11 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
   const DevModel &M = mdl->M;
   const bool adj = o.grad == INLA_GRAD_ADJOINT;
   const bool need_sel = (centre_flags & 1) != 0;
+  // mixed precision on a fine mesh: the selected inversion from an FP64 factorisation
+  // at the mode, in the same (FP64-sized) workspace
+  const bool esc = sizeof(R) == sizeof(float) && need_sel && mixed_fp64_selinv(M, o);
+  Work Wd = W;
+  Wd.rb = 8;
   CUDA_OK(cudaMemsetAsync(W.sc, 0, sizeof(double) * 32 * W.P, L.st));
   CUDA_OK(cudaMemsetAsync(W.pt, 0, sizeof(double) * W.sPt * W.P, L.st));
   CUDA_OK(cudaMemsetAsync(W.status, 0, sizeof(int) * W.P, L.st));
@@ -803,7 +844,12 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     factor<R>(L, M, W, ASM_Q, SC_LOGDET_Q);
     if (adj) {
       k_set_active(L, W, 2);
-      selinv<R>(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false);
+      if (esc) {
+        factor<double>(L, M, Wd, ASM_Q, SC_LOGDET_Q);
+        selinv<double>(L, M, Wd, ASM_Q, true, nullptr, nullptr, 0, false);
+      } else {
+        selinv<R>(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false);
+      }
       k_set_active(L, W, 0);
     }
   }
@@ -815,7 +861,12 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
       k_set_active(L, W, 1);
-      selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+      if (esc) {
+        factor<double>(L, M, Wd, ASM_QC, SC_LOGDET_QC);
+        selinv<double>(L, M, Wd, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+      } else {
+        selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+      }
       k_set_active(L, W, 0);
     }
   } else {
@@ -885,14 +936,20 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
       k_set_active(L, W, 1);
-      selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+      if (esc) {
+        factor<double>(L, M, Wd, ASM_QC, SC_LOGDET_QC);   // Q_c at the mode, assembled above
+        selinv<double>(L, M, Wd, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+      } else {
+        selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+      }
       if (adj) {
         k_set_active(L, W, 2);
         k_poisson_wobs(L, M, W);
         CUDA_OK(cudaMemsetAsync(W.rhs, 0, sizeof(double) * W.sVec * W.P, L.st));
         k_obs_assemble(L, M, W.P, W.active, nullptr, 0, W.wobs, W.sM, false, nullptr, nullptr, 0, nullptr, 0,
                        nullptr, 0, W.rhs, W.sVec, W.tippart);
-        solve<R>(L, M, W, W.rhs, W.xprev);
+        if (esc) solve<double>(L, M, Wd, W.rhs, W.xprev);
+        else solve<R>(L, M, W, W.rhs, W.xprev);
         k_quadforms(L, M, W, W.xprev, W.x, PT_LD_C, SC_TIP_LX);
       }
       k_set_active(L, W, 0);
@@ -935,8 +992,8 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
   mdl->launches = 0;
   // the workspace is shared by all calls on this model: order this call after the previous one
   if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
-  const int Pw = wave_points(mdl, P_total, rb);
-  ensure_workspace(mdl, Pw, rb);
+  const int Pw = wave_points(mdl, P_total, *opts);
+  ensure_workspace(mdl, Pw, *opts);
   BatchBufs bb = batch_buffers(mdl, P_total);
   if (opts->use_graph && Pw == P_total && !mdl->prof.enabled) {
     replay_graph(mdl, B, theta_dev, opts, out, st, bb, rb);
@@ -966,7 +1023,7 @@ void enqueue_eval(inla_model *mdl, Launch &L, int B, const double *theta_dev, co
   if (opts->grad == INLA_GRAD_ADJOINT) centre_flags |= 2;
   for (int64_t w0 = 0; w0 < P_total; w0 += Pw) {
     const int P = (int)std::min<int64_t>(Pw, P_total - w0);
-    Work W = carve(mdl->M, mdl->ws, Pw, rb);
+    Work W = carve_for(mdl->M, mdl->ws, Pw, *opts);
     W.P = P;
     CUDA_OK(cudaMemcpyAsync(W.theta, bb.theta_all + 4 * w0, sizeof(double) * 4 * P, cudaMemcpyDeviceToDevice, st));
     // theta rows are read with stride 4 by the parameter kernel
@@ -1118,7 +1175,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   const double eps = opts->fd_eps > 0 ? opts->fd_eps : 1e-3;
   const int64_t P_total = (int64_t)B * per;
   // the whole batch is one wave: workspace, then the per-point batch arrays
-  const int64_t ws_bytes = point_bytes(mdl->M, rb) * P_total;
+  const int64_t ws_bytes = point_bytes_for(mdl->M, *opts) * P_total;
   const int64_t bb_bytes = rup(32 * P_total, 256) + rup(8 * P_total, 256) + rup(32 * P_total, 256) +
                            3 * rup(4 * P_total, 256);
   if (P_total > 65535 || ws_bytes + bb_bytes > (int64_t)INLA_STATIC_SCRATCH_BYTES)
@@ -1130,7 +1187,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   mdl->launches = 0;
   Launch L{st, &mdl->launches, nullptr};
   if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
-  Work W0 = carve(mdl->M, base, (int)P_total, rb);
+  Work W0 = carve_for(mdl->M, base, (int)P_total, *opts);
   char *p = base + ws_bytes;
   auto take = [&](int64_t bytes) { char *r = p; p += rup(bytes, 256); return r; };
   BatchBufs bb;
@@ -1177,7 +1234,7 @@ int inla_workspace_bytes(const inla_model *model, int B, const inla_eval_opts *o
   return guarded([&] {
     if (!model || !opts || !bytes || B < 1) throw ApiError(INLA_ERR_ARG, "invalid arguments");
     const int per = fd_points_per_centre(opts->grad);
-    *bytes = (size_t)point_bytes(model->M, opts->precision == INLA_MIXED ? 4 : 8) * (size_t)B * per;
+    *bytes = (size_t)point_bytes_for(model->M, *opts) * (size_t)B * per;
   });
 }
 

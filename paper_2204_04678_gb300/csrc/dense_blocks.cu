@@ -823,20 +823,23 @@ void ensure_attrs() {
   done[dev] = true;
 }
 
-// Block sweep inversion with G x G pivots (see the kernels above).
+// Block sweep inversion with G x G pivots (see the kernels above) of the
+// nsub x nsub block at A (leading dimension ld; the kernels' n_p argument is
+// the leading dimension).
 template <typename R, int G>
-void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet_out,
-                 int logdet_slot_stride) {
+void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, int ld, int nsub,
+                 double *logdet_out, int logdet_slot_stride) {
   using S = Sweep<G>;
-  const int n_p = M.n_p, nt = n_p / G, P = W.P;
+  const int n_p = ld, nt = nsub / G, P = W.P;
   const int ntri = nt * (nt + 1) / 2;
-  const int64_t sCO = (int64_t)n_p * G;
-  const int tnt = n_p / T, tntri = tnt * (tnt + 1) / 2;
+  const int64_t sCO = (int64_t)M.n_p * G;
+  const int tnt = nsub / T, tntri = tnt * (tnt + 1) / 2;
   R *Pb = reinterpret_cast<R *>(W.gjP);
   R *Cb = reinterpret_cast<R *>(W.gjC);
   R *Ob = reinterpret_cast<R *>(W.gjO);
   const double unit = (double)G * G * G / (64.0 * 64.0 * 64.0);   // one tile product in 64^3 units
-  const bool tensor_update = sizeof(R) == 4 && G == 64 && M.sweep_g32 == INLA_SWEEP_TF32X3 && n_p % 128 == 0;
+  const bool tensor_update =
+      sizeof(R) == 4 && G == 64 && M.sweep_g32 == INLA_SWEEP_TF32X3 && n_p % 128 == 0 && nsub == ld;
   for (int K = 0; K < nt; ++K) {
     if (K == 0) {
       L.start(KID_GJ_PIVOT, (double)P);
@@ -900,12 +903,135 @@ void dense_prepare() {
 // pivot sweeps matter on the slow FP64 pipe; 64 for FP32, which gives each
 // block 4x the work); inla_autotune may change them.
 template <typename R>
+void gj_invert_sub(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, int ld, int nsub,
+                   double *logdet_out, int logdet_slot_stride) {
+  ensure_attrs<R>();
+  const int g = sizeof(R) == 4 ? M.sweep_g32 : M.sweep_g64;
+  if (g == 64 || g == INLA_SWEEP_TF32X3)
+    gj_invert_g<R, 64>(L, M, W, A, strideA, ld, nsub, logdet_out, logdet_slot_stride);
+  else
+    gj_invert_g<R, 32>(L, M, W, A, strideA, ld, nsub, logdet_out, logdet_slot_stride);
+}
+
+// ---------------------------------------------------------------- blocked inversion on the tensor cores
+//
+// D^-1 and log|D| by 2 x 2 block recursion on multiples of 128, with
+//   D = [A11 A21^T; A21 A22],  Wt = A21 A11^-1,  S = A22 - Wt A21^T,
+//   D^-1 = [A11^-1 + Wt^T S^-1 Wt,  -(S^-1 Wt)^T;  -S^-1 Wt,  S^-1],
+//   log|D| = log|A11| + log|S|
+// (the block LDL^T of Sec. 2.4 applied inside one block).  Every product is an
+// X Y^T of row-major operands on the tensor cores: FP64 blocks through BF16
+// digit slices (ozaki.cu), FP32 blocks through the 3xTF32 split product
+// (tc_gemm.cu).  128 x 128 diagonal blocks are inverted by the block sweep
+// (their pivots give the log-determinant and the positive-definiteness test).
+// The four products per level cost (n/2)^3 (1 + 1/2 + 1 + 1/2) multiply-adds,
+// n^3 flops over the recursion, as the sweep.  Scratch: W.S, W.SigN, W.SigC
+// (free during a factorisation) for Wt, its transpose and the transpose of the
+// new A21; two operand buffers: digit slices W.Zd/Ed and W.Zs/Es (FP64), TF32
+// hi / lo parts W.Dh/Dl and W.Sh/Sl (FP32).
+constexpr int INV_BASE = 128;
+
+template <typename R>
+__global__ void transpose_kernel(const R *__restrict__ src, int64_t lds, int64_t ss, R *__restrict__ dst,
+                                 int64_t ldd, int64_t sd, int rows, int cols, const int *active) {
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  __shared__ R t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = src[b * ss + (int64_t)r * lds + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[b * sd + (int64_t)c * ldd + r] = t[threadIdx.x][i];
+  }
+}
+
+template <typename R>
+void transpose(Launch &L, int P, int rows, int cols, const R *src, int64_t lds, int64_t ss, R *dst, int64_t ldd,
+               int64_t sd, const int *active) {
+  transpose_kernel<R><<<dim3((cols + 31) / 32, (rows + 31) / 32, P), dim3(32, 8), 0, L.st>>>(src, lds, ss, dst, ldd,
+                                                                                            sd, rows, cols, active);
+  L.tick();
+}
+
+template <typename R>
+void mirror_sub(Launch &L, int P, int n, int ld, R *A, int64_t sA, const int *active);
+
+// Operand buffer `which` (0 or 1) of a tensor-core product: the rows x K block at
+// src (leading dimension ld, point stride ss) in the product's input format.
+void split_operand(Launch &L, const Work &W, int which, int rows, int K, const double *src, int64_t ld, int64_t ss) {
+  ozaki_split(L, W.P, rows, K, src, ld, ss, which ? W.Zs : W.Zd, W.sZ, which ? W.Es : W.Ed, W.sE, W.active);
+}
+void split_operand(Launch &L, const Work &W, int which, int rows, int K, const float *src, int64_t ld, int64_t ss) {
+  split_tf32_2d(L, W.P, rows, K, src, ld, ss, which ? W.Sh : W.Dh, which ? W.Sl : W.Dl, W.sMat, W.active);
+}
+
+// C = alpha X Y^T + beta C0 with X in operand buffer x and Y in buffer y.
+void operand_gemm(Launch &L, const Work &W, int Mr, int Nr, int K, int x, int y, double *C, int64_t ldc, int64_t sC,
+                  double alpha, const double *C0, int64_t ldc0, int64_t sC0, double beta, bool lower) {
+  gemm_nt_ozaki(L, W.P, Mr, Nr, K, x ? W.Zs : W.Zd, W.sZ, x ? W.Es : W.Ed, W.sE, y ? W.Zs : W.Zd, W.sZ,
+                y ? W.Es : W.Ed, W.sE, C, ldc, sC, alpha, C0, ldc0, sC0, beta, lower, W.active, W.status);
+}
+void operand_gemm(Launch &L, const Work &W, int Mr, int Nr, int K, int x, int y, float *C, int64_t ldc, int64_t sC,
+                  float alpha, const float *C0, int64_t ldc0, int64_t sC0, float beta, bool lower) {
+  gemm_nt_tf32x3_split(L, W.P, Mr, Nr, K, x ? W.Sh : W.Dh, x ? W.Sl : W.Dl, W.sMat, y ? W.Sh : W.Dh,
+                       y ? W.Sl : W.Dl, W.sMat, C, ldc, sC, alpha, C0, ldc0, sC0, beta, nullptr, nullptr, lower,
+                       W.active, W.status);
+}
+
+template <typename R>
+void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int ld, int o, int n, double *logdet,
+             int ldst) {
+  R *A11 = A + (int64_t)o * ld + o;
+  if (n <= INV_BASE) {
+    gj_invert_sub<R>(L, M, W, A11, sA, ld, n, logdet, ldst);
+    return;
+  }
+  const int n1 = 128 * (n / 256), n2 = n - n1, P = W.P;
+  R *A21 = A11 + (int64_t)n1 * ld, *A22 = A21 + n1;
+  R *Wt = static_cast<R *>(W.S), *Wm = static_cast<R *>(W.SigN), *Vt = static_cast<R *>(W.SigC);
+  const int64_t sM = W.sMat;
+  inv_rec<R>(L, M, W, A, sA, ld, o, n1, logdet, ldst);   // A11 <- A11^-1, full symmetric
+  // Wt = A21 A11^-1 (n2 x n1)
+  split_operand(L, W, 1, n2, n1, A21, ld, sA);
+  split_operand(L, W, 0, n1, n1, A11, ld, sA);
+  operand_gemm(L, W, n2, n1, n1, 1, 0, Wt, n1, sM, R(1), nullptr, 0, 0, R(0), false);
+  // A22 <- S = A22 - Wt A21^T (lower tiles; the sweep and the recursion read the lower triangle)
+  split_operand(L, W, 0, n2, n1, Wt, n1, sM);
+  operand_gemm(L, W, n2, n2, n1, 0, 1, A22, ld, sA, R(-1), A22, ld, sA, R(1), true);
+  inv_rec<R>(L, M, W, A, sA, ld, o + n1, n2, logdet, ldst);   // A22 <- S^-1, full symmetric
+  // A21 <- -S^-1 Wt = -(S^-1) (Wt^T)^T
+  transpose<R>(L, P, n2, n1, Wt, n1, sM, Wm, n2, sM, W.active);   // Wm = Wt^T (n1 x n2)
+  split_operand(L, W, 0, n2, n2, A22, ld, sA);
+  split_operand(L, W, 1, n1, n2, Wm, n2, sM);
+  operand_gemm(L, W, n2, n1, n2, 0, 1, A21, ld, sA, R(-1), nullptr, 0, 0, R(0), false);
+  // A11 <- A11^-1 + Wm S^-1 Wm^T = A11^-1 - A21^T Wm^T (A21 now -S^-1 Wt)
+  transpose<R>(L, P, n2, n1, A21, ld, sA, Vt, n2, sM, W.active);   // Vt = A21^T (n1 x n2)
+  split_operand(L, W, 0, n1, n2, Vt, n2, sM);
+  operand_gemm(L, W, n1, n1, n2, 0, 1, A11, ld, sA, R(-1), A11, ld, sA, R(1), true);
+  mirror_sub<R>(L, P, n, ld, A11, sA, W.active);   // upper triangle = lower (A12 = A21^T, A11 full)
+}
+
+// Whether D^-1 is formed by the blocked recursion with tensor-core products.
+template <typename R>
+bool blocked_inverse(const DevModel &M, const Work &W) {
+  if (M.n_p % 128 || M.n_p <= INV_BASE) return false;
+  if (sizeof(R) == 8) return M.f64_tensor && W.Zd;
+  return M.gemm_t32 == INLA_GEMM_TF32X3 && M.sweep_g32 != INLA_SWEEP_TF32X3 && W.Dh;
+}
+
+template <typename R>
 void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t strideA, double *logdet_out,
                int logdet_slot_stride) {
   ensure_attrs<R>();
-  const int g = sizeof(R) == 4 ? M.sweep_g32 : M.sweep_g64;
-  if (g == 64 || g == INLA_SWEEP_TF32X3) gj_invert_g<R, 64>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
-  else gj_invert_g<R, 32>(L, M, W, A, strideA, logdet_out, logdet_slot_stride);
+  if (blocked_inverse<R>(M, W)) {
+    inv_rec<R>(L, M, W, A, strideA, M.n_p, 0, M.n_p, logdet_out, logdet_slot_stride);
+    return;
+  }
+  gj_invert_sub<R>(L, M, W, A, strideA, M.n_p, M.n_p, logdet_out, logdet_slot_stride);
 }
 
 template <typename R>
@@ -935,10 +1061,15 @@ void gemm_nn(Launch &L, int P, int n, const R *A, int64_t sA, const R *B, int64_
 }
 
 template <typename R>
-void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active) {
+void mirror_sub(Launch &L, int P, int n, int ld, R *A, int64_t sA, const int *active) {
   const int nt = n / T;
-  mirror_kernel<R><<<dim3(nt * (nt + 1) / 2, P), 256, 0, L.st>>>(A, sA, n, active);
+  mirror_kernel<R><<<dim3(nt * (nt + 1) / 2, P), 256, 0, L.st>>>(A, sA, ld, active);
   L.tick();
+}
+
+template <typename R>
+void mirror_lower(Launch &L, int P, int n, R *A, int64_t sA, const int *active) {
+  mirror_sub<R>(L, P, n, n, A, sA, active);
 }
 
 template void gj_invert<double>(Launch &, const DevModel &, const Work &, double *, int64_t, double *, int);

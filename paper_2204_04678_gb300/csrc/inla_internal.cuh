@@ -255,12 +255,16 @@ void gemm_nt_tf32x3(Launch &L, int P, int n, const float *X, int64_t sX, const f
                     int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, bool lower_only,
                     const int *active, int *status);
 // The same product with operands already split into TF32 hi / lo parts (P
-// matrices each, sX / sY floats apart), fed by TMA; with Chi != nullptr the
-// result is stored split (Chi / Clo, stride sC) instead of to C.
-void gemm_nt_tf32x3_split(Launch &L, int P, int n, const float *Xh, const float *Xl, int64_t sX, const float *Yh,
-                          const float *Yl, int64_t sY, float *C, int64_t sC, float alpha, const float *C0,
-                          int64_t sC0, float beta, float *Chi, float *Clo, bool lower_only, const int *active,
-                          int *status);
+// compact M x K and N x K matrices, sX / sY floats apart; M, N % 128 == 0,
+// K % 32 == 0), fed by TMA, into C (leading dimension ldc); with Chi != nullptr
+// the result is stored split (Chi / Clo, leading dimension ldc) instead of to C.
+void gemm_nt_tf32x3_split(Launch &L, int P, int M, int N, int K, const float *Xh, const float *Xl, int64_t sX,
+                          const float *Yh, const float *Yl, int64_t sY, float *C, int64_t ldc, int64_t sC, float alpha,
+                          const float *C0, int64_t ldc0, int64_t sC0, float beta, float *Chi, float *Clo,
+                          bool lower_only, const int *active, int *status);
+// hi / lo parts of the rows x K block at src (leading dimension lds) into compact arrays (K % 4 == 0).
+void split_tf32_2d(Launch &L, int P, int rows, int K, const float *src, int64_t lds, int64_t ssrc, float *hi,
+                   float *lo, int64_t sdst, const int *active);
 // hi = tf32(x), lo = tf32(x - hi) for P matrices of `count` floats (count % 4 == 0).
 void split_tf32(Launch &L, int P, const float *src, int64_t ssrc, float *hi, float *lo, int64_t sdst, int64_t count,
                 const int *active);

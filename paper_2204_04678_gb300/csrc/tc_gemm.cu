@@ -305,9 +305,10 @@ __device__ __forceinline__ void tma_load_slab(uint32_t dst, const CUtensorMap *m
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tf32x3_tma_kernel(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
-                           const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl, int n,
-                           float *C, int64_t sC, float alpha, const float *C0, int64_t sC0, float beta, float *Chi,
-                           float *Clo, int lower_only, const int *active, int *status, uint64_t wait_ns) {
+                           const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl, int N,
+                           int K, float *C, int64_t ldc, int64_t sC, float alpha, const float *C0, int64_t ldc0,
+                           int64_t sC0, float beta, float *Chi, float *Clo, int lower_only, const int *active,
+                           int *status, uint64_t wait_ns) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   int ti, tj;
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     while (ti * (ti + 1) / 2 > t) --ti;
     tj = t - ti * (ti + 1) / 2;
   } else {
-    const int nt = n / TCM;
+    const int nt = N / TCM;
     ti = blockIdx.x / nt;
     tj = blockIdx.x % nt;
   }
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  const int nch = n / TCK;
+  const int nch = K / TCK;
   // the four slabs of chunk c into stage c % TMA_STAGES (thread 0)
   auto issue = [&](int c) {
     const int s = c % TMA_STAGES;
@@ -443,8 +444,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (!aborted) {
     const int row = i0 + 32 * quarter + lane;
-    const int64_t off = (int64_t)row * n + j0 + half * 64;
-    const float *c0row = C0 ? C0 + b * sC0 + off : nullptr;
+    const int64_t off = (int64_t)row * ldc + j0 + half * 64;
+    const float *c0row = C0 ? C0 + b * sC0 + (int64_t)row * ldc0 + j0 + half * 64 : nullptr;
 #pragma unroll
     for (int e = 0; e < 64; e += 4) {
       float4 o = make_float4(alpha * racc[e], alpha * racc[e + 1], alpha * racc[e + 2], alpha * racc[e + 3]);
@@ -494,12 +495,27 @@ __global__ void split_tf32_kernel(const float *__restrict__ src, int64_t ssrc, f
               v);
 }
 
-// P row-major n x n FP32 matrices, `point_stride` floats apart; one box is a
+// hi / lo parts of the rows x K block at src (leading dimension lds) of P
+// points into compact rows x K arrays (point stride sdst).  K % 4 == 0.
+__global__ void split_tf32_2d_kernel(const float *__restrict__ src, int64_t lds, int64_t ssrc, int rows, int K,
+                                     float *__restrict__ hi, float *__restrict__ lo, int64_t sdst, const int *active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int q4 = K / 4;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)rows * q4) return;
+  const int r = (int)(q / q4), c = (int)(q % q4) * 4;
+  const float4 v = *reinterpret_cast<const float4 *>(src + b * ssrc + (int64_t)r * lds + c);
+  const int64_t o = b * sdst + (int64_t)r * K + c;
+  split_store(reinterpret_cast<uint8_t *>(hi + o), reinterpret_cast<uint8_t *>(lo + o), 0u, v);
+}
+
+// P row-major rows x K FP32 matrices, `point_stride` floats apart; one box is a
 // 128-row x 32-float slab (128 bytes per row, 128-byte swizzle).
-CUtensorMap slab_map(const float *base, int n, int P, int64_t point_stride) {
+CUtensorMap slab_map(const float *base, int rows, int K, int P, int64_t point_stride) {
   CUtensorMap m;
-  const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)P};
-  const cuuint64_t strides[2] = {(cuuint64_t)n * 4u, (cuuint64_t)point_stride * 4u};
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)P};
+  const cuuint64_t strides[2] = {(cuuint64_t)K * 4u, (cuuint64_t)point_stride * 4u};
   const cuuint32_t box[3] = {(cuuint32_t)TCK, (cuuint32_t)TCM, 1u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUresult r = tc::encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box,
@@ -554,18 +570,28 @@ void split_tf32(Launch &L, int P, const float *src, int64_t ssrc, float *hi, flo
   L.tick();
 }
 
-void gemm_nt_tf32x3_split(Launch &L, int P, int n, const float *Xh, const float *Xl, int64_t sX, const float *Yh,
-                          const float *Yl, int64_t sY, float *C, int64_t sC, float alpha, const float *C0,
-                          int64_t sC0, float beta, float *Chi, float *Clo, bool lower_only, const int *active,
-                          int *status) {
+void split_tf32_2d(Launch &L, int P, int rows, int K, const float *src, int64_t lds, int64_t ssrc, float *hi,
+                   float *lo, int64_t sdst, const int *active) {
+  const int64_t quads = (int64_t)rows * (K / 4);
+  split_tf32_2d_kernel<<<dim3((unsigned)((quads + 255) / 256), P), 256, 0, L.st>>>(src, lds, ssrc, rows, K, hi, lo,
+                                                                                   sdst, active);
+  L.tick();
+}
+
+void gemm_nt_tf32x3_split(Launch &L, int P, int M, int N, int K, const float *Xh, const float *Xl, int64_t sX,
+                          const float *Yh, const float *Yl, int64_t sY, float *C, int64_t ldc, int64_t sC, float alpha,
+                          const float *C0, int64_t ldc0, int64_t sC0, float beta, float *Chi, float *Clo,
+                          bool lower_only, const int *active, int *status) {
+  if (M % TCM || N % TCM || K % TCK || (lower_only && M != N))
+    throw std::runtime_error("gemm_nt_tf32x3_split: M, N % 128 and K % 32 must be 0 (M == N for lower_only)");
   tc_prepare();
-  const CUtensorMap mXh = slab_map(Xh, n, P, sX), mXl = slab_map(Xl, n, P, sX);
-  const CUtensorMap mYh = slab_map(Yh, n, P, sY), mYl = slab_map(Yl, n, P, sY);
-  const int nt = n / TCM;
-  const int tiles = lower_only ? nt * (nt + 1) / 2 : nt * nt;
-  L.start(KID_GEMM, (double)P * tiles * nt * 8.0);   // 8 units of 64^3 per 128^3 tile product
+  const CUtensorMap mXh = slab_map(Xh, M, K, P, sX), mXl = slab_map(Xl, M, K, P, sX);
+  const CUtensorMap mYh = slab_map(Yh, N, K, P, sY), mYl = slab_map(Yl, N, K, P, sY);
+  const int tm = M / TCM, tn = N / TCM;
+  const int tiles = lower_only ? tm * (tm + 1) / 2 : tm * tn;
+  L.start(KID_GEMM, (double)P * tiles * 8.0 * (K / 128.0));   // 8 units of 64^3 per 128 x 128 x 128
   gemm_tf32x3_tma_kernel<<<dim3(tiles, P), TC_THREADS, TMA_SMEM, L.st>>>(
-      mXh, mXl, mYh, mYl, n, C, sC, alpha, C0, sC0, beta, Chi, Clo, lower_only ? 1 : 0, active, status,
+      mXh, mXl, mYh, mYl, N, K, C, ldc, sC, alpha, C0, ldc0, sC0, beta, Chi, Clo, lower_only ? 1 : 0, active, status,
       wait_limit_ns());
   L.stop();
   L.tick();

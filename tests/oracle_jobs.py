@@ -34,10 +34,13 @@ def centre(key):
     return theta_batch(2, mdl)[0]
 
 
+BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
 def set_threads(threads):
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    """BLAS threads of worker processes started after this call (set in the parent)."""
+    for v in BLAS_ENV:
         os.environ[v] = str(threads)
-    os.environ["CUDA_VISIBLE_DEVICES"] = ""
 
 
 def evaluate(key, theta, want):

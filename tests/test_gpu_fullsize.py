@@ -34,8 +34,20 @@ def oracle():
     case (64 x 64 blocks) gets a worker with four BLAS threads of its own."""
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
-    big = ctx.Pool(1, initializer=J.set_threads, initargs=(min(4, cores),))
-    small = ctx.Pool(max(1, min(12, cores - 4)), initializer=J.set_threads, initargs=(1,))
+    # the workers import numpy before any initializer runs, so their BLAS thread
+    # counts come from the environment they are started with
+    saved = {v: os.environ.get(v) for v in J.BLAS_ENV}
+    try:
+        J.set_threads(min(4, cores))
+        big = ctx.Pool(1)
+        J.set_threads(1)
+        small = ctx.Pool(max(1, min(12, cores - 4)))
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
     jobs = {"c5s": big.apply_async(J.evaluate, ("c5s", J.centre("c5s"), True))}
     for key in ("c2", "c3s", "c4s"):
         jobs[key] = small.apply_async(J.evaluate, (key, J.centre(key), True))
