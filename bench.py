@@ -496,7 +496,38 @@ def extra_forms(model, centre, stream, steps, dist_world):
         "theta_iterations_per_s"] / its["fd_fp64"]["theta_iterations_per_s"],
         definition="gradient at the stencil centre + one 16-point line-search batch (f only), each form in "
                    "its own precision")
+    # the FD step replayed as one captured CUDA graph (the whole call, every kernel), against eager launches
+    kw = dict(grad="fd")
+    model.eval(cen, use_graph=True, **kw)
+    sec_g, _ = timed_calls(model, cen, dict(kw, use_graph=True), steps, stream)
+    sec_e, nl = timed_calls(model, cen, kw, steps, stream)
+    forms["fd_fp64_graph"] = {"value": steps / sec_g, "unit": UNIT, "ms_per_step": 1e3 * sec_g / steps,
+                              "eager_ms_per_step": 1e3 * sec_e / steps, "gpu_launches_per_step": nl / steps}
+    forms["config1_fd_fp64"] = small_workload_leg(steps)
     return forms, outs
+
+
+def small_workload_leg(steps):
+    """The 8 x 8 x 8 workload (n = 514): one FD step per call, where launch latency, not
+    arithmetic, sets the time; eager launches and one graph launch, each step timed alone
+    after a 512 MiB rewrite (the workspace fits in L2)."""
+    import torch
+    import paper_2204_04678_gb300 as pkg
+    from synth import config_model, theta_batch
+    mdl = config_model(1)
+    model = pkg.Model(mdl)
+    th = torch.tensor(theta_batch(1, mdl)[:1], dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, g in (("eager", False), ("graph", True)):
+        for _ in range(2):
+            model.eval(th, grad="fd", use_graph=g)
+        sec, nl = timed_calls(model, th, dict(grad="fd", use_graph=g), max(steps, 5), stream, flush)
+        out[name] = {"ms_per_step": 1e3 * sec / max(steps, 5), "value": max(steps, 5) / sec,
+                     "gpu_launches_per_step": nl / max(steps, 5)}
+    model.close()
+    return dict(out, unit=UNIT, workload=CONFIG_WORKLOAD[1])
 
 
 def main():

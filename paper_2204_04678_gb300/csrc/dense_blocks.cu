@@ -982,9 +982,11 @@ void operand_gemm(Launch &L, const Work &W, int Mr, int Nr, int K, int x, int y,
                        W.active, W.status);
 }
 
+// woff: offset of this level's Wt in W.S.  Wt must survive the recursion on A22,
+// which therefore places its own Wt after it (n^2 / 3 elements over all levels).
 template <typename R>
 void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int ld, int o, int n, double *logdet,
-             int ldst) {
+             int ldst, int64_t woff) {
   R *A11 = A + (int64_t)o * ld + o;
   if (n <= INV_BASE) {
     gj_invert_sub<R>(L, M, W, A11, sA, ld, n, logdet, ldst);
@@ -992,9 +994,9 @@ void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int 
   }
   const int n1 = 128 * (n / 256), n2 = n - n1, P = W.P;
   R *A21 = A11 + (int64_t)n1 * ld, *A22 = A21 + n1;
-  R *Wt = static_cast<R *>(W.S), *Wm = static_cast<R *>(W.SigN), *Vt = static_cast<R *>(W.SigC);
+  R *Wt = static_cast<R *>(W.S) + woff, *Wm = static_cast<R *>(W.SigN), *Vt = static_cast<R *>(W.SigC);
   const int64_t sM = W.sMat;
-  inv_rec<R>(L, M, W, A, sA, ld, o, n1, logdet, ldst);   // A11 <- A11^-1, full symmetric
+  inv_rec<R>(L, M, W, A, sA, ld, o, n1, logdet, ldst, woff);   // A11 <- A11^-1, full symmetric
   // Wt = A21 A11^-1 (n2 x n1)
   split_operand(L, W, 1, n2, n1, A21, ld, sA);
   split_operand(L, W, 0, n1, n1, A11, ld, sA);
@@ -1002,7 +1004,7 @@ void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int 
   // A22 <- S = A22 - Wt A21^T (lower tiles; the sweep and the recursion read the lower triangle)
   split_operand(L, W, 0, n2, n1, Wt, n1, sM);
   operand_gemm(L, W, n2, n2, n1, 0, 1, A22, ld, sA, R(-1), A22, ld, sA, R(1), true);
-  inv_rec<R>(L, M, W, A, sA, ld, o + n1, n2, logdet, ldst);   // A22 <- S^-1, full symmetric
+  inv_rec<R>(L, M, W, A, sA, ld, o + n1, n2, logdet, ldst, woff + (int64_t)n1 * n2);   // A22 <- S^-1, full
   // A21 <- -S^-1 Wt = -(S^-1) (Wt^T)^T
   transpose<R>(L, P, n2, n1, Wt, n1, sM, Wm, n2, sM, W.active);   // Wm = Wt^T (n1 x n2)
   split_operand(L, W, 0, n2, n2, A22, ld, sA);
@@ -1028,7 +1030,7 @@ void gj_invert(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stride
                int logdet_slot_stride) {
   ensure_attrs<R>();
   if (blocked_inverse<R>(M, W)) {
-    inv_rec<R>(L, M, W, A, strideA, M.n_p, 0, M.n_p, logdet_out, logdet_slot_stride);
+    inv_rec<R>(L, M, W, A, strideA, M.n_p, 0, M.n_p, logdet_out, logdet_slot_stride, 0);
     return;
   }
   gj_invert_sub<R>(L, M, W, A, strideA, M.n_p, M.n_p, logdet_out, logdet_slot_stride);

@@ -48,7 +48,7 @@ using tc::mbar_init;
 using tc::mbar_wait;
 using tc::mma_commit;
 using tc::smem_addr;
-using tc::tma_load_3d;
+using tc::tma_load_4d;
 using tc::tmem_ld16;
 using tc::WAIT_NS;
 
@@ -184,10 +184,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const uint32_t st = smem_addr(base + s * OZ_STAGE), bar = smem_addr(&full[s]);
     mbar_expect_tx(bar, (uint32_t)OZ_STAGE);
 #pragma unroll
-    for (int a = 0; a < OZ_SLICES; ++a) tma_load_3d(st + a * OZ_XBOX, &mX, c * OZ_KS, i0, b * OZ_SLICES + a, bar);
+    for (int a = 0; a < OZ_SLICES; ++a) tma_load_4d(st + a * OZ_XBOX, &mX, c * OZ_KS, i0, a, b, bar);
 #pragma unroll
-    for (int a = 0; a < OZ_SLICES; ++a)
-      tma_load_3d(st + OZ_SLICES * OZ_XBOX + a * OZ_YBOX, &mY, c * OZ_KS, j0, b * OZ_SLICES + a, bar);
+    for (int a = 0; a < OZ_SLICES; ++a) tma_load_4d(st + OZ_SLICES * OZ_XBOX + a * OZ_YBOX, &mY, c * OZ_KS, j0, a, b, bar);
   };
   if (tid == 0) {
     issue(0);
@@ -303,15 +302,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
-// P operands of `rows` x K digit slices: dims (K, rows, 8 P), one box = 32 x box_rows.
+// P operands of `rows` x K digit slices (each point's 8 planes contiguous, points
+// point_stride elements apart): dims (K, rows, 8, P), one box = 32 x box_rows.
 CUtensorMap slice_map(const uint16_t *base, int rows, int K, int P, int64_t point_stride, int box_rows) {
   CUtensorMap m;
-  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)P * OZ_SLICES};
-  const cuuint64_t strides[2] = {(cuuint64_t)K * 2u, (cuuint64_t)rows * K * 2u};
-  const cuuint32_t box[3] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, 1u};
-  const cuuint32_t estr[3] = {1u, 1u, 1u};
-  if (point_stride != (int64_t)OZ_SLICES * rows * K) throw std::runtime_error("digit slices must be contiguous");
-  const CUresult r = tc::encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t *>(base), dims,
+  const cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)OZ_SLICES, (cuuint64_t)P};
+  const cuuint64_t strides[3] = {(cuuint64_t)K * 2u, (cuuint64_t)rows * K * 2u, (cuuint64_t)point_stride * 2u};
+  const cuuint32_t box[4] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, 1u, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  if (point_stride < (int64_t)OZ_SLICES * rows * K) throw std::runtime_error("digit slices overlap");
+  const CUresult r = tc::encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(base), dims,
                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
