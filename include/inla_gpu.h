@@ -65,11 +65,14 @@ typedef enum {
   INLA_ERR_UNSUPPORTED = 7      /* option not available in this build          */
 } inla_status;
 
-/* Likelihoods (canonical links): Gaussian y ~ N(eta, 1/tau_y); Poisson
- * y ~ Pois(E exp(eta)); binomial y ~ Bin(N, 1 / (1 + exp(-eta))) with the
- * number of trials N in the E array.  The non-Gaussian ones are handled by
- * the Laplace approximation with a Newton inner loop (Sec. 2.2). */
-enum { INLA_LIK_GAUSSIAN = 0, INLA_LIK_POISSON = 1, INLA_LIK_BINOMIAL = 2 };
+/* Likelihoods: Gaussian y ~ N(eta, 1/tau_y); Poisson y ~ Pois(E exp(eta));
+ * binomial y ~ Bin(N, 1 / (1 + exp(-eta))) with the number of trials N in the
+ * E array; negative binomial y ~ NB(mean E exp(eta), size r) with the size r
+ * (overdispersion, var = mean + mean^2 / r) a fixed model constant (nb_size).
+ * The non-Gaussian ones are handled by the Laplace approximation with a Newton
+ * inner loop (Sec. 2.2); for the negative binomial's log link, which is not
+ * canonical, the Newton weight is the observed information. */
+enum { INLA_LIK_GAUSSIAN = 0, INLA_LIK_POISSON = 1, INLA_LIK_BINOMIAL = 2, INLA_LIK_NEGBINOMIAL = 3 };
 /* Gradient of f: none; central differences (Eq. central_diff: 2d + 1 = 9
  * evaluations per centre); the adjoint (selected-inverse traces, one extra
  * solve for non-Gaussian data); forward differences (d + 1 = 5 evaluations
@@ -110,7 +113,7 @@ typedef struct {
   int32_t n_t;            /* number of time steps (>= 1)                          */
   int32_t n_s;            /* number of mesh vertices (>= 1)                       */
   int32_t n_b;            /* number of fixed effects (>= 0)                       */
-  int32_t lik;            /* INLA_LIK_GAUSSIAN, _POISSON or _BINOMIAL             */
+  int32_t lik;            /* INLA_LIK_GAUSSIAN, _POISSON, _BINOMIAL, _NEGBINOMIAL  */
   int64_t m;              /* number of observations (>= 1)                        */
   const double *C_diag;   /* [n_s] lumped mass matrix C (all > 0)                 */
   const int32_t *G_rowptr;/* [n_s+1] CSR row pointers of the stiffness matrix G   */
@@ -121,14 +124,16 @@ typedef struct {
                           /* one time block [t n_s, (t+1) n_s) and any number of   */
                           /* fixed-effect entries in [n_t n_s, n)                   */
   const double *A_val;    /* values                                                */
-  const double *y;        /* [m] observations (Poisson: non-negative integers;     */
-                          /* binomial: integers 0 <= y <= N)                       */
-  const double *E;        /* [m] Poisson: exposures (> 0); binomial: numbers of    */
-                          /* trials N (positive integers); NULL for Gaussian        */
+  const double *y;        /* [m] observations (Poisson, negative binomial:         */
+                          /* non-negative integers; binomial: integers 0..N)       */
+  const double *E;        /* [m] Poisson, negative binomial: exposures (> 0);      */
+                          /* binomial: numbers of trials N (positive integers);    */
+                          /* NULL for Gaussian                                      */
   double tau_b;           /* fixed-effect prior precision (Gaussian; > 0; the      */
                           /* other likelihoods take tau_b = exp(theta_1))          */
   double prior_mean[4];   /* hyperprior: theta_j ~ N(prior_mean[j], prior_sd[j]^2) */
   double prior_sd[4];
+  double nb_size;         /* negative binomial: size r > 0 (ignored otherwise)     */
 } inla_model_desc;
 
 typedef struct {

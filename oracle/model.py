@@ -12,6 +12,8 @@ here is the workload's reading of it:
   Q(theta) = Q_t (x) Q_s  (+)  tau_b I_{n_b}       (time-major, fixed effects last)
   Gaussian: theta_1 = log tau_y, y | x ~ N(A x, tau_y^-1 I), tau_b fixed
   Poisson:  theta_1 = log tau_b, y_i | x ~ Poisson(E_i exp(eta_i))
+  binomial: theta_1 = log tau_b, y_i | x ~ Bin(N_i, logistic(eta_i))
+  negative binomial: theta_1 = log tau_b, y_i | x ~ NB(mean E_i exp(eta_i), size r), r fixed
   log pi(theta) = sum_j log N(theta_j; mu_j, s_j^2)
 
 Everything is float64 and built with scipy.sparse exactly as written above.
@@ -107,9 +109,23 @@ def binomial_loglik(model, eta):
     return float(np.sum(logC - y * np.logaddexp(0.0, -eta) - (N - y) * np.logaddexp(0.0, eta)))
 
 
+def negbinomial_loglik(model, eta):
+    """sum_i log NB(y_i; mean mu_i = E_i e^eta_i, size r):
+    lgamma(y + r) - lgamma(r) - lgamma(y + 1) + r log(r / (r + mu)) + y log(mu / (r + mu))."""
+    from scipy.special import gammaln
+    y, r = model.y, float(model.nb_size)
+    mu = model.E * np.exp(eta)
+    return float(np.sum(gammaln(y + r) - gammaln(r) - gammaln(y + 1.0) + r * np.log(r / (r + mu))
+                        + y * np.log(mu / (r + mu))))
+
+
 def glm_loglik(model, eta):
-    """log p(y | eta) of a non-Gaussian likelihood (Poisson or binomial)."""
-    return poisson_loglik(model, eta) if model.lik == "poisson" else binomial_loglik(model, eta)
+    """log p(y | eta) of a non-Gaussian likelihood (Poisson, binomial or negative binomial)."""
+    if model.lik == "poisson":
+        return poisson_loglik(model, eta)
+    if model.lik == "negbinomial":
+        return negbinomial_loglik(model, eta)
+    return binomial_loglik(model, eta)
 
 
 NEWTON_DETA = 2.0
@@ -126,14 +142,23 @@ def capped_step(A, x, xn, deta=NEWTON_DETA):
 
 
 def glm_terms(model, eta):
-    """First, second and third derivatives of b, where log p(y | eta) =
-    y eta - b(eta) + const (canonical link): Poisson b = E e^eta, binomial
-    b = N log(1 + e^eta).  They are the mean, the Newton weight D and the
-    derivative of D (for the adjoint gradient)."""
+    """(y - score, D, dD/deta) per observation, with score = d log p(y | eta) / d eta
+    and D = -d^2 log p / d eta^2, the Newton weight.  For the canonical links
+    (log p = y eta - b(eta) + const: Poisson b = E e^eta, binomial
+    b = N log(1 + e^eta)) these are the first three derivatives of b: the mean,
+    the Newton weight and its derivative.  The negative binomial with the log
+    link (mean mu = E e^eta, size r) is not canonical: score = y - (y + r) mu / (r + mu)
+    and D = (y + r) r mu / (r + mu)^2, the observed information, which the
+    Laplace approximation's Hessian at the mode uses (Sec. 2.2)."""
     eta = np.asarray(eta, dtype=float)
     if model.lik == "poisson":
         mu = model.E * np.exp(eta)
         return mu, mu, mu
+    if model.lik == "negbinomial":
+        y, r = model.y, float(model.nb_size)
+        mu = model.E * np.exp(eta)
+        s = r + mu
+        return (y + r) * mu / s, (y + r) * r * mu / s ** 2, (y + r) * r * mu * (r - mu) / s ** 3
     p = 1.0 / (1.0 + np.exp(-eta))
     q = 1.0 / (1.0 + np.exp(eta))
     N = model.E

@@ -44,8 +44,9 @@ class Model:
 
     ``data`` provides n_t, n_s, n_b, m, lik ('gaussian' / 'poisson'), C_diag,
     G (CSR: G_rowptr, G_col, G_val), A (CSR: A_rowptr int64, A_col, A_val),
-    y, E (Poisson exposures / binomial trials), tau_b, prior_mean[4], prior_sd[4]
-    (e.g. ``synth.GridModel``); lik is "gaussian", "poisson" or "binomial".
+    y, E (Poisson / negative-binomial exposures, binomial trials), tau_b,
+    prior_mean[4], prior_sd[4], nb_size (negative binomial) (e.g. ``synth.GridModel``);
+    lik is "gaussian", "poisson", "binomial" or "negbinomial".
     """
 
     def __init__(self, data, device: int = 0):
@@ -57,7 +58,8 @@ class Model:
         d = C.inla_model_desc()
         d.n_t, d.n_s, d.n_b, d.m = int(data.n_t), int(data.n_s), int(data.n_b), int(data.m)
         d.lik = {"gaussian": C.INLA_LIK_GAUSSIAN, "poisson": C.INLA_LIK_POISSON,
-                 "binomial": C.INLA_LIK_BINOMIAL}[data.lik]
+                 "binomial": C.INLA_LIK_BINOMIAL, "negbinomial": C.INLA_LIK_NEGBINOMIAL}[data.lik]
+        d.nb_size = float(getattr(data, "nb_size", 0.0) or 0.0)
         d.C_diag = _ptr(keep["C"], c_double)
         d.G_rowptr = _ptr(keep["Gr"], ctypes.c_int32)
         d.G_col = _ptr(keep["Gc"], ctypes.c_int32)

@@ -20,6 +20,7 @@ INLA_ERR_UNSUPPORTED = 7
 INLA_LIK_GAUSSIAN = 0
 INLA_LIK_POISSON = 1
 INLA_LIK_BINOMIAL = 2
+INLA_LIK_NEGBINOMIAL = 3
 INLA_GRAD_NONE = 0
 INLA_GRAD_FD_CENTRAL = 1
 INLA_GRAD_ADJOINT = 2
@@ -48,7 +49,8 @@ class inla_model_desc(ctypes.Structure):
                 ("G_rowptr", POINTER(c_int32)), ("G_col", POINTER(c_int32)), ("G_val", POINTER(c_double)),
                 ("A_rowptr", POINTER(c_int64)), ("A_col", POINTER(c_int32)), ("A_val", POINTER(c_double)),
                 ("y", POINTER(c_double)), ("E", POINTER(c_double)),
-                ("tau_b", c_double), ("prior_mean", c_double * 4), ("prior_sd", c_double * 4)]
+                ("tau_b", c_double), ("prior_mean", c_double * 4), ("prior_sd", c_double * 4),
+                ("nb_size", c_double)]
 
 
 class inla_eval_opts(ctypes.Structure):

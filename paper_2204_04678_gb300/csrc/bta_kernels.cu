@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(256) obs_reduce_kernel(DevModel M, Work W, int
       const double r = M.y[i] - eta;
       s = fma(r, r, s);
     } else {
-      s += M.y[i] * eta - glm_terms(M.lik, M.E[i], eta).b;
+      s += M.y[i] * eta - glm_terms(M.lik, M.E[i], M.y[i], M.nb_size, eta).b;
     }
   }
   s = block_sum(s, red);
@@ -1082,14 +1082,14 @@ __global__ void poisson_eta_kernel(DevModel M, Work W, const double *x) {
   if (i >= M.m) return;
   const double eta = obs_eta(M, x + b * W.sVec, i);
   W.eta[b * W.sM + i] = eta;
-  W.mu[b * W.sM + i] = glm_terms(M.lik, M.E[i], eta).weight;
+  W.mu[b * W.sM + i] = glm_terms(M.lik, M.E[i], M.y[i], M.nb_size, eta).weight;
 }
 
 __device__ __forceinline__ double obs_r(const DevModel &M, const double *r, int64_t sR, bool r_newton,
                                         const double *mu, int64_t sMu, const double *eta, int b, int64_t i) {
   if (r_newton) {   // Newton right-hand side per observation: y - b'(eta) + b''(eta) eta
     const double e = eta[b * sMu + i];
-    return M.y[i] - glm_terms(M.lik, M.E[i], e).mean + mu[b * sMu + i] * e;
+    return M.y[i] - glm_terms(M.lik, M.E[i], M.y[i], M.nb_size, e).mean + mu[b * sMu + i] * e;
   }
   return r[b * sR + i];
 }
@@ -1241,7 +1241,7 @@ __global__ void poisson_wobs_kernel(DevModel M, Work W) {
   if (!W.active[b]) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M.m) return;
-  W.wobs[b * W.sM + i] = 0.5 * W.qobs[b * W.sM + i] * glm_terms(M.lik, M.E[i], W.eta[b * W.sM + i]).third;
+  W.wobs[b * W.sM + i] = 0.5 * W.qobs[b * W.sM + i] * glm_terms(M.lik, M.E[i], M.y[i], M.nb_size, W.eta[b * W.sM + i]).third;
 }
 
 // r = b - Q_c x in FP64 from the sparse blocks (iterative refinement of the

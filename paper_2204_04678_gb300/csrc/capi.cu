@@ -161,11 +161,14 @@ void validate(const inla_model_desc *d) {
   if (d->n_t < 1 || d->n_s < 1) bad("n_t and n_s must be >= 1");
   if (d->n_b < 0 || d->n_b > MAX_NB) bad("n_b must be in [0, 16]");
   if (d->m < 1 || d->m > (int64_t)INT32_MAX) bad("m must be in [1, 2^31)");
-  if (d->lik != INLA_LIK_GAUSSIAN && d->lik != INLA_LIK_POISSON && d->lik != INLA_LIK_BINOMIAL)
+  if (d->lik != INLA_LIK_GAUSSIAN && d->lik != INLA_LIK_POISSON && d->lik != INLA_LIK_BINOMIAL &&
+      d->lik != INLA_LIK_NEGBINOMIAL)
     bad("unknown likelihood");
+  if (d->lik == INLA_LIK_NEGBINOMIAL && !(d->nb_size > 0.0 && std::isfinite(d->nb_size)))
+    bad("negative binomial size must be positive and finite");
   if (!d->C_diag || !d->G_rowptr || !d->G_col || !d->G_val || !d->A_rowptr || !d->A_col || !d->A_val || !d->y)
     bad("a required array is NULL");
-  if (d->lik == INLA_LIK_POISSON && !d->E) bad("Poisson likelihood needs exposures E");
+  if ((d->lik == INLA_LIK_POISSON || d->lik == INLA_LIK_NEGBINOMIAL) && !d->E) bad("this likelihood needs exposures E");
   if (d->lik == INLA_LIK_BINOMIAL && !d->E) bad("binomial likelihood needs the numbers of trials in E");
   if (d->lik == INLA_LIK_GAUSSIAN && !(d->tau_b > 0.0)) bad("tau_b must be > 0");
   for (int j = 0; j < 4; ++j)
@@ -201,9 +204,9 @@ void validate(const inla_model_desc *d) {
     }
     if (nsp < 1 || nsp > MAX_SPATIAL) bad("each A row needs 1 to 3 spatial entries");
     if (!std::isfinite(d->y[r])) bad("y not finite");
-    if (d->lik == INLA_LIK_POISSON) {
+    if (d->lik == INLA_LIK_POISSON || d->lik == INLA_LIK_NEGBINOMIAL) {
       if (!(d->E[r] > 0.0) || !std::isfinite(d->E[r])) bad("E must be positive");
-      if (d->y[r] < 0.0 || d->y[r] != std::floor(d->y[r])) bad("Poisson y must be non-negative integers");
+      if (d->y[r] < 0.0 || d->y[r] != std::floor(d->y[r])) bad("count data y must be non-negative integers");
     }
     if (d->lik == INLA_LIK_BINOMIAL) {
       if (!(d->E[r] >= 1.0) || d->E[r] != std::floor(d->E[r]) || d->E[r] > 1e9)
@@ -232,6 +235,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     M.nv = (int64_t)n_t * M.n_p + n_b;
     for (int j = 0; j < 4; ++j) { M.prior_mean[j] = d->prior_mean[j]; M.prior_sd[j] = d->prior_sd[j]; }
     M.tau_b_fixed = d->tau_b;
+    M.nb_size = d->lik == INLA_LIK_NEGBINOMIAL ? d->nb_size : 0.0;
 
     // observations: time block, vertices, weights, covariates; stable sort by time
     std::vector<int> ot(m);

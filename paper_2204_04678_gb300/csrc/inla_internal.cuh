@@ -77,6 +77,7 @@ struct DevModel {
   const double *consts;          // [4]: y^T y, sum lgamma(y+1), sum y log E
   double prior_mean[4], prior_sd[4];
   double tau_b_fixed;
+  double nb_size;                // negative binomial size r (0 for the other likelihoods)
 };
 
 // Per-wave workspace (device) with per-point strides (in elements).  The dense
@@ -197,16 +198,28 @@ struct Launch {
   }
 };
 
-// Canonical-link likelihood terms per observation: y eta - b(eta) is the
-// log-likelihood up to constants, b' the mean, b'' the Newton weight and b''' the
-// derivative of the weight (adjoint gradient).  Poisson: b = E exp(eta) (all
-// three derivatives equal b); binomial: b = N log(1 + exp(eta)), p = logistic(eta),
-// b' = N p, b'' = N p (1 - p), b''' = N p (1 - p) (1 - 2 p).
+// Likelihood terms per observation: y eta - b is the log-likelihood up to
+// theta-free constants, y - mean its derivative in eta (the score), weight the
+// Newton weight -d^2 log p / d eta^2, third the derivative of the weight
+// (adjoint gradient).  Canonical links: Poisson b = E exp(eta) (mean, weight and
+// third all equal b); binomial b = N log(1 + exp(eta)), p = logistic(eta), mean
+// N p, weight N p (1 - p), third N p (1 - p) (1 - 2 p).  Negative binomial with
+// the log link (mu = E exp(eta), size r; not canonical): b = (y + r) log(mu + r),
+// mean (y + r) mu / (mu + r), weight (y + r) r mu / (mu + r)^2 (the observed
+// information), third (y + r) r mu (r - mu) / (mu + r)^3.
 struct GlmTerms {
   double b, mean, weight, third;
 };
-__device__ __forceinline__ GlmTerms glm_terms(int lik, double E, double eta) {
+__device__ __forceinline__ GlmTerms glm_terms(int lik, double E, double y, double r, double eta) {
   GlmTerms g;
+  if (lik == INLA_LIK_NEGBINOMIAL) {
+    const double mu = E * exp(eta), s = mu + r, a = (y + r) * mu / s;
+    g.b = (y + r) * log(s);
+    g.mean = a;
+    g.weight = a * r / s;
+    g.third = g.weight * (r - mu) / s;
+    return g;
+  }
   if (lik == INLA_LIK_BINOMIAL) {
     const double p = 1.0 / (1.0 + exp(-eta));
     const double q = 1.0 / (1.0 + exp(eta));   // 1 - p without cancellation

@@ -27,8 +27,9 @@ __global__ void fem_values_kernel(int nnz, const int *prow_of, const int *pcol, 
 
 // consts[0] = y^T y; the theta-free part of the log-likelihood is
 // consts[2] - consts[1]: Poisson sum(y log E) - sum(log y!), binomial
-// sum(log N! - log (N - y)!) - sum(log y!) = sum log C(N, y).
-__global__ void consts_kernel(int64_t m, const double *y, const double *E, int lik, double *consts) {
+// sum(log N! - log (N - y)!) - sum(log y!) = sum log C(N, y), negative binomial
+// sum(y log E + log Gamma(y + r) - log Gamma(r) + r log r) - sum(log y!).
+__global__ void consts_kernel(int64_t m, const double *y, const double *E, int lik, double r, double *consts) {
   __shared__ double red[3][256];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
@@ -39,6 +40,9 @@ __global__ void consts_kernel(int64_t m, const double *y, const double *E, int l
     } else if (lik == INLA_LIK_BINOMIAL) {
       s1 += lgamma(y[i] + 1.0);
       s2 += lgamma(E[i] + 1.0) - lgamma(E[i] - y[i] + 1.0);
+    } else if (lik == INLA_LIK_NEGBINOMIAL) {
+      s1 += lgamma(y[i] + 1.0);
+      s2 += y[i] * log(E[i]) + lgamma(y[i] + r) - lgamma(r) + r * log(r);
     }
   }
   red[0][threadIdx.x] = s0;
@@ -68,7 +72,7 @@ void setup_theta_free(cudaStream_t st, DevModel &M, const int64_t *d_hptr, const
 }
 
 void setup_consts(cudaStream_t st, DevModel &M, double *consts) {
-  consts_kernel<<<1, 256, 0, st>>>(M.m, M.y, M.E, M.lik, consts);
+  consts_kernel<<<1, 256, 0, st>>>(M.m, M.y, M.E, M.lik, M.nb_size, consts);
 }
 
 void setup_gaussian(cudaStream_t st, DevModel &M, double *AtA, double *Arw, double *Tip, double *Aty,

@@ -278,6 +278,7 @@ void build(int n_t, int nx, int n_b, int64_t m, int lik, uint64_t seed, const do
   d->y = o.y.data();
   d->E = lik != INLA_LIK_GAUSSIAN ? o.E.data() : nullptr;
   d->tau_b = tau_b;
+  d->nb_size = 0.0;
   for (int j = 0; j < 4; ++j) {
     d->prior_mean[j] = 0.0;
     d->prior_sd[j] = 10.0;

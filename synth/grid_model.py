@@ -15,8 +15,9 @@ random Fourier features and an AR(1) recursion in time, not from any
 precision matrix the method assembles.
 
 Substream ids (seed 0 unless stated): 0 observation times, 1 observation
-locations, 2 covariates, 3 field, 4 beta, 5 noise / Poisson / binomial
-draws, 6 exposure / numbers of trials (1..10), 7 hyperparameter batch.
+locations, 2 covariates, 3 field, 4 beta, 5 noise / Poisson / binomial /
+negative-binomial draws, 6 exposure / numbers of trials (1..10), 7
+hyperparameter batch.
 """
 from dataclasses import dataclass, field
 import numpy as np
@@ -26,6 +27,7 @@ from .rng import Stream
 THETA_TRUE_GAUSSIAN = np.array([1.0, -1.0, 0.0, 1.5])
 THETA_TRUE_POISSON = np.array([np.log(1e-3), -1.0, 0.0, 1.5])
 FD_EPS = 1e-3
+NB_SIZE = 4   # size (overdispersion) r of the negative-binomial workloads, a fixed model constant
 
 
 @dataclass
@@ -46,7 +48,8 @@ class GridModel:
     A_col: np.ndarray             # int32 column indices
     A_val: np.ndarray
     y: np.ndarray                 # [m]
-    E: np.ndarray = None          # [m] exposure (Poisson) / number of trials (binomial)
+    E: np.ndarray = None          # [m] exposure (Poisson, negative binomial) / number of trials (binomial)
+    nb_size: float = 0.0          # negative binomial size r (0 for the other likelihoods)
     prior_mean: np.ndarray = field(default_factory=lambda: np.zeros(4))
     prior_sd: np.ndarray = field(default_factory=lambda: np.full(4, 10.0))
     obs_t: np.ndarray = None      # [m] time slice of each observation
@@ -172,7 +175,7 @@ def matern_field(stream: Stream, nx: int, n_t: int, range_: float, sigma: float,
 def build(name: str, n_t: int, nx: int, n_b: int, m: int, lik: str = "gaussian", seed: int = 0,
           theta_true=None, tau_b: float = 1e-3) -> GridModel:
     """Build one workload.  See the module docstring for the recipe."""
-    if lik not in ("gaussian", "poisson", "binomial"):
+    if lik not in ("gaussian", "poisson", "binomial", "negbinomial"):
         raise ValueError(lik)
     theta_true = np.array(theta_true if theta_true is not None else
                           (THETA_TRUE_GAUSSIAN if lik == "gaussian" else THETA_TRUE_POISSON), dtype=float)
@@ -211,12 +214,17 @@ def build(name: str, n_t: int, nx: int, n_b: int, m: int, lik: str = "gaussian",
         E = 0.5 + 1.5 * s_exp.uniform(m)
         y = s_noise.poisson(E * np.exp(eta)).astype(np.float64)
         prior_mean = np.array([np.log(1e-3), 0.0, 0.0, 0.0])
+    elif lik == "negbinomial":
+        E = 0.5 + 1.5 * s_exp.uniform(m)
+        y = s_noise.negbinomial(NB_SIZE, E * np.exp(eta)).astype(np.float64)
+        prior_mean = np.array([np.log(1e-3), 0.0, 0.0, 0.0])
     else:
         trials = 1 + s_exp.integers(m, 10)
         E = trials.astype(np.float64)
         y = s_noise.binomial(trials, 1.0 / (1.0 + np.exp(-eta))).astype(np.float64)
         prior_mean = np.array([np.log(1e-3), 0.0, 0.0, 0.0])
     return GridModel(name=name, n_t=n_t, nx=nx, n_b=n_b, m=m, lik=lik, tau_b=tau_b,
+                     nb_size=float(NB_SIZE) if lik == "negbinomial" else 0.0,
                      C_diag=C, G_rowptr=G_rowptr, G_col=G_col, G_val=G_val,
                      A_rowptr=A_rowptr, A_col=A_col.ravel(), A_val=A_val.ravel(), y=y, E=E,
                      prior_mean=prior_mean, prior_sd=np.full(4, 10.0), obs_t=obs_t,

@@ -99,6 +99,18 @@ class Stream:
             active[idx] = (u[idx] > cdf[idx]) & (p[idx] > 0.0)
         return k
 
+    def negbinomial(self, size: int, mean: np.ndarray) -> np.ndarray:
+        """Negative binomial counts NB(mean, size) for an integer size r: the sum of r
+        geometric counts of success probability r / (r + mean), each by inversion
+        floor(log U / log(1 - p)) of one uniform (r uniforms per count)."""
+        mean = np.asarray(mean, dtype=np.float64)
+        q = mean / (size + mean)                    # failure probability 1 - p
+        u = self.uniform_open(size * mean.size).reshape(size, mean.size)
+        with np.errstate(divide="ignore"):
+            g = np.floor(np.log(u) / np.log(q))
+        g = np.where(q > 0.0, g, 0.0)
+        return g.sum(axis=0).astype(np.int64)
+
     def binomial(self, trials: np.ndarray, p: np.ndarray) -> np.ndarray:
         """Binomial counts Bin(trials, p) by CDF inversion, one uniform each."""
         n = np.asarray(trials, dtype=np.int64)

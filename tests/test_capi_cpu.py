@@ -112,7 +112,8 @@ def _split_row(m):
     (lambda d, m: m.A_col.__setitem__(0, 10 ** 6), "out of range"),
     (lambda d, m: m.C_diag.__setitem__(3, 0.0), "C_diag"),
     (lambda d, m: _split_row(m), "one time block"),
-    (lambda d, m: setattr(d, "lik", 3), "unknown likelihood"),
+    (lambda d, m: setattr(d, "lik", 4), "unknown likelihood"),
+    (lambda d, m: setattr(d, "lik", 3), "negative binomial size"),
     (lambda d, m: setattr(d, "lik", C.INLA_LIK_BINOMIAL), "trials"),
     (lambda d, m: _binomial(d, m, trials=2.5), "positive integers"),
     (lambda d, m: _binomial(d, m, y=3.0), "[0, N]"),

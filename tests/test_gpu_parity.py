@@ -77,7 +77,9 @@ def test_gaussian_batch_matches_oracle(pkg, n_t, nx, n_b, m):
 
 @pytest.mark.parametrize("lik,n_t,nx,n_b,m", [("poisson", 3, 4, 2, 250), ("poisson", 2, 10, 1, 400),
                                               ("poisson", 1, 3, 0, 80), ("binomial", 3, 4, 2, 250),
-                                              ("binomial", 2, 10, 1, 400), ("binomial", 1, 3, 0, 80)])
+                                              ("binomial", 2, 10, 1, 400), ("binomial", 1, 3, 0, 80),
+                                              ("negbinomial", 3, 4, 2, 250), ("negbinomial", 2, 10, 1, 400),
+                                              ("negbinomial", 1, 3, 0, 80), ("negbinomial", 3, 16, 2, 900)])
 def test_poisson_batch_matches_oracle(pkg, lik, n_t, nx, n_b, m):
     mdl = build("p", n_t, nx, n_b, m, lik, seed=5)
     th = thetas(mdl, k=3, seed=1)
@@ -225,7 +227,8 @@ MIX_F, MIX_G, MIX_X, MIX_V = 1e-6, 1e-5, 1e-9, 5e-5
 
 @pytest.mark.parametrize("lik,n_t,nx,n_b,m", [("gaussian", 4, 10, 3, 600), ("gaussian", 6, 13, 2, 1500),
                                               ("gaussian", 1, 4, 0, 60), ("poisson", 3, 6, 2, 400),
-                                              ("binomial", 3, 6, 2, 400)])
+                                              ("binomial", 3, 6, 2, 400), ("negbinomial", 3, 6, 2, 400),
+                                              ("gaussian", 3, 16, 2, 900), ("negbinomial", 3, 16, 2, 900)])
 def test_mixed_precision_matches_oracle(pkg, lik, n_t, nx, n_b, m):
     mdl = build("mx", n_t, nx, n_b, m, lik, seed=7)
     th = thetas(mdl, 3, seed=3)
@@ -261,7 +264,7 @@ def test_cuda_graph_replay_matches_eager(pkg):
                     assert torch.equal(eager[key], graph[key]), (kw, k, key)
 
 
-@pytest.mark.parametrize("lik", ["poisson", "binomial"])
+@pytest.mark.parametrize("lik", ["poisson", "binomial", "negbinomial"])
 def test_cuda_graph_newton_loop_matches_eager(pkg, lik):
     # uneven Newton counts in one graph launch: the loop is a conditional while-node
     mdl = build("p", 3, 6, 2, 400, lik, seed=13)

@@ -140,7 +140,27 @@ def test_binomial_loglik_matches_scipy_and_its_derivatives_are_b_prime():
                            rtol=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("lik", ["gaussian", "poisson", "binomial"])
+def test_negbinomial_loglik_matches_scipy_and_its_terms_are_derivatives():
+    mdl = small(lik="negbinomial")
+    eta = np.linspace(-2, 2, mdl.m)
+    r = mdl.nb_size
+    mu = mdl.E * np.exp(eta)
+    ref = stats.nbinom.logpmf(mdl.y, r, r / (r + mu)).sum()
+    assert np.isclose(M.negbinomial_loglik(mdl, eta), ref, rtol=1e-12)
+    # (y - score, D, dD/deta) against central differences of the log-likelihood, observation by observation
+    ll = lambda e: (stats.nbinom.logpmf(mdl.y, r, r / (r + mdl.E * np.exp(e))))
+    h = 1e-4
+    score = (ll(eta + h) - ll(eta - h)) / (2 * h)
+    ymm, wgt, third = M.glm_terms(mdl, eta)
+    assert np.allclose(mdl.y - ymm, score, rtol=1e-6, atol=1e-8)
+    d2 = (ll(eta + h) - 2 * ll(eta) + ll(eta - h)) / h ** 2
+    assert np.allclose(wgt, -d2, rtol=1e-4, atol=1e-6)
+    assert np.all(wgt > 0)
+    assert np.allclose(third, (M.glm_terms(mdl, eta + h)[1] - M.glm_terms(mdl, eta - h)[1]) / (2 * h),
+                       rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("lik", ["gaussian", "poisson", "binomial", "negbinomial"])
 def test_dQ_matches_finite_difference_of_Q(lik):
     mdl = small(lik=lik)
     th = mdl.theta_true + np.array([0.1, 0.05, -0.1, 0.2])
@@ -309,7 +329,7 @@ def test_gaussian_bta_matches_dense_definition():
     assert np.allclose(d["var"], b["var"], rtol=1e-11)
 
 
-@pytest.mark.parametrize("lik", ["gaussian", "poisson", "binomial"])
+@pytest.mark.parametrize("lik", ["gaussian", "poisson", "binomial", "negbinomial"])
 def test_adjoint_gradient_matches_central_differences(lik):
     mdl = small(n_t=3, nx=4, n_b=2, m=200, lik=lik)
     th = mdl.theta_true + np.array([0.1, -0.1, 0.05, 0.2])
@@ -342,7 +362,7 @@ def test_fd_stencil_layout_and_gradient():
 
 # ---------------------------------------------------------------- Poisson (Laplace, Sec. 2.2)
 
-@pytest.mark.parametrize("lik", ["poisson", "binomial"])
+@pytest.mark.parametrize("lik", ["poisson", "binomial", "negbinomial"])
 def test_poisson_mode_is_stationary_and_matches_dense_newton(lik):
     mdl = small(n_t=3, nx=4, n_b=2, m=250, lik=lik)
     th = mdl.theta_true + np.array([0.5, 0.0, 0.1, 0.0])
@@ -351,8 +371,14 @@ def test_poisson_mode_is_stationary_and_matches_dense_newton(lik):
     A = M.obs_matrix(mdl)
     Q = M.prior_Q(mdl, th)
     eta = A @ b["x"]
-    mean = mdl.E * np.exp(eta) if lik == "poisson" else mdl.E / (1.0 + np.exp(-eta))
-    grad = Q @ b["x"] - A.T @ (mdl.y - mean)
+    if lik == "poisson":
+        score = mdl.y - mdl.E * np.exp(eta)
+    elif lik == "binomial":
+        score = mdl.y - mdl.E / (1.0 + np.exp(-eta))
+    else:   # d/deta of log NB(y; E e^eta, r), written out independently of glm_terms
+        mu = mdl.E * np.exp(eta)
+        score = mdl.y * mdl.nb_size / (mdl.nb_size + mu) - mdl.nb_size * mu / (mdl.nb_size + mu)
+    grad = Q @ b["x"] - A.T @ score
     assert np.abs(grad).max() < 1e-8 * max(1.0, np.abs(A.T @ mdl.y).max())
     assert b["converged"] and d["converged"]
     assert abs(b["f"] - d["f"]) < 1e-11 * abs(d["f"])
@@ -360,7 +386,7 @@ def test_poisson_mode_is_stationary_and_matches_dense_newton(lik):
     assert np.allclose(b["var"], d["var"], rtol=1e-10)
 
 
-@pytest.mark.parametrize("lik", ["poisson", "binomial"])
+@pytest.mark.parametrize("lik", ["poisson", "binomial", "negbinomial"])
 def test_poisson_laplace_matches_generic_laplace_formula(lik):
     # log p(y|theta) ~ h(x*) + (n/2) log 2 pi - 1/2 log|-h''(x*)|, with
     # h(x) = log pi(x|theta) + log p(y|x, theta), mode from a generic optimiser
@@ -372,15 +398,23 @@ def test_poisson_laplace_matches_generic_laplace_formula(lik):
     n = mdl.n
     logdetQ = np.linalg.slogdet(Q)[1]
 
+    r = mdl.nb_size
+
     def logp(eta):
         if lik == "poisson":
             return stats.poisson.logpmf(mdl.y, mdl.E * np.exp(eta)).sum()
+        if lik == "negbinomial":
+            return stats.nbinom.logpmf(mdl.y, r, r / (r + mdl.E * np.exp(eta))).sum()
         return stats.binom.logpmf(mdl.y, mdl.E, 1.0 / (1.0 + np.exp(-eta))).sum()
 
     def mean_and_weight(eta):
+        """(y - d logp / d eta, -d^2 logp / d eta^2) per observation."""
         if lik == "poisson":
             mu = mdl.E * np.exp(eta)
             return mu, mu
+        if lik == "negbinomial":
+            mu = mdl.E * np.exp(eta)
+            return mdl.y - r * (mdl.y - mu) / (r + mu), r * mu * (mdl.y + r) / (r + mu) ** 2
         pr = 1.0 / (1.0 + np.exp(-eta))
         return mdl.E * pr, mdl.E * pr * (1.0 - pr)
 

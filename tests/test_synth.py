@@ -85,3 +85,13 @@ def test_theta_batches():
     assert len({tuple(r) for r in ccd}) == 25
     lp = line_points(np.zeros(4), np.array([1.0, 0, 0, 0]))
     assert lp.shape == (16, 4) and np.isclose(lp[:, 0].max(), 0.5) and np.isclose(lp[:, 0].min(), -0.1)
+
+
+def test_negative_binomial_draws_have_the_nb_moments():
+    from synth.rng import Stream
+    mean = np.full(200_000, 3.0)
+    y = Stream(11, 5).negbinomial(4, mean).astype(float)
+    # NB(mean 3, size 4): variance mean + mean^2 / size = 5.25
+    assert abs(y.mean() - 3.0) < 0.02
+    assert abs(y.var() - 5.25) < 0.1
+    assert y.min() >= 0 and np.all(y == np.floor(y))
