@@ -792,8 +792,8 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
       const double *Dd = reinterpret_cast<const double *>(Dt);
       double *Ud = reinterpret_cast<double *>(T1);
       const int n = M.n_p;
-      ozaki_split(L, W.P, n, n, Dd, n, W.sDinv, W.Zd, W.sZ, W.Ed, W.sE, W.active);
-      ozaki_split(L, W.P, n, n, reinterpret_cast<const double *>(S), n, W.sMat, W.Zs, W.sZ, W.Es, W.sE, W.active);
+      ozaki_split2(L, W.P, n, n, Dd, n, W.sDinv, W.Zd, W.Ed, n, n, reinterpret_cast<const double *>(S), n, W.sMat,
+                   W.Zs, W.Es, W.sZ, W.sE, W.active);
       gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE, Ud, n, W.sMat, 1.0, nullptr, 0,
                     0, 0.0, false, W.active, W.status);
       ozaki_split(L, W.P, n, n, Ud, n, W.sMat, W.Zs, W.sZ, W.Es, W.sE, W.active);

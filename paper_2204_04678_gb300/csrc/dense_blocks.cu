@@ -196,79 +196,15 @@ __device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) 
   }
 }
 
-// Scalar sweep of the lower triangle: G steps, each one FMA per lower entry;
-// the fewest FP64 instructions, which matters when the fused sweep shares an
-// SM whose FP64 pipe the update blocks saturate.
-template <typename R, int G>
-__device__ void sweep_tile_scalar(R *sm, R *Pout, double *logdet, int *status) {
-  using S = Sweep<G>;
-  R *a = sm;                       // [G][LD]
-  R *colp = sm + G * S::LD;        // [G]  column p of the current state
-  R *cinv = colp + G;              // [G]  column p divided by the pivot
-  R *pivs = cinv + G;              // [G]  pivots
-  __shared__ R s_inv;
-  __shared__ int s_bad;
-  __shared__ double s_log[2];
-  const int tid = threadIdx.x;
-  int ei[S::PER], ej[S::PER];
-  int ne = 0;
-  for (int e = tid; e < S::TRI; e += S::THREADS) {
-    int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= e) ++i;
-    while (i * (i + 1) / 2 > e) --i;
-    ei[ne] = i;
-    ej[ne] = e - i * (i + 1) / 2;
-    ++ne;
-  }
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int p = 0; p < G; ++p) {
-    if (tid == 0) {
-      const R piv = a[p * S::LD + p];
-      const bool ok = (piv > R(0)) && (piv < R(INFINITY));
-      pivs[p] = ok ? piv : R(1);
-      s_inv = ok ? R(1) / piv : R(0);
-      if (!ok) s_bad = 1;
-    }
-    __syncthreads();
-    if (tid < G) {
-      const R c = (tid >= p) ? a[tid * S::LD + p] : a[p * S::LD + tid];
-      colp[tid] = c;
-      cinv[tid] = c * s_inv;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < S::PER; ++k) {
-      if (k >= ne) break;
-      const int i = ei[k], j = ej[k];
-      R *ap = &a[i * S::LD + j];
-      if (i == p) *ap = (j == p) ? -s_inv : cinv[j];
-      else if (j == p) *ap = cinv[i];
-      else *ap = fma(-cinv[i], colp[j], *ap);
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < G * G; e += S::THREADS) {
-    const int i = e >> S::SHIFT, j = e & (G - 1);
-    Pout[e] = -((j <= i) ? a[i * S::LD + j] : a[j * S::LD + i]);
-  }
-  if (tid < G) {
-    double l = log((double)pivs[tid]);
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((tid & 31) == 0) s_log[tid >> 5] = l;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    *logdet += s_log[0] + (G > 32 ? s_log[1] : 0.0);
-    if (s_bad) *status = INLA_ERR_NOT_SPD;
-  }
-}
-
-// FP64: scalar sweep; FP32: two-level sweep (12 block barriers instead of 192).
+// The two-level sweep (16 x 16 sub-pivots swept by one warp with shuffles,
+// G / 16 * 3 block barriers instead of 3 G).  The pivot inversion sits on the
+// critical path of every sweep step, and with the dense products on the tensor
+// cores the sweep runs only on 128 x 128 base blocks, where its launches are short:
+// an element-by-element sweep (one FMA per lower entry per step, the fewest FP64
+// instructions) measured ~40 us per 32 x 32 FP64 pivot there.
 template <typename R, int G>
 __device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
-  if (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
-  else sweep_tile_scalar<R, G>(sm, Pout, logdet, status);
+  sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
 }
 
 // Pivot block 0 of an inversion (later pivots are inverted by the update
@@ -968,6 +904,17 @@ void split_operand(Launch &L, const Work &W, int which, int rows, int K, const d
 void split_operand(Launch &L, const Work &W, int which, int rows, int K, const float *src, int64_t ld, int64_t ss) {
   split_tf32_2d(L, W.P, rows, K, src, ld, ss, which ? W.Sh : W.Dh, which ? W.Sl : W.Dl, W.sMat, W.active);
 }
+// Both operand buffers at once: src0 into buffer 0, src1 into buffer 1.
+void split_operands(Launch &L, const Work &W, int rows0, int K0, const double *src0, int64_t ld0, int64_t ss0,
+                    int rows1, int K1, const double *src1, int64_t ld1, int64_t ss1) {
+  ozaki_split2(L, W.P, rows0, K0, src0, ld0, ss0, W.Zd, W.Ed, rows1, K1, src1, ld1, ss1, W.Zs, W.Es, W.sZ, W.sE,
+               W.active);
+}
+void split_operands(Launch &L, const Work &W, int rows0, int K0, const float *src0, int64_t ld0, int64_t ss0,
+                    int rows1, int K1, const float *src1, int64_t ld1, int64_t ss1) {
+  split_operand(L, W, 0, rows0, K0, src0, ld0, ss0);
+  split_operand(L, W, 1, rows1, K1, src1, ld1, ss1);
+}
 
 // C = alpha X Y^T + beta C0 with X in operand buffer x and Y in buffer y.
 void operand_gemm(Launch &L, const Work &W, int Mr, int Nr, int K, int x, int y, double *C, int64_t ldc, int64_t sC,
@@ -998,8 +945,7 @@ void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int 
   const int64_t sM = W.sMat;
   inv_rec<R>(L, M, W, A, sA, ld, o, n1, logdet, ldst, woff);   // A11 <- A11^-1, full symmetric
   // Wt = A21 A11^-1 (n2 x n1)
-  split_operand(L, W, 1, n2, n1, A21, ld, sA);
-  split_operand(L, W, 0, n1, n1, A11, ld, sA);
+  split_operands(L, W, n1, n1, A11, ld, sA, n2, n1, A21, ld, sA);
   operand_gemm(L, W, n2, n1, n1, 1, 0, Wt, n1, sM, R(1), nullptr, 0, 0, R(0), false);
   // A22 <- S = A22 - Wt A21^T (lower tiles; the sweep and the recursion read the lower triangle)
   split_operand(L, W, 0, n2, n1, Wt, n1, sM);
@@ -1007,8 +953,7 @@ void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int 
   inv_rec<R>(L, M, W, A, sA, ld, o + n1, n2, logdet, ldst, woff + (int64_t)n1 * n2);   // A22 <- S^-1, full
   // A21 <- -S^-1 Wt = -(S^-1) (Wt^T)^T
   transpose<R>(L, P, n2, n1, Wt, n1, sM, Wm, n2, sM, W.active);   // Wm = Wt^T (n1 x n2)
-  split_operand(L, W, 0, n2, n2, A22, ld, sA);
-  split_operand(L, W, 1, n1, n2, Wm, n2, sM);
+  split_operands(L, W, n2, n2, A22, ld, sA, n1, n2, Wm, n2, sM);
   operand_gemm(L, W, n2, n1, n2, 0, 1, A21, ld, sA, R(-1), nullptr, 0, 0, R(0), false);
   // A11 <- A11^-1 + Wm S^-1 Wm^T = A11^-1 - A21^T Wm^T (A21 now -S^-1 Wt)
   transpose<R>(L, P, n2, n1, A21, ld, sA, Vt, n2, sM, W.active);   // Vt = A21^T (n1 x n2)

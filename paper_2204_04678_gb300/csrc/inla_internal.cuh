@@ -256,6 +256,10 @@ constexpr int OZ_LEVELS = 8;   // digit products s_a t_b with a + b < OZ_LEVELS
 void ozaki_prepare();
 void ozaki_split(Launch &L, int P, int rows, int K, const double *X, int64_t ldx, int64_t sX, uint16_t *S,
                  int64_t sS, int32_t *E, int64_t sE, const int *active);
+// two operands in one launch (same point strides of the slices and exponents)
+void ozaki_split2(Launch &L, int P, int rows0, int K0, const double *X0, int64_t ldx0, int64_t sX0, uint16_t *S0,
+                  int32_t *E0, int rows1, int K1, const double *X1, int64_t ldx1, int64_t sX1, uint16_t *S1,
+                  int32_t *E1, int64_t sS, int64_t sE, const int *active);
 void gemm_nt_ozaki(Launch &L, int P, int M, int N, int K, const uint16_t *Xs, int64_t sXs, const int32_t *Xe,
                    int64_t sXe, const uint16_t *Ys, int64_t sYs, const int32_t *Ye, int64_t sYe, double *C,
                    int64_t ldc, int64_t sC, double alpha, const double *C0, int64_t ldc0, int64_t sC0, double beta,

@@ -85,29 +85,38 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
 }
 
 // Row r of point b: the exponent e_r (|x| < 2^e_r on the row) and the 8 digit
-// slices, stored as S[b][a][r][k] (BF16) and E[b][r].  One block per row.
-__global__ void __launch_bounds__(256) ozaki_split_kernel(const double *__restrict__ X, int64_t ldx, int64_t sX,
-                                                          int rows, int K, uint16_t *__restrict__ S, int64_t sS,
-                                                          int32_t *__restrict__ E, int64_t sE, const int *active) {
-  const int r = blockIdx.x, b = blockIdx.y;
+// slices, stored as S[b][a][r][k] (BF16) and E[b][r].  One warp per row, 8 rows
+// per block; up to two operands per launch (rows of both are multiples of 8).
+struct SplitJob {
+  const double *X;
+  int64_t ldx, sX;
+  int rows, K;
+  uint16_t *S;
+  int64_t sS;
+  int32_t *E;
+  int64_t sE;
+};
+
+__global__ void __launch_bounds__(256) ozaki_split_kernel(SplitJob j0, SplitJob j1, int blocks0, const int *active) {
+  const int b = blockIdx.y;
   if (active && !active[b]) return;
-  const double *xr = X + b * sX + (int64_t)r * ldx;
-  __shared__ int s_max[8];
+  const bool second = (int)blockIdx.x >= blocks0;
+  const SplitJob &J = second ? j1 : j0;
+  const int r = ((int)blockIdx.x - (second ? blocks0 : 0)) * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= J.rows) return;
+  const int K = J.K;
+  const double *xr = J.X + b * J.sX + (int64_t)r * J.ldx;
   int fmax = 0;   // largest biased exponent field of the row (0: zero and subnormal entries only)
-  for (int k = threadIdx.x; k < K; k += 256) {
+  for (int k = lane; k < K; k += 32) {
     const int f = (int)((__double_as_longlong(xr[k]) >> 52) & 0x7FF);
     if (f != 0x7FF) fmax = max(fmax, f);
   }
   for (int o = 16; o > 0; o >>= 1) fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
-  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = fmax;
-  __syncthreads();
-  fmax = s_max[0];
-  for (int w = 1; w < 8; ++w) fmax = max(fmax, s_max[w]);
   const int e = (fmax == 0 ? 1 : fmax) - 1022;   // |x| < 2^e for every normal entry of the row
-  if (threadIdx.x == 0) E[b * sE + r] = e;
-  uint16_t *sr = S + b * sS + (int64_t)r * K;
-  const int64_t plane = (int64_t)rows * K;
-  for (int k = threadIdx.x; k < K; k += 256) {
+  if (lane == 0) J.E[b * J.sE + r] = e;
+  uint16_t *sr = J.S + b * J.sS + (int64_t)r * K;
+  const int64_t plane = (int64_t)J.rows * K;
+  for (int k = lane; k < K; k += 32) {
     const int64_t bits = __double_as_longlong(xr[k]);
     const int f = (int)((bits >> 52) & 0x7FF);
     int64_t T = 0;   // round(x 2^(55 - e)), |T| < 2^55
@@ -333,7 +342,18 @@ void ozaki_prepare() {
 
 void ozaki_split(Launch &L, int P, int rows, int K, const double *X, int64_t ldx, int64_t sX, uint16_t *S,
                  int64_t sS, int32_t *E, int64_t sE, const int *active) {
-  ozaki_split_kernel<<<dim3(rows, P), 256, 0, L.st>>>(X, ldx, sX, rows, K, S, sS, E, sE, active);
+  const SplitJob j{X, ldx, sX, rows, K, S, sS, E, sE};
+  const int blocks = (rows + 7) / 8;
+  ozaki_split_kernel<<<dim3(blocks, P), 256, 0, L.st>>>(j, j, blocks, active);
+  L.tick();
+}
+
+void ozaki_split2(Launch &L, int P, int rows0, int K0, const double *X0, int64_t ldx0, int64_t sX0, uint16_t *S0,
+                  int32_t *E0, int rows1, int K1, const double *X1, int64_t ldx1, int64_t sX1, uint16_t *S1,
+                  int32_t *E1, int64_t sS, int64_t sE, const int *active) {
+  const SplitJob j0{X0, ldx0, sX0, rows0, K0, S0, sS, E0, sE}, j1{X1, ldx1, sX1, rows1, K1, S1, sS, E1, sE};
+  const int b0 = (rows0 + 7) / 8, b1 = (rows1 + 7) / 8;
+  ozaki_split_kernel<<<dim3(b0 + b1, P), 256, 0, L.st>>>(j0, j1, b0, active);
   L.tick();
 }
 
