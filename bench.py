@@ -58,11 +58,14 @@ def parse():
                     help="fd: one f+grad from the 9-point stencil per step; adjoint: every point of the "
                          "workload's batch gets f and an adjoint gradient (default: the workload's own)")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
-    ap.add_argument("--graph", action="store_true", help="replay each step as a captured CUDA graph")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every kernel of a step from the host (default: replay the step as one captured CUDA "
+                         "graph, the library's use_graph option)")
     ap.add_argument("--gemm", default=None, choices=["cuda-core", "tensor"],
                     help="FP32 selected-inversion GEMM: 128x128 FP32 FMA tiles or tcgen05 3xTF32")
-    ap.add_argument("--sweep", default=None, choices=["cuda-core", "tensor"],
-                    help="FP32 block-sweep updates: FP32 FMA tiles (the library's default) or tcgen05 3xTF32")
+    ap.add_argument("--sweep", default=None, choices=["cuda-core", "tensor", "blocked"],
+                    help="FP32 Schur-block inversion: the sweep with FP32 FMA tile updates, the sweep with tcgen05 "
+                         "3xTF32 updates, or the blocked recursion with 3xTF32 products (the library picks by size)")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1,
                     help="stencil centres per step (FD mode) / copies of the batch (adjoint mode); profiling only")
@@ -579,8 +582,10 @@ def main():
     n_p = -(-mdl.n_s // 64) * 64
     tensor_sweep = n_p % 128 == 0 and args.sweep == "tensor"
     if args.gemm or args.sweep:
-        model.set_tiles(32, capi.INLA_SWEEP_TF32X3 if tensor_sweep else 64,
-                        capi.INLA_GEMM_TF32X3 if args.gemm != "cuda-core" else 128)
+        sw = {"tensor": capi.INLA_SWEEP_TF32X3, "blocked": capi.INLA_INV_BLOCKED}.get(args.sweep, 64)
+        if args.sweep is None:
+            sw = capi.INLA_INV_BLOCKED if (n_p % 128 == 0 and n_p >= 2048) else 64
+        model.set_tiles(32, sw, capi.INLA_GEMM_TF32X3 if args.gemm != "cuda-core" else 128)
     stream = torch.cuda.current_stream()
     if args.grad == "fd":
         cen = centre[None, :] + 0.01 * np.arange(args.centres)[:, None]
@@ -598,7 +603,8 @@ def main():
     grad = args.grad
     prec = args.precision
     out = model.eval(theta, grad=grad, precision=prec)
-    kw = dict(grad=grad, out=out, precision=prec, use_graph=args.graph)
+    graph = not args.eager
+    kw = dict(grad=grad, out=out, precision=prec, use_graph=graph)
     for _ in range(max(args.warmup, 1)):
         model.eval(theta, **kw)
     torch.cuda.synchronize()
@@ -684,10 +690,10 @@ def main():
     e2e = None
     if not args.no_e2e:
         th_host = theta.cpu().numpy().copy()
-        model.eval_host(th_host, grad=grad, precision=prec)
+        model.eval_host(th_host, grad=grad, precision=prec, use_graph=graph)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            model.eval_host(th_host, grad=grad, precision=prec)
+            model.eval_host(th_host, grad=grad, precision=prec, use_graph=graph)
         e2e_s = (time.perf_counter() - t0) / args.steps
         if dist:
             from paper_2204_04678_gb300.replicas import max_over_ranks
@@ -747,6 +753,7 @@ def main():
                                                         if tensor_gemm else "cuda-core"} if prec == "mixed" else {})),
                 "clocks": clk,
                 "gpu_launches": launches,
+                "launch_mode": "one captured CUDA graph per step (use_graph)" if graph else "eager launches",
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "f_evals_per_s": 9 * value if grad == "fd" else value,
                 "grad_mode": grad,

@@ -105,6 +105,12 @@ enum { INLA_FP64 = 0, INLA_MIXED = 1 };
  * (elsewhere the 64-wide CUDA-core sweep runs).  Not the default: with K = 64
  * per launch it measured slower than the CUDA-core update on GB300. */
 #define INLA_SWEEP_TF32X3 3
+/* FP32 blocks (inla_set_tiles): D_t^-1 by the 2 x 2 block recursion whose
+ * products run on the tensor cores in 3xTF32 (TMA-fed, as the selected
+ * inversion's), with 64-wide sweeps only on the 128 x 128 base blocks; used where
+ * n_s rounded up to 64 is a multiple of 128 (elsewhere the 64-wide CUDA-core
+ * sweep runs).  The default for FP32 blocks of 2048 rows or more. */
+#define INLA_INV_BLOCKED 4
 
 /* Model description.  Every pointer is a HOST pointer; the arrays are read
  * (and copied to the device) by inla_model_create and may be freed after it
@@ -259,9 +265,10 @@ int inla_eval_batch_host(inla_model *model, int B, const double *theta, const in
 int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_eval_opts *opts, int32_t *choice);
 
 /* Set the tile shapes explicitly (e.g. a choice saved from inla_autotune):
- * sweep width 32 or 64 for FP64 blocks; 32, 64 or INLA_SWEEP_TF32X3 for FP32
- * blocks; FP32 GEMM 64, 128 or INLA_GEMM_TF32X3.  A new model starts at
- * (32, 64, INLA_GEMM_TF32X3).  Errors: INLA_ERR_ARG for other values. */
+ * sweep width 32 or 64 for FP64 blocks; 32, 64, INLA_SWEEP_TF32X3 or
+ * INLA_INV_BLOCKED for FP32 blocks; FP32 GEMM 64, 128 or INLA_GEMM_TF32X3.  A
+ * new model starts at (32, 64 or INLA_INV_BLOCKED by size, INLA_GEMM_TF32X3).
+ * Errors: INLA_ERR_ARG for other values. */
 int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_fp32);
 
 /* Bound on each wait of the tensor-core kernels for their own asynchronous

@@ -205,7 +205,7 @@ class Model:
         return out
 
     def eval_host(self, theta, grad="none", prior="kronecker", want_mode=False, want_marg_var=False,
-                  max_newton=50, newton_tol=1e-8, fd_eps=1e-3, precision="fp64"):
+                  max_newton=50, newton_tol=1e-8, fd_eps=1e-3, precision="fp64", use_graph=False):
         """Evaluate with HOST numpy buffers (copies in and out inside the call)."""
         theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 4))
         B = theta.shape[0]
@@ -216,7 +216,7 @@ class Model:
             res["x_mode"] = np.empty((B, self.n))
         if want_marg_var:
             res["marg_var"] = np.empty((B, self.n))
-        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision)
+        o = make_opts(grad, prior, want_mode, want_marg_var, max_newton, newton_tol, fd_eps, precision, use_graph)
         so = C.inla_eval_out_host()
         so.f = res["f"].ctypes.data
         so.status = res["status"].ctypes.data

@@ -31,6 +31,7 @@ INLA_FP64 = 0
 INLA_MIXED = 1
 INLA_GEMM_TF32X3 = 3
 INLA_SWEEP_TF32X3 = 3
+INLA_INV_BLOCKED = 4
 KERNEL_GJ_UPDATE = 0
 KERNEL_GEMM = 1
 KERNEL_GJ_PIVOT = 2

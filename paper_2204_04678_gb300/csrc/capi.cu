@@ -315,7 +315,9 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     M.sweep_g64 = 32;
     // the CUDA-core FP32 sweep update measured faster than the tensor-core one (INLA_SWEEP_TF32X3):
     // 29.4 vs 22.9 TFLOP/s at n_p = 2560, 33.0 vs 27.6 at n_p = 4096
-    M.sweep_g32 = 64;
+    // FP32 blocks: the blocked inversion with tensor-core products measured ahead of the CUDA-core
+    // sweep from 2560 rows on (and behind it at 1024), so it is the default from 2048 on
+    M.sweep_g32 = (M.n_p % 128 == 0 && M.n_p >= 2048) ? INLA_INV_BLOCKED : 64;
     M.gemm_t32 = INLA_GEMM_TF32X3;   // tensor cores where n_p % 128 == 0, else 128-wide CUDA-core tiles
     M.f64_tensor = 1;                // FP64 selected inversion through BF16 digit slices where n_p % 128 == 0
     auto find = [&](int i, int j) -> int {
@@ -1256,10 +1258,10 @@ int inla_set_tiles(inla_model *model, int sweep_fp64, int sweep_fp32, int gemm_f
   return guarded([&] {
     if (!model) throw ApiError(INLA_ERR_ARG, "model is NULL");
     if ((sweep_fp64 != 32 && sweep_fp64 != 64) ||
-        (sweep_fp32 != 32 && sweep_fp32 != 64 && sweep_fp32 != INLA_SWEEP_TF32X3) ||
+        (sweep_fp32 != 32 && sweep_fp32 != 64 && sweep_fp32 != INLA_SWEEP_TF32X3 && sweep_fp32 != INLA_INV_BLOCKED) ||
         (gemm_fp32 != 64 && gemm_fp32 != 128 && gemm_fp32 != INLA_GEMM_TF32X3))
-      throw ApiError(INLA_ERR_ARG, "tile widths: FP64 sweep 32 or 64, FP32 sweep 32, 64 or INLA_SWEEP_TF32X3, "
-                                   "FP32 GEMM 64, 128 or INLA_GEMM_TF32X3");
+      throw ApiError(INLA_ERR_ARG, "tile widths: FP64 sweep 32 or 64, FP32 sweep 32, 64, INLA_SWEEP_TF32X3 or "
+                                   "INLA_INV_BLOCKED, FP32 GEMM 64, 128 or INLA_GEMM_TF32X3");
     CUDA_OK(cudaSetDevice(model->device));
     CUDA_OK(cudaDeviceSynchronize());
     model->M.sweep_g64 = sweep_fp64;
@@ -1304,6 +1306,7 @@ int inla_autotune(inla_model *model, int B, const double *theta_dev, const inla_
         cands.push_back({32, INLA_GEMM_TF32X3});
         cands.push_back({INLA_SWEEP_TF32X3, INLA_GEMM_TF32X3});
         cands.push_back({INLA_SWEEP_TF32X3, 128});
+        cands.push_back({INLA_INV_BLOCKED, INLA_GEMM_TF32X3});
       }
     }
     else cands = {{32, M.gemm_t32}, {64, M.gemm_t32}};

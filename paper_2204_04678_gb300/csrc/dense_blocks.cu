@@ -196,15 +196,82 @@ __device__ void sweep_tile_blocked(R *sm, R *Pout, double *logdet, int *status) 
   }
 }
 
-// The two-level sweep (16 x 16 sub-pivots swept by one warp with shuffles,
-// G / 16 * 3 block barriers instead of 3 G).  The pivot inversion sits on the
-// critical path of every sweep step, and with the dense products on the tensor
-// cores the sweep runs only on 128 x 128 base blocks, where its launches are short:
-// an element-by-element sweep (one FMA per lower entry per step, the fewest FP64
-// instructions) measured ~40 us per 32 x 32 FP64 pivot there.
+// Scalar sweep of the lower triangle: G steps, each one FMA per lower entry;
+// the fewest FP64 instructions, which matters when the fused sweep shares an
+// SM whose FP64 pipe the update blocks saturate.
+template <typename R, int G>
+__device__ void sweep_tile_scalar(R *sm, R *Pout, double *logdet, int *status) {
+  using S = Sweep<G>;
+  R *a = sm;                       // [G][LD]
+  R *colp = sm + G * S::LD;        // [G]  column p of the current state
+  R *cinv = colp + G;              // [G]  column p divided by the pivot
+  R *pivs = cinv + G;              // [G]  pivots
+  __shared__ R s_inv;
+  __shared__ int s_bad;
+  __shared__ double s_log[2];
+  const int tid = threadIdx.x;
+  int ei[S::PER], ej[S::PER];
+  int ne = 0;
+  for (int e = tid; e < S::TRI; e += S::THREADS) {
+    int i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    ei[ne] = i;
+    ej[ne] = e - i * (i + 1) / 2;
+    ++ne;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int p = 0; p < G; ++p) {
+    if (tid == 0) {
+      const R piv = a[p * S::LD + p];
+      const bool ok = (piv > R(0)) && (piv < R(INFINITY));
+      pivs[p] = ok ? piv : R(1);
+      s_inv = ok ? R(1) / piv : R(0);
+      if (!ok) s_bad = 1;
+    }
+    __syncthreads();
+    if (tid < G) {
+      const R c = (tid >= p) ? a[tid * S::LD + p] : a[p * S::LD + tid];
+      colp[tid] = c;
+      cinv[tid] = c * s_inv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < S::PER; ++k) {
+      if (k >= ne) break;
+      const int i = ei[k], j = ej[k];
+      R *ap = &a[i * S::LD + j];
+      if (i == p) *ap = (j == p) ? -s_inv : cinv[j];
+      else if (j == p) *ap = cinv[i];
+      else *ap = fma(-cinv[i], colp[j], *ap);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < G * G; e += S::THREADS) {
+    const int i = e >> S::SHIFT, j = e & (G - 1);
+    Pout[e] = -((j <= i) ? a[i * S::LD + j] : a[j * S::LD + i]);
+  }
+  if (tid < G) {
+    double l = log((double)pivs[tid]);
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((tid & 31) == 0) s_log[tid >> 5] = l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    *logdet += s_log[0] + (G > 32 ? s_log[1] : 0.0);
+    if (s_bad) *status = INLA_ERR_NOT_SPD;
+  }
+}
+
+// FP64: the element-by-element sweep (one FMA per lower entry per step, the
+// fewest FP64 instructions: the two-level form does ~3x as many FP64 FMAs and
+// measured slower on the 128 x 128 base blocks); FP32: the two-level sweep
+// (12 block barriers instead of 192).
 template <typename R, int G>
 __device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
-  sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
+  if (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
+  else sweep_tile_scalar<R, G>(sm, Pout, logdet, status);
 }
 
 // Pivot block 0 of an inversion (later pivots are inverted by the update
@@ -843,7 +910,7 @@ void gj_invert_sub(Launch &L, const DevModel &M, const Work &W, R *A, int64_t st
                    double *logdet_out, int logdet_slot_stride) {
   ensure_attrs<R>();
   const int g = sizeof(R) == 4 ? M.sweep_g32 : M.sweep_g64;
-  if (g == 64 || g == INLA_SWEEP_TF32X3)
+  if (g == 64 || g == INLA_SWEEP_TF32X3 || g == INLA_INV_BLOCKED)
     gj_invert_g<R, 64>(L, M, W, A, strideA, ld, nsub, logdet_out, logdet_slot_stride);
   else
     gj_invert_g<R, 32>(L, M, W, A, strideA, ld, nsub, logdet_out, logdet_slot_stride);
@@ -967,7 +1034,7 @@ template <typename R>
 bool blocked_inverse(const DevModel &M, const Work &W) {
   if (M.n_p % 128 || M.n_p <= INV_BASE) return false;
   if (sizeof(R) == 8) return M.f64_tensor && W.Zd;
-  return M.gemm_t32 == INLA_GEMM_TF32X3 && M.sweep_g32 != INLA_SWEEP_TF32X3 && W.Dh;
+  return M.sweep_g32 == INLA_INV_BLOCKED && W.Dh;
 }
 
 template <typename R>

@@ -97,6 +97,16 @@ def test_mixed_with_tensor_gemm_matches_oracle(pkg, lik):
     _mixed_vs_oracle(pkg, mdl, th, capi.INLA_GEMM_TF32X3)
 
 
+@pytest.mark.parametrize("lik,nx", [("gaussian", 16), ("poisson", 16), ("gaussian", 23)])
+def test_mixed_blocked_inverse_matches_oracle(pkg, lik, nx):
+    # n_s = 256 and 529 (padded to 256 and 640): D_t^-1 by the block recursion with
+    # 3xTF32 tensor-core products (one and two levels above the 128 x 128 base blocks)
+    from paper_2204_04678_gb300 import capi
+    mdl = build("tb", 3, nx, 2, 1500, lik, seed=5)
+    th = mdl.theta_true[None, :] + np.array([[0.0, 0.0, 0.0, 0.0], [0.1, -0.1, 0.05, -0.2]])
+    _mixed_vs_oracle(pkg, mdl, th, capi.INLA_GEMM_TF32X3, sweep=capi.INLA_INV_BLOCKED)
+
+
 def test_mixed_tensor_gemm_full_size_config2(pkg):
     """n_t = 50, 32 x 32 grid, m = 100 000: the stencil batch with the tensor-core
     GEMM against the FP64 path (which matches the oracle to 1e-10)."""
