@@ -925,14 +925,18 @@ void gj_invert_sub(Launch &L, const DevModel &M, const Work &W, R *A, int64_t st
 // (the block LDL^T of Sec. 2.4 applied inside one block).  Every product is an
 // X Y^T of row-major operands on the tensor cores: FP64 blocks through BF16
 // digit slices (ozaki.cu), FP32 blocks through the 3xTF32 split product
-// (tc_gemm.cu).  128 x 128 diagonal blocks are inverted by the block sweep
+// (tc_gemm.cu).  Diagonal blocks of up to 256 (FP64) or 128 (FP32) rows are inverted by the block sweep
 // (their pivots give the log-determinant and the positive-definiteness test).
 // The four products per level cost (n/2)^3 (1 + 1/2 + 1 + 1/2) multiply-adds,
 // n^3 flops over the recursion, as the sweep.  Scratch: W.S, W.SigN, W.SigC
 // (free during a factorisation) for Wt, its transpose and the transpose of the
 // new A21; two operand buffers: digit slices W.Zd/Ed and W.Zs/Es (FP64), TF32
 // hi / lo parts W.Dh/Dl and W.Sh/Sl (FP32).
-constexpr int INV_BASE = 128;
+// Diagonal blocks at most this size are inverted by the sweep: FP64 256 (the
+// sweep's launches on 128 x 128 blocks are latency-bound; 256 measured 6% faster per
+// step at n_s = 1024), FP32 128.
+template <typename R>
+constexpr int inv_base() { return sizeof(R) == 8 ? 256 : 128; }
 
 template <typename R>
 __global__ void transpose_kernel(const R *__restrict__ src, int64_t lds, int64_t ss, R *__restrict__ dst,
@@ -1002,7 +1006,7 @@ template <typename R>
 void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int ld, int o, int n, double *logdet,
              int ldst, int64_t woff) {
   R *A11 = A + (int64_t)o * ld + o;
-  if (n <= INV_BASE) {
+  if (n <= inv_base<R>()) {
     gj_invert_sub<R>(L, M, W, A11, sA, ld, n, logdet, ldst);
     return;
   }
@@ -1032,7 +1036,7 @@ void inv_rec(Launch &L, const DevModel &M, const Work &W, R *A, int64_t sA, int 
 // Whether D^-1 is formed by the blocked recursion with tensor-core products.
 template <typename R>
 bool blocked_inverse(const DevModel &M, const Work &W) {
-  if (M.n_p % 128 || M.n_p <= INV_BASE) return false;
+  if (M.n_p % 128 || M.n_p <= inv_base<R>()) return false;
   if (sizeof(R) == 8) return M.f64_tensor && W.Zd;
   return M.sweep_g32 == INLA_INV_BLOCKED && W.Dh;
 }

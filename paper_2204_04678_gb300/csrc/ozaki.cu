@@ -21,7 +21,8 @@
 //     holds it exactly; P_4..P_7 may round, 2^-24 of terms already 2^-28
 //     below the leading one.
 //   * Combination (once per 1024 of K): P_0..P_3 as one exact 64-bit integer,
-//     P_4..P_7 summed in FP32, then five FP64 operations per output entry.
+//     P_4..P_7 summed in FP32, then three FP64 operations per output entry (the
+//     scaling by powers of two and the conversions are integer operations).
 // One CTA computes one 128 x 64 tile of C: 4 warps; thread 0 issues the TMA
 // copies (two 96 KB stages: the 8 digit slices of a 128 x 32 slab of X and a
 // 64 x 32 slab of Y, 64-byte swizzle) and the MMAs (tcgen05.mma kind::f16, BF16
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int row = i0 + 32 * warp + lane;   // TMEM lane = row of the tile
   const uint32_t lane_addr = (uint32_t)(32 * warp) << 16;
   const int32_t er = Xe[b * sXe + row];
+  const bool unit_alpha = alpha == 1.0 || alpha == -1.0, neg = unit_alpha && alpha < 0.0;
   double *crow = C + b * sC + (int64_t)row * ldc + j0;
   const double *c0row = C0 ? C0 + b * sC0 + (int64_t)row * ldc0 + j0 : nullptr;
 
@@ -277,12 +279,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int j = j0 + 16 * g + q;
+          // Three FP64 operations per entry (the FP64 pipe does 2 per clock per SM): the
+          // sign of alpha = +-1, the power of two and the float -> double conversion of F
+          // are integer operations on the bit patterns.
+          int64_t Iq = I[q];
+          float Fq = F[q];
+          if (neg) {
+            Iq = -Iq;
+            Fq = -Fq;
+          }
           // |I| < 2^51: exact through the 2^52 + 2^51 bias
-          double dv = __longlong_as_double(0x4338000000000000ll + I[q]) - 6755399441055744.0;
-          dv = fma((double)F[q], 0x1p-7, dv);
-          const int ex = er + Ye[b * sYe + j] - 33 + 1023;
-          const double scale = ex <= 0 ? 0.0 : (ex >= 2047 ? INFINITY : __longlong_as_double((int64_t)ex << 52));
-          double o = alpha * (dv * scale);
+          const double dI = __longlong_as_double(0x4338000000000000ll + Iq) - 6755399441055744.0;
+          // F 2^-7 as a double: exponent rebiased (127 -> 1023, minus 7), mantissa widened
+          const uint32_t fb = __float_as_uint(Fq);
+          const uint32_t fe = (fb >> 23) & 0xFFu;
+          const double dF = fe == 0u ? 0.0
+                                     : __longlong_as_double(((int64_t)(fb >> 31) << 63) |
+                                                            ((int64_t)(fe + 1023u - 127u - 7u) << 52) |
+                                                            ((int64_t)(fb & 0x7FFFFFu) << 29));
+          double v = dI + dF;
+          if (!unit_alpha) v *= alpha;
+          const int k = er + Ye[b * sYe + j] - 33;   // C = 2^k (I + 2^-7 F)
+          const int64_t vb = __double_as_longlong(v);
+          const int ve = (int)((vb >> 52) & 0x7FF);
+          double o;
+          if (ve == 0) o = 0.0;
+          else if (ve + k > 0 && ve + k < 2047) o = __longlong_as_double(vb + ((int64_t)k << 52));
+          else o = ldexp(v, k);
           if (first) {
             if (c0row) o = fma(beta, c0row[16 * g + q], o);
           } else {
