@@ -107,7 +107,7 @@ enum { INLA_FP64 = 0, INLA_MIXED = 1 };
 #define INLA_SWEEP_TF32X3 3
 /* FP32 blocks (inla_set_tiles): D_t^-1 by the 2 x 2 block recursion whose
  * products run on the tensor cores in 3xTF32 (TMA-fed, as the selected
- * inversion's), with 64-wide sweeps only on the 128 x 128 base blocks; used where
+ * inversion's), with 64-wide sweeps only on base blocks of at most 256 rows; used where
  * n_s rounded up to 64 is a multiple of 128 (elsewhere the 64-wide CUDA-core
  * sweep runs).  The default for FP32 blocks of 2048 rows or more. */
 #define INLA_INV_BLOCKED 4

@@ -264,13 +264,56 @@ __device__ void sweep_tile_scalar(R *sm, R *Pout, double *logdet, int *status) {
   }
 }
 
-// FP64: the element-by-element sweep (one FMA per lower entry per step, the
-// fewest FP64 instructions: the two-level form does ~3x as many FP64 FMAs and
-// measured slower on the 128 x 128 base blocks); FP32: the two-level sweep
+// 32 x 32 FP64 pivot block swept by one warp with the block in registers (lane j
+// holds column j, all 32 rows): the pivot and its column reach every lane by
+// shuffles, so a step has no block barrier.  Each step updates the full column
+// (twice the FMAs of the lower-triangle sweep), but the pivot inversion sits on the
+// critical path of every sweep step of the small base blocks, where the three block
+// barriers and the serial division per step of the element-by-element sweep cost
+// ~40 us per pivot.  The other warps of the block do nothing here.
+template <typename R, int G>
+__device__ void sweep_tile_warp(R *sm, R *Pout, double *logdet, int *status) {
+  static_assert(G == 32, "one column per lane");
+  using S = Sweep<G>;
+  if (threadIdx.x >= 32) return;
+  const int j = threadIdx.x;
+  R a[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) a[i] = (i >= j) ? sm[i * S::LD + j] : sm[j * S::LD + i];
+  double lsum = 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < G; ++p) {
+    const R piv = __shfl_sync(0xffffffffu, a[p], p);
+    const bool ok = (piv > R(0)) && (piv < R(INFINITY));
+    if (!ok) bad = true;
+    const R inv = ok ? R(1) / piv : R(0);
+    lsum += log(ok ? (double)piv : 1.0);
+    const R cj = a[p];   // entry (j, p) = (p, j) of the current state
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const R ci = __shfl_sync(0xffffffffu, a[i], p);   // entry (i, p)
+      if (i == p) a[i] = (j == p) ? -inv : cj * inv;
+      else if (j == p) a[i] = ci * inv;
+      else a[i] = fma(-ci * inv, cj, a[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < G; ++i) Pout[i * G + j] = -a[i];
+  if (j == 0) {
+    *logdet += lsum;
+    if (bad) *status = INLA_ERR_NOT_SPD;
+  }
+}
+
+// FP64: 32 x 32 pivots by one warp in registers; wider FP64 pivots by the
+// element-by-element sweep (one FMA per lower entry per step; the two-level form
+// does ~3x as many FP64 FMAs and measured slower); FP32: the two-level sweep
 // (12 block barriers instead of 192).
 template <typename R, int G>
 __device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
-  if (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
+  if constexpr (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
+  else if constexpr (G == 32) sweep_tile_warp<R, G>(sm, Pout, logdet, status);
   else sweep_tile_scalar<R, G>(sm, Pout, logdet, status);
 }
 
@@ -925,18 +968,19 @@ void gj_invert_sub(Launch &L, const DevModel &M, const Work &W, R *A, int64_t st
 // (the block LDL^T of Sec. 2.4 applied inside one block).  Every product is an
 // X Y^T of row-major operands on the tensor cores: FP64 blocks through BF16
 // digit slices (ozaki.cu), FP32 blocks through the 3xTF32 split product
-// (tc_gemm.cu).  Diagonal blocks of up to 256 (FP64) or 128 (FP32) rows are inverted by the block sweep
+// (tc_gemm.cu).  Diagonal blocks of up to 256 rows are inverted by the block sweep
 // (their pivots give the log-determinant and the positive-definiteness test).
 // The four products per level cost (n/2)^3 (1 + 1/2 + 1 + 1/2) multiply-adds,
 // n^3 flops over the recursion, as the sweep.  Scratch: W.S, W.SigN, W.SigC
 // (free during a factorisation) for Wt, its transpose and the transpose of the
 // new A21; two operand buffers: digit slices W.Zd/Ed and W.Zs/Es (FP64), TF32
 // hi / lo parts W.Dh/Dl and W.Sh/Sl (FP32).
-// Diagonal blocks at most this size are inverted by the sweep: FP64 256 (the
-// sweep's launches on 128 x 128 blocks are latency-bound; 256 measured 6% faster per
-// step at n_s = 1024), FP32 128.
+// Diagonal blocks of at most this size are inverted by the sweep: the sweep's
+// launches on 128 x 128 blocks are latency-bound, and 256 measured faster per step
+// in both precisions (FP64 at n_s = 1024: 206 against 217 ms; FP32 at n_s = 2500:
+// 2.58 against 2.72 s).
 template <typename R>
-constexpr int inv_base() { return sizeof(R) == 8 ? 256 : 128; }
+constexpr int inv_base() { return 256; }
 
 template <typename R>
 __global__ void transpose_kernel(const R *__restrict__ src, int64_t lds, int64_t ss, R *__restrict__ dst,
