@@ -264,56 +264,13 @@ __device__ void sweep_tile_scalar(R *sm, R *Pout, double *logdet, int *status) {
   }
 }
 
-// 32 x 32 FP64 pivot block swept by one warp with the block in registers (lane j
-// holds column j, all 32 rows): the pivot and its column reach every lane by
-// shuffles, so a step has no block barrier.  Each step updates the full column
-// (twice the FMAs of the lower-triangle sweep), but the pivot inversion sits on the
-// critical path of every sweep step of the small base blocks, where the three block
-// barriers and the serial division per step of the element-by-element sweep cost
-// ~40 us per pivot.  The other warps of the block do nothing here.
-template <typename R, int G>
-__device__ void sweep_tile_warp(R *sm, R *Pout, double *logdet, int *status) {
-  static_assert(G == 32, "one column per lane");
-  using S = Sweep<G>;
-  if (threadIdx.x >= 32) return;
-  const int j = threadIdx.x;
-  R a[G];
-#pragma unroll
-  for (int i = 0; i < G; ++i) a[i] = (i >= j) ? sm[i * S::LD + j] : sm[j * S::LD + i];
-  double lsum = 0.0;
-  bool bad = false;
-#pragma unroll
-  for (int p = 0; p < G; ++p) {
-    const R piv = __shfl_sync(0xffffffffu, a[p], p);
-    const bool ok = (piv > R(0)) && (piv < R(INFINITY));
-    if (!ok) bad = true;
-    const R inv = ok ? R(1) / piv : R(0);
-    lsum += log(ok ? (double)piv : 1.0);
-    const R cj = a[p];   // entry (j, p) = (p, j) of the current state
-#pragma unroll
-    for (int i = 0; i < G; ++i) {
-      const R ci = __shfl_sync(0xffffffffu, a[i], p);   // entry (i, p)
-      if (i == p) a[i] = (j == p) ? -inv : cj * inv;
-      else if (j == p) a[i] = ci * inv;
-      else a[i] = fma(-ci * inv, cj, a[i]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < G; ++i) Pout[i * G + j] = -a[i];
-  if (j == 0) {
-    *logdet += lsum;
-    if (bad) *status = INLA_ERR_NOT_SPD;
-  }
-}
-
-// FP64: 32 x 32 pivots by one warp in registers; wider FP64 pivots by the
-// element-by-element sweep (one FMA per lower entry per step; the two-level form
-// does ~3x as many FP64 FMAs and measured slower); FP32: the two-level sweep
+// FP64: the element-by-element sweep (one FMA per lower entry per step, the
+// fewest FP64 instructions: the two-level form does ~3x as many FP64 FMAs and
+// measured slower on the 128 x 128 base blocks); FP32: the two-level sweep
 // (12 block barriers instead of 192).
 template <typename R, int G>
 __device__ void sweep_tile(R *sm, R *Pout, double *logdet, int *status) {
-  if constexpr (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
-  else if constexpr (G == 32) sweep_tile_warp<R, G>(sm, Pout, logdet, status);
+  if (sizeof(R) == 4) sweep_tile_blocked<R, G>(sm, Pout, logdet, status);
   else sweep_tile_scalar<R, G>(sm, Pout, logdet, status);
 }
 

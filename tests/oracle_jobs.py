@@ -20,7 +20,7 @@ def shortened(cfg, n_t):
     return c
 
 
-CASES = {"c2": dict(CONFIGS[2]), "c3s": shortened(3, 10), "c4s": shortened(4, 6), "c5s": shortened(5, 2)}
+CASES = {"c2": dict(CONFIGS[2]), "c3s": shortened(3, 20), "c4s": shortened(4, 12), "c5s": shortened(5, 2)}
 
 
 def model(key):

@@ -7,7 +7,7 @@ against the oracle (not against the GPU's FP64 path).  The larger models are
 run at full mesh, n_b and likelihood with fewer time steps (the oracle's dense
 per-block factorisations of 2025 x 2025 to 4096 x 4096 blocks take tens of
 seconds per time step on the host, times the Newton iterations for Poisson
-data): 45 x 45 with n_t = 10, 50 x 50 with n_t = 6 and 64 x 64 Poisson with
+data): 45 x 45 with n_t = 20, 50 x 50 with n_t = 12 and 64 x 64 Poisson with
 n_t = 2, observations per time step as in the full workloads.  The oracle jobs run in a spawn process pool started before the
 first GPU call of this module, in parallel with the GPU work.
 """
