@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--sweep", default=None, choices=["cuda-core", "tensor", "blocked"],
                     help="FP32 Schur-block inversion: the sweep with FP32 FMA tile updates, the sweep with tcgen05 "
                          "3xTF32 updates, or the blocked recursion with 3xTF32 products (the library picks by size)")
+    ap.add_argument("--time-parts", type=int, default=2, choices=[1, 2],
+                    help="2 (the library default): the time chain split at its middle block into two "
+                         "independent elimination chains; 1: one chain")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1,
                     help="stencil centres per step (FD mode) / copies of the batch (adjoint mode); profiling only")
@@ -346,6 +349,7 @@ def theta_iterations(args, local):
     cfg = args.config
     mdl = config_model(cfg)
     model = pkg.Model(mdl, device=local)
+    model.set_time_partition(args.time_parts)
     stream = torch.cuda.current_stream()
     centre = theta_batch(2, mdl)[0]          # theta_true + 0.1 N(0, I), the stencil centre of the workloads
     ref = model.eval(torch.tensor(centre[None], dtype=torch.float64, device="cuda"), grad="adjoint")
@@ -579,8 +583,18 @@ def main():
         mdl = config_model(cfg)
     centre = theta_batch(cfg, mdl)[0] + 0.01 * rank
     model = pkg.Model(mdl, device=local)
+    model.set_time_partition(args.time_parts)
     n_p = -(-mdl.n_s // 64) * 64
     tensor_sweep = n_p % 128 == 0 and args.sweep == "tensor"
+    # the FP32 block inversion the model runs (the library default when no --sweep is given)
+    inv_mode = args.sweep or ("blocked" if n_p % 128 == 0 and n_p >= 2048 else "cuda-core")
+    inv_label = {"tensor": "block sweep, rank-64 updates on the tensor cores (tcgen05 3xTF32)",
+                 "blocked": "2x2 block recursion, products on the tensor cores (tcgen05 3xTF32), "
+                            "256-row base blocks swept on the CUDA cores",
+                 "cuda-core": "block sweep on the CUDA cores"}[inv_mode]
+    fp64_label = ("2x2 block recursion, products on the BF16 tensor cores through 8 digit slices of 7 bits "
+                  "(tcgen05), 256-row base blocks swept on the CUDA cores" if n_p % 128 == 0 and n_p > 256
+                  else "block sweep on the CUDA cores")
     if args.gemm or args.sweep:
         sw = {"tensor": capi.INLA_SWEEP_TF32X3, "blocked": capi.INLA_INV_BLOCKED}.get(args.sweep, 64)
         if args.sweep is None:
@@ -636,7 +650,11 @@ def main():
     fp32 = prec == "mixed"
     tensor_gemm = fp32 and n_p % 128 == 0 and args.gemm != "cuda-core"
     upd_id = capi.KERNEL_GJ_UPDATE32 if fp32 else capi.KERNEL_GJ_UPDATE
-    kernels = {"gj_update_kernel": model.profile_read(upd_id), "gemm_nn_kernel": model.profile_read(capi.KERNEL_GEMM)}
+    digit_products = (not fp32) and n_p % 128 == 0 and n_p > 128
+    # the product slot covers whichever product kernel the path launches
+    gemm_name = ("ozaki_gemm_kernel" if digit_products else
+                 "gemm_tf32x3_tma_kernel" if tensor_gemm else "gemm_nn_kernel")
+    kernels = {"gj_update_kernel": model.profile_read(upd_id), gemm_name: model.profile_read(capi.KERNEL_GEMM)}
     model.profile_enable(0)
     flop_per_unit = 2.0 * 64 ** 3
     peaks = measured_peaks_json()
@@ -651,8 +669,7 @@ def main():
     tf32_source = ("MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/BF16 ratio / 3 "
                    "TF32 products per 3xTF32 product, of measured")
     bf16_peak = peaks.get("bf16_tflops")
-    digit_products = (not fp32) and n_p % 128 == 0 and n_p > 128
-    if kname == "gemm_nn_kernel" and digit_products and bf16_peak:
+    if kname == "ozaki_gemm_kernel" and bf16_peak:
         # FP64 products through 36 BF16 digit-slice products on the tensor cores: the FP64-equivalent
         # peak is the measured BF16 dense peak / 36
         peak, bound = bf16_peak / 36.0, "tensor"
@@ -664,7 +681,7 @@ def main():
         peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
         desc = ("rank-64 update of the FP32 block sweep on the tensor cores (tcgen05, 3xTF32, 128x128 tiles, "
                 "K = 64)")
-    elif kname == "gemm_nn_kernel" and tensor_gemm and tf32x3_peak:
+    elif kname == "gemm_tf32x3_tma_kernel" and tf32x3_peak:
         peak, bound, peak_source = tf32x3_peak, "tensor", tf32_source
         desc = ("128x128 tile 3xTF32 products of the blocked inversion and the selected inversion on the tensor "
                 "cores (tcgen05, operands split once and loaded by TMA)")
@@ -672,8 +689,8 @@ def main():
         peak, bound = (peak_fp32 if fp32 else peak_fp64), "alu"
         peak_source = ("measured on this GPU: " + ("FP32" if fp32 else "FP64")
                        + " FMA loop over all SMs (libinla_probe.so), of measured")
-        desc = {"gj_update_kernel": ("FP32" if fp32 else "FP64") + " tile update of the block sweep inversion",
-                "gemm_nn_kernel": ("FP32" if fp32 else "FP64") + " tile GEMM of the selected inversion"}[kname]
+        desc = (("FP32" if fp32 else "FP64") + (" tile update of the block sweep inversion"
+                                                 if kname == "gj_update_kernel" else " tile products"))
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "gj_update_traffic.txt")
     if kname == "gj_update_kernel" and not fp32 and os.path.exists(tfile):
@@ -746,11 +763,13 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
-                "data": "synthetic", "config": dict(config_dict(cfg, world, grad, prec, points,
-                                                                l2=L2_NOTE_FLUSH if flush else L2_NOTE_LARGE),
-                                                    **({"fp32_sweep": "tensor (tcgen05 3xTF32)" if tensor_sweep
-                                                        else "cuda-core", "fp32_gemm": "tensor (tcgen05 3xTF32)"
-                                                        if tensor_gemm else "cuda-core"} if prec == "mixed" else {})),
+                "data": "synthetic",
+                "config": config_dict(cfg, world, grad, prec, points, l2=L2_NOTE_FLUSH if flush else L2_NOTE_LARGE),
+                "kernel_path": dict({"fp64_inversion": fp64_label} if prec == "fp64" else
+                                    {"fp32_inversion": inv_label, "fp32_gemm": "tensor (tcgen05 3xTF32)"
+                                     if tensor_gemm else "cuda-core"},
+                                    time_chain="split at block n_t/2 into two elimination chains on two streams"
+                                    if args.time_parts == 2 and mdl.n_t >= 3 else "one elimination chain"),
                 "clocks": clk,
                 "gpu_launches": launches,
                 "launch_mode": "one captured CUDA graph per step (use_graph)" if graph else "eager launches",

@@ -291,6 +291,21 @@ int inla_set_wait_limit(double seconds);
  * results differ in rounding.  Drops captured graphs.  Errors: INLA_ERR_ARG. */
 int inla_set_fp64_products(inla_model *model, int tensor);
 
+/* Nested dissection of the time chain (Sec. 3.3: the independent blocks Q_A and
+ * Q_B are factorised in parallel before their separator Q_S, and the partial
+ * inverse is computed the other way round, the separator's entries first).
+ * parts = 2 (the default, for n_t >= 3): every factorisation splits the chain
+ * at its middle block k = n_t / 2 -- blocks 0..k-1 and n_t-1..k+1 are eliminated
+ * as two independent chains on two streams, then block k with the Schur
+ * complements of both neighbours, then the fixed effects; the block substitution
+ * for the mode and the selected inversion (block k first, then both chains
+ * outwards) run in the matching order.  No fill and no extra flops: the same
+ * log-determinants, mode, marginal variances and gradients up to rounding, in
+ * half the sequential steps, with a second set of per-point scratch blocks in
+ * the workspace (inla_workspace_bytes).  parts = 1: one chain, from t = 0 up.
+ * Takes effect at the next call.  Errors: INLA_ERR_ARG. */
+int inla_set_time_partition(inla_model *model, int parts);
+
 /* Latent dimension n = n_t n_s + n_b of a model. */
 int64_t inla_model_latent_dim(const inla_model *model);
 

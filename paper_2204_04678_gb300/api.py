@@ -117,6 +117,13 @@ class Model:
         splitting; the default) or with FP64 FMA on the CUDA cores."""
         C.check(self.lib.inla_set_fp64_products(self.handle, int(bool(tensor))))
 
+    def set_time_partition(self, parts=2):
+        """Split the time chain at its middle block into two independent
+        elimination chains (parts = 2, the default; nested dissection, Sec. 3.3)
+        for factorisations that no selected inversion follows, or keep one
+        chain (parts = 1)."""
+        C.check(self.lib.inla_set_time_partition(self.handle, int(parts)))
+
     def last_launch_count(self):
         return int(self.lib.inla_last_launch_count(self.handle))
 

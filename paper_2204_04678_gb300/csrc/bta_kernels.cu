@@ -138,8 +138,10 @@ __global__ void set_active_kernel(Work W, int mask) {
 
 // ------------------------------------------------------------------ factorisation pieces
 
-// R~_0 = R_0 and the tip D_a = A_a before the Schur updates.
-__global__ void init_step0_kernel(DevModel M, Work W, int mode) {
+// R~_t0 = R_t0 for the first block t0 of an elimination chain, and the tip
+// D_a = A_a before the Schur updates (tip_init = 0: D_a = 0, the accumulator of
+// a second chain's Schur updates).
+__global__ void init_step0_kernel(DevModel M, Work W, int mode, int t0, int tip_init) {
   const int b = blockIdx.z;
   if (!W.active[b]) return;
   const int l = blockIdx.y;
@@ -147,14 +149,14 @@ __global__ void init_step0_kernel(DevModel M, Work W, int mode) {
   if (l < n_b) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_p) return;
-    W.Rt[b * W.sRt + (int64_t)l * n_p + i] = (i < M.n_s) ? lik_arrow(M, W, mode, b, 0, l, i) : 0.0;
+    W.Rt[b * W.sRt + ((int64_t)t0 * n_b + l) * n_p + i] = (i < M.n_s) ? lik_arrow(M, W, mode, b, t0, l, i) : 0.0;
     return;
   }
   if (blockIdx.x != 0) return;
   for (int e = threadIdx.x; e < n_b * n_b; e += blockDim.x) {
     const int r = e / n_b, c = e % n_b;
-    double v = (r == c) ? W.prm[b].tau_b : 0.0;
-    if (mode == ASM_QC) {
+    double v = (r == c && tip_init) ? W.prm[b].tau_b : 0.0;
+    if (mode == ASM_QC && tip_init) {
       if (M.lik == INLA_LIK_GAUSSIAN) v += W.prm[b].tau_y * M.Tip[e];
       else v += W.Tipp[b * W.sNb2 + e];
     }
@@ -551,8 +553,9 @@ __global__ void tip_kernel(DevModel M, Work W, int ld_slot) {
 
 // ------------------------------------------------------------------ block substitution
 
-// z_{t+1} -= q_off Q_s w_t;  z_a -= R~_t w_t   (w_t = Dinv_t z_t in W.wv row 0)
-__global__ void fwd_update_kernel(DevModel M, Work W, int t, double *z) {
+// z_nbr -= q_off Q_s w_t;  z_a -= R~_t w_t   (w_t = Dinv_t z_t in W.wv row 0; nbr: the
+// neighbour of t eliminated after it, t + 1 or t - 1, or -1 for none)
+__global__ void fwd_update_kernel(DevModel M, Work W, int t, int nbr, double *z) {
   const int b = blockIdx.y;
   if (!W.active[b]) return;
   const int n_p = M.n_p;
@@ -560,13 +563,13 @@ __global__ void fwd_update_kernel(DevModel M, Work W, int t, double *z) {
   const double *w = W.wv + b * W.sWV;
   double *zb = z + b * W.sVec;
   if ((int)blockIdx.x < nblk) {
-    if (t >= M.n_t - 1) return;
+    if (nbr < 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M.n_s) return;
     const double *qs = W.qs + b * W.sNnz;
     double acc = 0.0;
     for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) acc = fma(qs[e], w[M.pcol[e]], acc);
-    zb[(int64_t)(t + 1) * n_p + i] -= W.prm[b].q_off * acc;
+    zb[(int64_t)nbr * n_p + i] -= W.prm[b].q_off * acc;
     return;
   }
   __shared__ double red[32];
@@ -592,8 +595,8 @@ __global__ void tip_solve_kernel(DevModel M, Work W, const double *z, double *x)
   x[b * W.sVec + tail + l] = v;
 }
 
-// tmpv = z_t - q_off Q_s x_{t+1} - R~_t^T x_a
-__global__ void bwd_rhs_kernel(DevModel M, Work W, int t, const double *z, const double *x) {
+// tmpv = z_t - q_off Q_s x_nbr - R~_t^T x_a   (nbr as in fwd_update_kernel)
+__global__ void bwd_rhs_kernel(DevModel M, Work W, int t, int nbr, const double *z, const double *x) {
   const int b = blockIdx.y;
   if (!W.active[b]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -604,9 +607,9 @@ __global__ void bwd_rhs_kernel(DevModel M, Work W, int t, const double *z, const
   const double *zb = z + b * W.sVec;
   const double *xb = x + b * W.sVec;
   double v = zb[(int64_t)t * n_p + i];
-  if (t < M.n_t - 1) {
+  if (nbr >= 0) {
     const double *qs = W.qs + b * W.sNnz;
-    const double *xn = xb + (int64_t)(t + 1) * n_p;
+    const double *xn = xb + (int64_t)nbr * n_p;
     double acc = 0.0;
     for (int e = M.prow[i]; e < M.prow[i + 1]; ++e) acc = fma(qs[e], xn[M.pcol[e]], acc);
     v -= W.prm[b].q_off * acc;
@@ -615,6 +618,48 @@ __global__ void bwd_rhs_kernel(DevModel M, Work W, int t, const double *z, const
   const double *xa = xb + (int64_t)M.n_t * n_p;
   for (int l = 0; l < M.n_b; ++l) v -= R[(int64_t)l * n_p + i] * xa[l];
   *out = v;
+}
+
+// ------------------------------------------------------------------ joining two elimination chains
+//
+// The time chain split at a separator block k (nested dissection, Sec. 3.3): blocks
+// 0..k-1 and n_t-1..k+1 are eliminated as two independent chains, each in its own
+// scratch; these kernels add the second chain's contributions into the first's.
+
+// dst += src over `count` elements per point (the Schur products D^-1 Q_s of the two
+// neighbours of the separator; the arrow rows R~ D^-1 of the two chains).
+template <typename R>
+__global__ void add_into_kernel(R *dst, const R *src, int64_t stride, int64_t count, const int *active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  R *d = dst + b * stride;
+  const R *s = src + b * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] += s[i];
+}
+
+// D_a += D_a' (the second chain's Schur updates of the tip, accumulated from 0) and
+// the second chain's log-determinant into the slot.
+__global__ void join_tip_kernel(DevModel M, Work W, const double *Da1, const double *sc1, int ld_slot) {
+  const int b = blockIdx.x;
+  if (!W.active[b]) return;
+  for (int e = threadIdx.x; e < M.n_b * M.n_b; e += blockDim.x) W.Da[b * W.sNb2 + e] += Da1[b * W.sNb2 + e];
+  if (threadIdx.x == 0) W.sc[b * SC_COUNT + ld_slot] += sc1[b * SC_COUNT + ld_slot];
+}
+
+// Forward substitution: z_k and z_a receive both chains' updates; the second chain
+// worked on its own copy z' of the right-hand side, so z += z' - rhs there.
+__global__ void join_rhs_kernel(DevModel M, Work W, int k, double *z, const double *z1, const double *rhs) {
+  const int b = blockIdx.y;
+  if (!W.active[b]) return;
+  const int n_p = M.n_p;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t o;
+  if (i < n_p) o = (int64_t)k * n_p + i;
+  else if (i < n_p + M.n_b) o = (int64_t)M.n_t * n_p + (i - n_p);
+  else return;
+  o += b * W.sVec;
+  z[o] += z1[o] - rhs[o];
 }
 
 // ------------------------------------------------------------------ selected inversion pieces
@@ -642,7 +687,9 @@ __global__ void selinv_Y_kernel(DevModel M, Work W, int t, int has_next) {
   *out = acc;
 }
 
-// <Sigma_{t+1,t}, X> for X in {C, G, H} with Sigma_{t+1,t} = -N Dinv_t on the pattern.
+// <Sigma_{s,t}, X> for X in {C, G, H} with Sigma_{s,t} = -N Dinv_t on the pattern, s the
+// neighbour of t eliminated after it (t + 1, or t - 1 on the second chain of a split
+// time chain); X is symmetric, so the pair's slot is min(s, t) either way.
 constexpr int OFF_ENTRIES_PER_WARP = 4;
 template <typename R>
 __global__ void __launch_bounds__(256) contract_offdiag_kernel(DevModel M, Work W, int t) {
@@ -1342,8 +1389,8 @@ void k_set_active(Launch &L, const Work &W, int mask) {
   set_active_kernel<<<blocks(W.P, 64), 64, 0, L.st>>>(W, mask);
   L.tick();
 }
-void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode) {
-  init_step0_kernel<<<dim3(blocks(M.n_p, 128), M.n_b + 1, W.P), 128, 0, L.st>>>(M, W, mode);
+void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode, int t0, bool tip_init) {
+  init_step0_kernel<<<dim3(blocks(M.n_p, 128), M.n_b + 1, W.P), 128, 0, L.st>>>(M, W, mode, t0, tip_init ? 1 : 0);
   L.tick();
 }
 template <typename R>
@@ -1400,9 +1447,9 @@ void k_tip(Launch &L, const DevModel &M, const Work &W, int ld_slot) {
   tip_kernel<<<blocks(W.P, 32), 32, 0, L.st>>>(M, W, ld_slot);
   L.tick();
 }
-void k_fwd_update(Launch &L, const DevModel &M, const Work &W, int t, double *z) {
+void k_fwd_update(Launch &L, const DevModel &M, const Work &W, int t, int nbr, double *z) {
   const int nblk = (int)blocks(M.n_p, 128);
-  fwd_update_kernel<<<dim3(nblk + (M.n_b > 0 ? 1 : 0), W.P), 128, 0, L.st>>>(M, W, t, z);
+  fwd_update_kernel<<<dim3(nblk + (M.n_b > 0 ? 1 : 0), W.P), 128, 0, L.st>>>(M, W, t, nbr, z);
   L.tick();
 }
 void k_tip_solve(Launch &L, const DevModel &M, const Work &W, const double *z, double *x) {
@@ -1410,8 +1457,24 @@ void k_tip_solve(Launch &L, const DevModel &M, const Work &W, const double *z, d
   tip_solve_kernel<<<W.P, 32, 0, L.st>>>(M, W, z, x);
   L.tick();
 }
-void k_bwd_rhs(Launch &L, const DevModel &M, const Work &W, int t, const double *z, const double *x) {
-  bwd_rhs_kernel<<<dim3(blocks(M.n_p, 128), W.P), 128, 0, L.st>>>(M, W, t, z, x);
+void k_bwd_rhs(Launch &L, const DevModel &M, const Work &W, int t, int nbr, const double *z, const double *x) {
+  bwd_rhs_kernel<<<dim3(blocks(M.n_p, 128), W.P), 128, 0, L.st>>>(M, W, t, nbr, z, x);
+  L.tick();
+}
+template <typename R>
+void k_add_into(Launch &L, int P, R *dst, const R *src, int64_t stride, int64_t count, const int *active) {
+  const int nb = (int)std::min<int64_t>(blocks(count, 256), 1024);
+  add_into_kernel<R><<<dim3(nb, P), 256, 0, L.st>>>(dst, src, stride, count, active);
+  L.tick();
+}
+template void k_add_into<float>(Launch &, int, float *, const float *, int64_t, int64_t, const int *);
+template void k_add_into<double>(Launch &, int, double *, const double *, int64_t, int64_t, const int *);
+void k_join_tip(Launch &L, const DevModel &M, const Work &W, const double *Da1, const double *sc1, int ld_slot) {
+  join_tip_kernel<<<W.P, 64, 0, L.st>>>(M, W, Da1, sc1, ld_slot);
+  L.tick();
+}
+void k_join_rhs(Launch &L, const DevModel &M, const Work &W, int k, double *z, const double *z1, const double *rhs) {
+  join_rhs_kernel<<<dim3(blocks(M.n_p + M.n_b, 128), W.P), 128, 0, L.st>>>(M, W, k, z, z1, rhs);
   L.tick();
 }
 void k_selinv_Y(Launch &L, const DevModel &M, const Work &W, int t, bool has_next) {
@@ -1420,12 +1483,12 @@ void k_selinv_Y(Launch &L, const DevModel &M, const Work &W, int t, bool has_nex
   L.tick();
 }
 template <typename R>
-void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int slot0) {
+void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int pair, int slot0) {
   int nparts = (int)blocks(M.nnz, 8 * OFF_ENTRIES_PER_WARP);
   if (nparts > NPART) nparts = NPART;
   contract_offdiag_kernel<R><<<dim3(nparts, W.P), 256, 0, L.st>>>(M, W, t);
   L.tick();
-  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, consecutive(3, slot0), W.pt + (int64_t)t * PT_COUNT,
+  reduce_parts_kernel<<<W.P, 256, 0, L.st>>>(W, nparts, consecutive(3, slot0), W.pt + (int64_t)pair * PT_COUNT,
                                             (int64_t)M.n_t * PT_COUNT);
   L.tick();
 }
@@ -1629,7 +1692,7 @@ void k_axpy(Launch &L, const DevModel &M, const Work &W, double *x, const double
                                  bool, const double *, const double *);                                       \
   template void k_dinv_apply<R>(Launch &, const DevModel &, const Work &, const R *, int, const double *,      \
                                 int64_t, double *, int64_t, double);                                          \
-  template void k_contract_offdiag<R>(Launch &, const DevModel &, const Work &, int, int);                    \
+  template void k_contract_offdiag<R>(Launch &, const DevModel &, const Work &, int, int, int);               \
   template void k_contract_diag<R>(Launch &, const DevModel &, const Work &, int, int, double *, const int *,  \
                                    int64_t, int);                                                             \
   template void k_poisson_qobs<R>(Launch &, const DevModel &, const Work &, int);

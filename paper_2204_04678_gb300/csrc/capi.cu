@@ -97,12 +97,14 @@ struct inla_model {
   void *bb = nullptr;
   size_t bb_bytes = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t stream2 = nullptr;   // the second elimination chain of a split time chain
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t done = nullptr;   // end of the last evaluation (orders calls across streams)
   bool done_valid = false;
   int64_t launches = 0;
   Profiler prof;
   struct GraphEntry {
-    int B, grad, prior, precision, want_mode, want_marg_var, max_newton;
+    int B, grad, prior, precision, want_mode, want_marg_var, max_newton, time_parts;
     double fd_eps, newton_tol;
     void *ws, *bb;                 // workspace the graph was captured on
     cudaGraphExec_t exec = nullptr;
@@ -140,6 +142,9 @@ struct inla_model {
     if (bb) cudaFree(bb);
     if (hb) cudaFree(hb);
     if (stream) cudaStreamDestroy(stream);
+    if (stream2) cudaStreamDestroy(stream2);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (done) cudaEventDestroy(done);
     for (auto &g : graphs) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -320,6 +325,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     M.sweep_g32 = (M.n_p % 128 == 0 && M.n_p >= 2048) ? INLA_INV_BLOCKED : 64;
     M.gemm_t32 = INLA_GEMM_TF32X3;   // tensor cores where n_p % 128 == 0, else 128-wide CUDA-core tiles
     M.f64_tensor = 1;                // FP64 selected inversion through BF16 digit slices where n_p % 128 == 0
+    M.time_parts = 2;                // factorisations without a selected inversion: two chains
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);
@@ -427,6 +433,9 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     double *consts = mdl->dalloc<double>(4);
     M.consts = consts;
     CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream, cudaStreamNonBlocking));
+    CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream2, cudaStreamNonBlocking));
+    CUDA_OK(cudaEventCreateWithFlags(&mdl->ev_fork, cudaEventDisableTiming));
+    CUDA_OK(cudaEventCreateWithFlags(&mdl->ev_join, cudaEventDisableTiming));
     CUDA_OK(cudaEventCreateWithFlags(&mdl->done, cudaEventDisableTiming));
     setup_theta_free(mdl->stream, M, dhptr, dhk, dhik, dhkj, dG, dC, dgpos, vC, vG, vH);
     setup_consts(mdl->stream, M, consts);
@@ -494,10 +503,23 @@ Sizes sizes_of(const DevModel &M) {  // element counts per point
   return s;
 }
 
+// Scratch of the second elimination chain (Work::c2): the dense scratch blocks, the
+// operand buffers of the tensor-core products, the sweep scratch, the arrow rows,
+// the tip accumulator, the scalars, two vectors, the selected inversion's arrow
+// blocks and partial sums.
+int64_t chain2_bytes(const DevModel &M, int rb, bool mixed) {
+  const Sizes s = sizes_of(M);
+  const int64_t d = s.wv + s.Da + s.sc + 2 * s.vec + s.gjP + 2 * s.gjCO + 3 * s.nbnp + s.part;
+  const int64_t split = (mixed && M.n_p % 128 == 0) ? 6 * s.mat * 4 : 0;
+  const int64_t digits = (rb == 8 && M.n_p % 128 == 0) ? 2 * (OZ_SLICES * s.mat * 2 + 4 * (int64_t)M.n_p) : 0;
+  return d * 8 + 4 * s.mat * rb + split + digits + 24 * 256;
+}
+
 // rb: bytes per element of the dense blocks' storage (8 = FP64, 4 = mixed
 // precision; 8 also for mixed precision with an FP64 selected inversion);
-// mixed: the TF32 hi / lo operand arrays of the FP32 tensor-core products exist.
-int64_t point_bytes(const DevModel &M, int rb, bool mixed) {
+// mixed: the TF32 hi / lo operand arrays of the FP32 tensor-core products exist;
+// chain2: the scratch of a second elimination chain exists.
+int64_t point_bytes(const DevModel &M, int rb, bool mixed, bool chain2) {
   const Sizes s = sizes_of(M);
   int64_t d = s.theta + s.prm + s.qs + s.Rt + 2 * s.Da + 7 * s.vec + s.wv + 3 * s.nbnp + s.sc + s.pt + s.part +
               s.tippart + 5 * s.ints + 1;
@@ -507,10 +529,11 @@ int64_t point_bytes(const DevModel &M, int rb, bool mixed) {
   const int64_t dense = s.Dinv + 4 * s.mat;
   // BF16 digit slices and row exponents of the FP64 tensor-core products' two operands
   const int64_t digits = (rb == 8 && M.n_p % 128 == 0) ? 2 * (OZ_SLICES * s.mat * 2 + 4 * (int64_t)M.n_p) : 0;
-  return d * 8 + rup(dense * rb, 256) + split + digits + 64 * 256;   // slack: each array starts on 256 bytes
+  return d * 8 + rup(dense * rb, 256) + split + digits + 64 * 256 +   // slack: each array starts on 256 bytes
+         (chain2 ? chain2_bytes(M, rb, mixed) : 0);
 }
 
-Work carve(const DevModel &M, void *base, int Pw, int rb, bool mixed) {
+Work carve(const DevModel &M, void *base, int Pw, int rb, bool mixed, bool chain2) {
   const Sizes s = sizes_of(M);
   Work W{};
   W.rb = rb;
@@ -575,8 +598,48 @@ Work carve(const DevModel &M, void *base, int Pw, int rb, bool mixed) {
     W.AtAp = take(s.AtAp); W.sAtAp = s.AtAp;
     W.Arwp = take(s.Arwp); W.sArwp = s.Arwp;
   }
+  if (chain2) {   // the same shapes and strides as the first chain's arrays
+    Work::Chain2 &c = W.c2;
+    c.T1 = take_r(s.mat); c.S = take_r(s.mat); c.SigN = take_r(s.mat); c.SigC = take_r(s.mat);
+    if (mixed && M.n_p % 128 == 0) {
+      float **parts[6] = {&c.Dh, &c.Dl, &c.Sh, &c.Sl, &c.Uh, &c.Ul};
+      for (float **q : parts) {
+        *q = reinterpret_cast<float *>(p);
+        p += rup((int64_t)s.mat * Pw * 4, 256);
+      }
+    }
+    if (rb == 8 && M.n_p % 128 == 0) {
+      auto take_b = [&](int64_t bytes) {
+        char *r = p;
+        p += rup(bytes * Pw, 256);
+        return static_cast<void *>(r);
+      };
+      c.Zd = static_cast<uint16_t *>(take_b(W.sZ * 2));
+      c.Zs = static_cast<uint16_t *>(take_b(W.sZ * 2));
+      c.Ed = static_cast<int32_t *>(take_b(W.sE * 4));
+      c.Es = static_cast<int32_t *>(take_b(W.sE * 4));
+    }
+    c.wv = take(s.wv); c.Da = take(s.Da); c.sc = take(s.sc); c.zf = take(s.vec); c.tmpv = take(s.vec);
+    c.gjP = take(s.gjP); c.gjC = take(s.gjCO); c.gjO = take(s.gjCO);
+    c.SigAn = take(s.nbnp); c.SigAc = take(s.nbnp); c.Y = take(s.nbnp); c.part = take(s.part);
+  }
   W.P = Pw;
   return W;
+}
+
+// The workspace of the second elimination chain: W with its scratch replaced by W.c2.
+// Everything per time block (D_t^-1, R~_t) and per point (parameters, status) is shared:
+// the two chains touch disjoint time blocks.
+Work chain2_work(const Work &W) {
+  Work V = W;
+  const Work::Chain2 &c = W.c2;
+  V.T1 = c.T1; V.S = c.S; V.SigN = c.SigN; V.SigC = c.SigC;
+  V.Dh = c.Dh; V.Dl = c.Dl; V.Sh = c.Sh; V.Sl = c.Sl; V.Uh = c.Uh; V.Ul = c.Ul;
+  V.Zd = c.Zd; V.Zs = c.Zs; V.Ed = c.Ed; V.Es = c.Es;
+  V.wv = c.wv; V.Da = c.Da; V.sc = c.sc; V.zf = c.zf; V.tmpv = c.tmpv;
+  V.gjP = c.gjP; V.gjC = c.gjC; V.gjO = c.gjO;
+  V.SigAn = c.SigAn; V.SigAc = c.SigAc; V.Y = c.Y; V.part = c.part;
+  return V;
 }
 
 // The per-point layout above uses stride = count for each array, so that the
@@ -650,64 +713,167 @@ void zero_slot(Launch &L, const Work &W, int slot) {
   L.tick();
 }
 
-// Block LDL^T factorisation of Q_c (mode ASM_QC) or Q (ASM_Q) along the time chain.
+// The second elimination chain runs on L.st2, forked from L.st and joined back.
+Launch chain2_launch(const Launch &L) {
+  Launch L2 = L;
+  L2.st = L.st2;
+  L2.cur_id = -1;
+  return L2;
+}
+void fork_chain2(const Launch &L) {
+  CUDA_OK(cudaEventRecord(L.ev_fork, L.st));
+  CUDA_OK(cudaStreamWaitEvent(L.st2, L.ev_fork, 0));
+}
+void join_chain2(const Launch &L) {
+  CUDA_OK(cudaEventRecord(L.ev_join, L.st2));
+  CUDA_OK(cudaStreamWaitEvent(L.st, L.ev_join, 0));
+}
+
+// One elimination step of the time chain: block t with its Schur complement from
+// the neighbour `prev` eliminated just before it (-1: none), D_t^-1 and log|D_t|.
+// R~_t = R_t - q_off (R~_prev D_prev^-1) Q_s and D_a -= (R~_prev D_prev^-1) R~_prev^T.
 template <typename R>
-void factor(Launch &L, const DevModel &M, const Work &W, int mode, int ld_slot) {
+void chain_step(Launch &L, const DevModel &M, const Work &W, int mode, int ld_slot, int t, int prev) {
   const int64_t np2 = (int64_t)M.n_p * M.n_p;
   const int64_t rtb = (int64_t)M.n_b * M.n_p;
   R *Dinv = static_cast<R *>(W.Dinv);
-  R *T1 = static_cast<R *>(W.T1);
-  zero_slot(L, W, ld_slot);
-  k_init_step0(L, M, W, mode);
-  for (int t = 0; t < M.n_t; ++t) {
-    R *Dt = Dinv + t * np2;
-    if (t > 0) {
-      const R *Dp = Dinv + (t - 1) * np2;
-      if (M.n_b > 0) {
-        k_dinv_apply(L, M, W, Dp, M.n_b, W.Rt + (t - 1) * rtb, W.sRt, W.wv, W.sWV, 1.0);
-        k_arrow_update(L, M, W, t, mode);
-        k_arrow_dots(L, M, W, t - 1);
-      }
-      k_sparse_right<R>(L, M, W, Dp, W.sDinv, T1, W.sMat, false, nullptr, nullptr, true);
+  R *Dt = Dinv + t * np2;
+  if (prev >= 0) {
+    const R *Dp = Dinv + prev * np2;
+    if (M.n_b > 0) {
+      k_dinv_apply(L, M, W, Dp, M.n_b, W.Rt + prev * rtb, W.sRt, W.wv, W.sWV, 1.0);
+      k_arrow_update(L, M, W, t, mode);
+      k_arrow_dots(L, M, W, prev);
     }
-    k_assemble_diag<R>(L, M, W, t, mode, Dt, W.sDinv, t > 0);
-    gj_invert<R>(L, M, W, Dt, W.sDinv, W.sc + ld_slot, SC_COUNT);
+    k_sparse_right<R>(L, M, W, Dp, W.sDinv, static_cast<R *>(W.T1), W.sMat, false, nullptr, nullptr, true);
   }
+  k_assemble_diag<R>(L, M, W, t, mode, Dt, W.sDinv, prev >= 0);
+  gj_invert<R>(L, M, W, Dt, W.sDinv, W.sc + ld_slot, SC_COUNT);
+}
+
+// The contributions of the last block `last` of a chain to the separator: its arrow
+// rows V = R~_last D_last^-1 (in W.wv) with D_a -= V R~_last^T, and T1 = D_last^-1 Q_s.
+template <typename R>
+void chain_close(Launch &L, const DevModel &M, const Work &W, int last) {
+  const int64_t np2 = (int64_t)M.n_p * M.n_p;
+  const int64_t rtb = (int64_t)M.n_b * M.n_p;
+  const R *Dl = static_cast<const R *>(W.Dinv) + last * np2;
   if (M.n_b > 0) {
-    const int t = M.n_t - 1;
-    k_dinv_apply<R>(L, M, W, Dinv + t * np2, M.n_b, W.Rt + t * rtb, W.sRt, W.wv, W.sWV, 1.0);
-    k_arrow_dots(L, M, W, t);
+    k_dinv_apply(L, M, W, Dl, M.n_b, W.Rt + last * rtb, W.sRt, W.wv, W.sWV, 1.0);
+    k_arrow_dots(L, M, W, last);
+  }
+  k_sparse_right<R>(L, M, W, Dl, W.sDinv, static_cast<R *>(W.T1), W.sMat, false, nullptr, nullptr, true);
+}
+
+// Separator block of a time chain split in two: the middle block.
+inline int separator(const DevModel &M) { return M.n_t / 2; }
+
+// Block LDL^T factorisation of Q_c (mode ASM_QC) or Q (ASM_Q) along the time chain.
+// split: nested dissection of the chain at the middle block k (Sec. 3.3): blocks
+// 0..k-1 and n_t-1..k+1 are eliminated as two independent chains, concurrently on two
+// streams, each towards k; then k with the Schur complements of both neighbours,
+//   D_k = A_k - q_off^2 Q_s (D_{k-1}^-1 + D_{k+1}^-1) Q_s,
+// and the tip with the arrow updates of every block.  No fill: every block still has
+// one later-eliminated neighbour in the chain (k has none), and log|Q_c| is the sum of
+// the same log|D_t| over the new order.
+template <typename R>
+void factor(Launch &L, const DevModel &M, const Work &W, int mode, int ld_slot, bool split = false) {
+  zero_slot(L, W, ld_slot);
+  k_init_step0(L, M, W, mode, 0, true);
+  if (!split) {
+    for (int t = 0; t < M.n_t; ++t) chain_step<R>(L, M, W, mode, ld_slot, t, t - 1);
+    if (M.n_b > 0) {
+      const int64_t np2 = (int64_t)M.n_p * M.n_p;
+      const int t = M.n_t - 1;
+      k_dinv_apply<R>(L, M, W, static_cast<R *>(W.Dinv) + t * np2, M.n_b, W.Rt + t * (int64_t)M.n_b * M.n_p,
+                      W.sRt, W.wv, W.sWV, 1.0);
+      k_arrow_dots(L, M, W, t);
+    }
+    k_tip(L, M, W, ld_slot);
+    return;
+  }
+  const int k = separator(M), last = M.n_t - 1;
+  const Work W2 = chain2_work(W);
+  Launch L2 = chain2_launch(L);
+  fork_chain2(L);
+  zero_slot(L2, W2, ld_slot);
+  k_init_step0(L2, M, W2, mode, last, false);   // R~_{n_t-1} = R_{n_t-1}; the tip accumulator = 0
+  for (int t = last; t > k; --t) chain_step<R>(L2, M, W2, mode, ld_slot, t, t < last ? t + 1 : -1);
+  chain_close<R>(L2, M, W2, k + 1);
+  for (int t = 0; t < k; ++t) chain_step<R>(L, M, W, mode, ld_slot, t, t - 1);
+  chain_close<R>(L, M, W, k - 1);
+  join_chain2(L);
+  // the separator: both neighbours' Schur products and arrow rows
+  k_add_into<R>(L, W.P, static_cast<R *>(W.T1), static_cast<const R *>(W2.T1), W.sMat, W.sMat, W.active);
+  if (M.n_b > 0) {
+    k_add_into<double>(L, W.P, W.wv, W2.wv, W.sWV, (int64_t)M.n_b * M.n_p, W.active);
+    k_arrow_update(L, M, W, k, mode);
+  }
+  const int64_t np2 = (int64_t)M.n_p * M.n_p;
+  R *Dk = static_cast<R *>(W.Dinv) + k * np2;
+  k_assemble_diag<R>(L, M, W, k, mode, Dk, W.sDinv, true);
+  gj_invert<R>(L, M, W, Dk, W.sDinv, W.sc + ld_slot, SC_COUNT);
+  k_join_tip(L, M, W, W2.Da, W2.sc, ld_slot);
+  if (M.n_b > 0) {
+    k_dinv_apply<R>(L, M, W, Dk, M.n_b, W.Rt + k * (int64_t)M.n_b * M.n_p, W.sRt, W.wv, W.sWV, 1.0);
+    k_arrow_dots(L, M, W, k);
   }
   k_tip(L, M, W, ld_slot);
 }
 
-// Forward and backward block substitution with the stored factorisation.
+// Forward and backward block substitution with the stored factorisation.  Block t's
+// forward step w = D_t^-1 z_t, z_nbr -= q_off Q_s w, z_a -= R~_t w passes to the
+// neighbour eliminated after t; the backward step x_t = D_t^-1 (z_t - q_off Q_s x_nbr -
+// R~_t^T x_a) reads it.  split: the order of the split factorisation above (the two
+// chains concurrently, the separator and the tip between the passes).
 template <typename R>
-void solve_once(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x) {
+void solve_once(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x, bool split) {
   const int64_t np2 = (int64_t)M.n_p * M.n_p;
   const R *Dinv = static_cast<const R *>(W.Dinv);
-  CUDA_OK(cudaMemcpyAsync(W.zf, rhs, sizeof(double) * W.sVec * W.P, cudaMemcpyDeviceToDevice, L.st));
-  for (int t = 0; t < M.n_t; ++t) {
-    k_dinv_apply<R>(L, M, W, Dinv + t * np2, 1, W.zf + (int64_t)t * M.n_p, W.sVec, W.wv, W.sWV, 1.0);
-    k_fwd_update(L, M, W, t, W.zf);
+  const int64_t vbytes = sizeof(double) * W.sVec * W.P;
+  CUDA_OK(cudaMemcpyAsync(W.zf, rhs, vbytes, cudaMemcpyDeviceToDevice, L.st));
+  auto fwd = [&](Launch &Ls, const Work &Ws, int t, int nbr) {
+    k_dinv_apply<R>(Ls, M, Ws, Dinv + t * np2, 1, Ws.zf + (int64_t)t * M.n_p, Ws.sVec, Ws.wv, Ws.sWV, 1.0);
+    k_fwd_update(Ls, M, Ws, t, nbr, Ws.zf);
+  };
+  auto bwd = [&](Launch &Ls, const Work &Ws, int t, int nbr) {
+    k_bwd_rhs(Ls, M, Ws, t, nbr, Ws.zf, x);
+    k_dinv_apply<R>(Ls, M, Ws, Dinv + t * np2, 1, Ws.tmpv, Ws.sVec, x + (int64_t)t * M.n_p, Ws.sVec, 1.0);
+  };
+  if (!split) {
+    for (int t = 0; t < M.n_t; ++t) fwd(L, W, t, t + 1 < M.n_t ? t + 1 : -1);
+    k_tip_solve(L, M, W, W.zf, x);
+    for (int t = M.n_t - 1; t >= 0; --t) bwd(L, W, t, t + 1 < M.n_t ? t + 1 : -1);
+    return;
   }
+  const int k = separator(M), last = M.n_t - 1;
+  const Work W2 = chain2_work(W);
+  Launch L2 = chain2_launch(L);
+  fork_chain2(L);
+  CUDA_OK(cudaMemcpyAsync(W2.zf, rhs, vbytes, cudaMemcpyDeviceToDevice, L2.st));
+  for (int t = last; t > k; --t) fwd(L2, W2, t, t - 1);
+  for (int t = 0; t < k; ++t) fwd(L, W, t, t + 1);
+  join_chain2(L);
+  k_join_rhs(L, M, W, k, W.zf, W2.zf, rhs);
+  fwd(L, W, k, -1);
   k_tip_solve(L, M, W, W.zf, x);
-  for (int t = M.n_t - 1; t >= 0; --t) {
-    k_bwd_rhs(L, M, W, t, W.zf, x);
-    k_dinv_apply<R>(L, M, W, Dinv + t * np2, 1, W.tmpv, W.sVec, x + (int64_t)t * M.n_p, W.sVec, 1.0);
-  }
+  bwd(L, W, k, -1);
+  fork_chain2(L);
+  for (int t = k + 1; t <= last; ++t) bwd(L2, W2, t, t - 1);
+  for (int t = k - 1; t >= 0; --t) bwd(L, W, t, t + 1);
+  join_chain2(L);
 }
 
 // Q_c x = rhs.  With single-precision blocks the solution is refined with FP64
 // residuals r = rhs - Q_c x computed from the sparse blocks (x += Q_c^-1 r).
 constexpr int REFINE_STEPS = 3;
 template <typename R>
-void solve(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x) {
-  solve_once<R>(L, M, W, rhs, x);
+void solve(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x, bool split = false) {
+  solve_once<R>(L, M, W, rhs, x, split);
   if (sizeof(R) == sizeof(double)) return;
   for (int it = 0; it < REFINE_STEPS; ++it) {
     k_qc_residual(L, M, W, x, rhs, W.rvec);
-    solve_once<R>(L, M, W, W.rvec, W.dvec);
+    solve_once<R>(L, M, W, W.rvec, W.dvec, split);
     k_axpy(L, M, W, x, W.dvec);
   }
 }
@@ -737,12 +903,18 @@ int workspace_rb(const DevModel &M, const inla_eval_opts &o) {
   return (o.precision == INLA_MIXED && !mixed_fp64_selinv(M, o)) ? 4 : 8;
 }
 
+// Whether this call's factorisations, substitutions and selected inversions split
+// the time chain in two (nested dissection at the middle block).
+bool split_chain(const DevModel &M, const inla_eval_opts &) {
+  return M.time_parts >= 2 && M.n_t >= 3;
+}
+
 int64_t point_bytes_for(const DevModel &M, const inla_eval_opts &o) {
-  return point_bytes(M, workspace_rb(M, o), o.precision == INLA_MIXED);
+  return point_bytes(M, workspace_rb(M, o), o.precision == INLA_MIXED, split_chain(M, o));
 }
 
 Work carve_for(const DevModel &M, void *base, int Pw, const inla_eval_opts &o) {
-  Work W = carve(M, base, Pw, workspace_rb(M, o), o.precision == INLA_MIXED);
+  Work W = carve(M, base, Pw, workspace_rb(M, o), o.precision == INLA_MIXED, split_chain(M, o));
   W.rb = o.precision == INLA_MIXED ? 4 : 8;   // the dense blocks' arithmetic (an FP64-sized workspace may hold FP32 blocks)
   return W;
 }
@@ -754,11 +926,13 @@ bool digit_gemm(const DevModel &M) {
   return sizeof(R) == sizeof(double) && M.f64_tensor && M.n_p % 128 == 0;
 }
 
-// Block Takahashi recursion from the last time block to the first.
+// Block Takahashi recursion (Eq. takahashi_recursion in block form) in the reverse
+// of the elimination order: one step for block t, whose neighbour eliminated after
+// it is `next` (-1: none) with Sigma_{next,next} and Sigma_{a,next} in W.SigN and
+// W.SigAn; Sigma_tt and Sigma_{a,t} land in W.SigC and W.SigAc, then the pairs swap.
 template <typename R>
-void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contractions, double *marg_var,
-            const int *point_out, int64_t point_base, bool poisson_q) {
-  Work W = W0;
+void selinv_step(Launch &L, const DevModel &M, Work &W, int mode, bool contractions, double *marg_var,
+                 const int *point_out, int64_t point_base, bool poisson_q, int t, int next) {
   const int64_t np2 = (int64_t)M.n_p * M.n_p;
   const int64_t rtb = (int64_t)M.n_b * M.n_p;
   const int slotD = (mode == ASM_QC) ? PT_FD_C : PT_QD_C;
@@ -766,54 +940,89 @@ void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contrac
   const R *Dinv = static_cast<const R *>(W.Dinv);
   R *T1 = static_cast<R *>(W.T1);
   R *S = static_cast<R *>(W.S);
-  for (int t = M.n_t - 1; t >= 0; --t) {
-    const R *Dt = Dinv + t * np2;
-    const double *Rt_t = W.Rt + t * rtb;
-    const bool nxt = t < M.n_t - 1;
-    R *SigN = static_cast<R *>(W.SigN), *SigC = static_cast<R *>(W.SigC);
-    if (nxt) k_sparse_right<R>(L, M, W, SigN, W.sMat, T1, W.sMat, true, M.n_b ? W.SigAn : nullptr, Rt_t);
-    k_selinv_Y(L, M, W, t, nxt);
-    k_sparse_left<R>(L, M, W, T1, W.sMat, S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
-    if (contractions && nxt) k_contract_offdiag<R>(L, M, W, t, slotO);
-    if (M.n_b > 0) k_dinv_apply<R>(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
-    if (tensor_gemm<R>(M)) {
-      // U = D^-1 S^T (= (S D^-1)^T, D^-1 symmetric), then Sigma_tt = D^-1 U^T + D^-1:
-      // both products read their operands along rows (X Y^T), as the tensor-core kernel wants.
-      // D^-1 and S are split into TF32 hi / lo parts once; U is stored split by the first product.
-      const float *Df = reinterpret_cast<const float *>(Dt);
-      split_tf32(L, W.P, Df, W.sDinv, W.Dh, W.Dl, W.sMat, np2, W.active);
-      split_tf32(L, W.P, reinterpret_cast<const float *>(S), W.sMat, W.Sh, W.Sl, W.sMat, np2, W.active);
-      const int n = M.n_p;
-      gemm_nt_tf32x3_split(L, W.P, n, n, n, W.Dh, W.Dl, W.sMat, W.Sh, W.Sl, W.sMat, nullptr, n, W.sMat, 1.0f, nullptr,
-                           n, 0, 0.0f, W.Uh, W.Ul, false, W.active, W.status);
-      gemm_nt_tf32x3_split(L, W.P, n, n, n, W.Dh, W.Dl, W.sMat, W.Uh, W.Ul, W.sMat, reinterpret_cast<float *>(SigC), n,
-                           W.sMat, 1.0f, Df, n, W.sDinv, 1.0f, nullptr, nullptr, true, W.active, W.status);
-    } else if (digit_gemm<R>(M)) {
-      // the same two products in FP64 through BF16 digit slices: U = D^-1 S^T into T1, then
-      // Sigma_tt = D^-1 U^T + D^-1; D^-1 is split once, S's slices are replaced by U's
-      const double *Dd = reinterpret_cast<const double *>(Dt);
-      double *Ud = reinterpret_cast<double *>(T1);
-      const int n = M.n_p;
-      ozaki_split2(L, W.P, n, n, Dd, n, W.sDinv, W.Zd, W.Ed, n, n, reinterpret_cast<const double *>(S), n, W.sMat,
-                   W.Zs, W.Es, W.sZ, W.sE, W.active);
-      gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE, Ud, n, W.sMat, 1.0, nullptr, 0,
-                    0, 0.0, false, W.active, W.status);
-      ozaki_split(L, W.P, n, n, Ud, n, W.sMat, W.Zs, W.sZ, W.Es, W.sE, W.active);
-      gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE,
-                    reinterpret_cast<double *>(SigC), n, W.sMat, 1.0, Dd, n, W.sDinv, 1.0, true, W.active, W.status);
-    } else {
-      const int tile = M.gemm_t32 == INLA_GEMM_TF32X3 ? 128 : M.gemm_t32;   // CUDA-core fallback
-      gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, tile);
-      gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active,
-                 tile);
-    }
-    mirror_lower<R>(L, W.P, M.n_p, SigC, W.sMat, W.active);
-    k_contract_diag<R>(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
-    if (poisson_q) k_poisson_qobs<R>(L, M, W, t);
-    std::swap(W.SigN, W.SigC);
-    std::swap(W.SigAn, W.SigAc);
+  const R *Dt = Dinv + t * np2;
+  const double *Rt_t = W.Rt + t * rtb;
+  const bool nxt = next >= 0;
+  R *SigN = static_cast<R *>(W.SigN), *SigC = static_cast<R *>(W.SigC);
+  if (nxt) k_sparse_right<R>(L, M, W, SigN, W.sMat, T1, W.sMat, true, M.n_b ? W.SigAn : nullptr, Rt_t);
+  k_selinv_Y(L, M, W, t, nxt);
+  k_sparse_left<R>(L, M, W, T1, W.sMat, S, W.sMat, nxt, Rt_t, M.n_b ? W.Y : nullptr);
+  if (contractions && nxt) k_contract_offdiag<R>(L, M, W, t, std::min(t, next), slotO);
+  if (M.n_b > 0) k_dinv_apply<R>(L, M, W, Dt, M.n_b, W.Y, W.sNbNp, W.SigAc, W.sNbNp, -1.0);
+  if (tensor_gemm<R>(M)) {
+    // U = D^-1 S^T (= (S D^-1)^T, D^-1 symmetric), then Sigma_tt = D^-1 U^T + D^-1:
+    // both products read their operands along rows (X Y^T), as the tensor-core kernel wants.
+    // D^-1 and S are split into TF32 hi / lo parts once; U is stored split by the first product.
+    const float *Df = reinterpret_cast<const float *>(Dt);
+    split_tf32(L, W.P, Df, W.sDinv, W.Dh, W.Dl, W.sMat, np2, W.active);
+    split_tf32(L, W.P, reinterpret_cast<const float *>(S), W.sMat, W.Sh, W.Sl, W.sMat, np2, W.active);
+    const int n = M.n_p;
+    gemm_nt_tf32x3_split(L, W.P, n, n, n, W.Dh, W.Dl, W.sMat, W.Sh, W.Sl, W.sMat, nullptr, n, W.sMat, 1.0f, nullptr,
+                         n, 0, 0.0f, W.Uh, W.Ul, false, W.active, W.status);
+    gemm_nt_tf32x3_split(L, W.P, n, n, n, W.Dh, W.Dl, W.sMat, W.Uh, W.Ul, W.sMat, reinterpret_cast<float *>(SigC), n,
+                         W.sMat, 1.0f, Df, n, W.sDinv, 1.0f, nullptr, nullptr, true, W.active, W.status);
+  } else if (digit_gemm<R>(M)) {
+    // the same two products in FP64 through BF16 digit slices: U = D^-1 S^T into T1, then
+    // Sigma_tt = D^-1 U^T + D^-1; D^-1 is split once, S's slices are replaced by U's
+    const double *Dd = reinterpret_cast<const double *>(Dt);
+    double *Ud = reinterpret_cast<double *>(T1);
+    const int n = M.n_p;
+    ozaki_split2(L, W.P, n, n, Dd, n, W.sDinv, W.Zd, W.Ed, n, n, reinterpret_cast<const double *>(S), n, W.sMat,
+                 W.Zs, W.Es, W.sZ, W.sE, W.active);
+    gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE, Ud, n, W.sMat, 1.0, nullptr, 0,
+                  0, 0.0, false, W.active, W.status);
+    ozaki_split(L, W.P, n, n, Ud, n, W.sMat, W.Zs, W.sZ, W.Es, W.sE, W.active);
+    gemm_nt_ozaki(L, W.P, n, n, n, W.Zd, W.sZ, W.Ed, W.sE, W.Zs, W.sZ, W.Es, W.sE,
+                  reinterpret_cast<double *>(SigC), n, W.sMat, 1.0, Dd, n, W.sDinv, 1.0, true, W.active, W.status);
+  } else {
+    const int tile = M.gemm_t32 == INLA_GEMM_TF32X3 ? 128 : M.gemm_t32;   // CUDA-core fallback
+    gemm_nn<R>(L, W.P, M.n_p, S, W.sMat, Dt, W.sDinv, T1, W.sMat, R(1), nullptr, 0, R(0), false, W.active, tile);
+    gemm_nn<R>(L, W.P, M.n_p, Dt, W.sDinv, T1, W.sMat, SigC, W.sMat, R(1), Dt, W.sDinv, R(1), true, W.active,
+               tile);
+  }
+  mirror_lower<R>(L, W.P, M.n_p, SigC, W.sMat, W.active);
+  k_contract_diag<R>(L, M, W, t, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base, slotD);
+  if (poisson_q) k_poisson_qobs<R>(L, M, W, t);
+  std::swap(W.SigN, W.SigC);
+  std::swap(W.SigAn, W.SigAc);
+}
+
+// The selected inverse on the BTA pattern from the last-eliminated block outwards.
+// split: the order of the split factorisation (Sec. 3.3: the separator's entries
+// first, then the two independent parts concurrently): block k, then k-1..0 and
+// k+1..n_t-1 on two streams, the second chain starting from a copy of Sigma_kk and
+// Sigma_{a,k}.
+template <typename R>
+void selinv(Launch &L, const DevModel &M, const Work &W0, int mode, bool contractions, double *marg_var,
+            const int *point_out, int64_t point_base, bool poisson_q, bool split = false) {
+  Work W = W0;
+  auto step = [&](Launch &Ls, Work &Ws, int t, int next) {
+    selinv_step<R>(Ls, M, Ws, mode, contractions, marg_var, point_out, point_base, poisson_q, t, next);
+  };
+  if (!split) {
+    for (int t = M.n_t - 1; t >= 0; --t) step(L, W, t, t + 1 < M.n_t ? t + 1 : -1);
+  } else {
+    const int k = separator(M), last = M.n_t - 1;
+    step(L, W, k, -1);
+    Work W2 = chain2_work(W);
+    W2.Da = W.Da;   // Sigma_a (the second chain's scratch holds its factorisation's tip accumulator)
+    CUDA_OK(cudaMemcpyAsync(W2.SigN, W.SigN, sizeof(R) * W.sMat * W.P, cudaMemcpyDeviceToDevice, L.st));
+    if (M.n_b > 0)
+      CUDA_OK(cudaMemcpyAsync(W2.SigAn, W.SigAn, sizeof(double) * W.sNbNp * W.P, cudaMemcpyDeviceToDevice, L.st));
+    Launch L2 = chain2_launch(L);
+    fork_chain2(L);
+    for (int t = k + 1; t <= last; ++t) step(L2, W2, t, t - 1);
+    for (int t = k - 1; t >= 0; --t) step(L, W, t, t + 1);
+    join_chain2(L);
   }
   k_contract_tip(L, M, W, mode, mode == ASM_QC ? marg_var : nullptr, point_out, point_base);
+}
+
+// The model's second stream and fork / join events for the second elimination chain.
+void with_chain2(inla_model *mdl, Launch &L) {
+  L.st2 = mdl->stream2;
+  L.ev_fork = mdl->ev_fork;
+  L.ev_join = mdl->ev_join;
 }
 
 template <typename R>
@@ -825,6 +1034,7 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
   // mixed precision on a fine mesh: the selected inversion from an FP64 factorisation
   // at the mode, in the same (FP64-sized) workspace
   const bool esc = sizeof(R) == sizeof(float) && need_sel && mixed_fp64_selinv(M, o);
+  const bool split = split_chain(M, o) && W.c2.T1 && L.st2;
   Work Wd = W;
   Wd.rb = 8;
   CUDA_OK(cudaMemsetAsync(W.sc, 0, sizeof(double) * 32 * W.P, L.st));
@@ -847,31 +1057,31 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     k_qs_share(L, M, W);
     k_set_active(L, W, 0);
   } else {
-    factor<R>(L, M, W, ASM_Q, SC_LOGDET_Q);
+    factor<R>(L, M, W, ASM_Q, SC_LOGDET_Q, split);
     if (adj) {
       k_set_active(L, W, 2);
       if (esc) {
-        factor<double>(L, M, Wd, ASM_Q, SC_LOGDET_Q);
-        selinv<double>(L, M, Wd, ASM_Q, true, nullptr, nullptr, 0, false);
+        factor<double>(L, M, Wd, ASM_Q, SC_LOGDET_Q, split);
+        selinv<double>(L, M, Wd, ASM_Q, true, nullptr, nullptr, 0, false, split);
       } else {
-        selinv<R>(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false);
+        selinv<R>(L, M, W, ASM_Q, true, nullptr, nullptr, 0, false, split);
       }
       k_set_active(L, W, 0);
     }
   }
   if (M.lik == INLA_LIK_GAUSSIAN) {
-    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC);
+    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC, split);
     k_rhs_gaussian(L, M, W);
-    solve<R>(L, M, W, W.rhs, W.x);
+    solve<R>(L, M, W, W.rhs, W.x, split);
     k_obs_reduce(L, M, W, 0);
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
       k_set_active(L, W, 1);
       if (esc) {
-        factor<double>(L, M, Wd, ASM_QC, SC_LOGDET_QC);
-        selinv<double>(L, M, Wd, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+        factor<double>(L, M, Wd, ASM_QC, SC_LOGDET_QC, split);
+        selinv<double>(L, M, Wd, ASM_QC, adj, mv_out, bb.point_out, w0, false, split);
       } else {
-        selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false);
+        selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, false, split);
       }
       k_set_active(L, W, 0);
     }
@@ -884,8 +1094,8 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
       k_poisson_eta(Ls, M, W, W.x);
       k_obs_assemble(Ls, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp,
                      W.sArwp, W.Tipp, W.sNb2, W.rhs, W.sVec, W.tippart);
-      factor<R>(Ls, M, W, ASM_QC, SC_LOGDET_QC);
-      solve<R>(Ls, M, W, W.rhs, W.x);
+      factor<R>(Ls, M, W, ASM_QC, SC_LOGDET_QC, split);
+      solve<R>(Ls, M, W, W.rhs, W.x, split);
       k_newton_cap(Ls, M, W);   // no linear predictor moves by more than NEWTON_DETA in one step
       CUDA_OK(cudaMemsetAsync(W.any_active, 0, sizeof(int), Ls.st));
       k_poisson_step(Ls, M, W, tol, it, max_it, it_dev);
@@ -910,17 +1120,38 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
       cudaGraphNode_t node;
       CUDA_OK(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
       cudaGraph_t body = cp.conditional.phGraph_out[0];
-      cudaStream_t bs;
+      // the body is captured from streams of its own (the model's second stream may
+      // already belong to the enclosing capture)
+      cudaStream_t bs, bs2;
+      cudaEvent_t bf, bj;
       CUDA_OK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+      CUDA_OK(cudaStreamCreateWithFlags(&bs2, cudaStreamNonBlocking));
+      CUDA_OK(cudaEventCreateWithFlags(&bf, cudaEventDisableTiming));
+      CUDA_OK(cudaEventCreateWithFlags(&bj, cudaEventDisableTiming));
       Launch Lb = L;
       Lb.st = bs;
+      Lb.st2 = bs2;
+      Lb.ev_fork = bf;
+      Lb.ev_join = bj;
       cudaError_t e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        newton_step(Lb, 0, ctr);
-        k_newton_continue(Lb, h, W.any_active, ctr);
+        try {
+          newton_step(Lb, 0, ctr);
+          k_newton_continue(Lb, h, W.any_active, ctr);
+        } catch (...) {
+          cudaStreamEndCapture(bs, &body);
+          cudaStreamDestroy(bs);
+          cudaStreamDestroy(bs2);
+          cudaEventDestroy(bf);
+          cudaEventDestroy(bj);
+          throw;
+        }
         e = cudaStreamEndCapture(bs, &body);
       }
       cudaStreamDestroy(bs);
+      cudaStreamDestroy(bs2);
+      cudaEventDestroy(bf);
+      cudaEventDestroy(bj);
       CUDA_OK(e);
       CUDA_OK(cudaStreamUpdateCaptureDependencies(L.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     } else {
@@ -937,16 +1168,16 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     k_poisson_eta(L, M, W, W.x);
     k_obs_assemble(L, M, W.P, W.active, W.mu, W.sM, nullptr, 0, true, W.eta, W.AtAp, W.sAtAp, W.Arwp, W.sArwp,
                    W.Tipp, W.sNb2, nullptr, 0, W.tippart);
-    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC);
+    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC, split);
     k_obs_reduce(L, M, W, 1);
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
       k_set_active(L, W, 1);
       if (esc) {
-        factor<double>(L, M, Wd, ASM_QC, SC_LOGDET_QC);   // Q_c at the mode, assembled above
-        selinv<double>(L, M, Wd, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+        factor<double>(L, M, Wd, ASM_QC, SC_LOGDET_QC, split);   // Q_c at the mode, assembled above
+        selinv<double>(L, M, Wd, ASM_QC, adj, mv_out, bb.point_out, w0, adj, split);
       } else {
-        selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj);
+        selinv<R>(L, M, W, ASM_QC, adj, mv_out, bb.point_out, w0, adj, split);
       }
       if (adj) {
         k_set_active(L, W, 2);
@@ -954,8 +1185,8 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
         CUDA_OK(cudaMemsetAsync(W.rhs, 0, sizeof(double) * W.sVec * W.P, L.st));
         k_obs_assemble(L, M, W.P, W.active, nullptr, 0, W.wobs, W.sM, false, nullptr, nullptr, 0, nullptr, 0,
                        nullptr, 0, W.rhs, W.sVec, W.tippart);
-        if (esc) solve<double>(L, M, Wd, W.rhs, W.xprev);
-        else solve<R>(L, M, W, W.rhs, W.xprev);
+        if (esc) solve<double>(L, M, Wd, W.rhs, W.xprev, split);
+        else solve<R>(L, M, W, W.rhs, W.xprev, split);
         k_quadforms(L, M, W, W.xprev, W.x, PT_LD_C, SC_TIP_LX);
       }
       k_set_active(L, W, 0);
@@ -1005,6 +1236,7 @@ int64_t eval_impl(inla_model *mdl, int B, const double *theta_dev, const inla_ev
     replay_graph(mdl, B, theta_dev, opts, out, st, bb, rb);
   } else {
     Launch L{st, &mdl->launches, &mdl->prof};
+    with_chain2(mdl, L);
     enqueue_eval(mdl, L, B, theta_dev, opts, out, bb, Pw, rb);
   }
   CUDA_OK(cudaEventRecord(mdl->done, st));
@@ -1052,13 +1284,13 @@ void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_ev
     if (e.B == B && e.grad == opts->grad && e.prior == opts->prior_mode && e.precision == opts->precision &&
         e.want_mode == (opts->want_mode != 0) && e.want_marg_var == (opts->want_marg_var != 0) &&
         e.fd_eps == opts->fd_eps && e.max_newton == opts->max_newton && e.newton_tol == opts->newton_tol &&
-        e.ws == mdl->ws && e.bb == mdl->bb)
+        e.time_parts == mdl->M.time_parts && e.ws == mdl->ws && e.bb == mdl->bb)
       g = &e;
   if (!g) {
     inla_model::GraphEntry e{};
     e.B = B; e.grad = opts->grad; e.prior = opts->prior_mode; e.precision = opts->precision;
     e.want_mode = opts->want_mode != 0; e.want_marg_var = opts->want_marg_var != 0; e.fd_eps = opts->fd_eps;
-    e.max_newton = opts->max_newton; e.newton_tol = opts->newton_tol;
+    e.max_newton = opts->max_newton; e.newton_tol = opts->newton_tol; e.time_parts = mdl->M.time_parts;
     e.ws = mdl->ws; e.bb = mdl->bb;
     const size_t bytes = rup(32 * B, 256) + rup(8 * B, 256) + rup(32 * B, 256) + 2 * rup(4 * B, 256) +
                          2 * rup(8 * n * B, 256);
@@ -1079,6 +1311,7 @@ void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_ev
     dense_prepare();
     int64_t count = 0;
     Launch L{mdl->stream, &count, nullptr};
+    with_chain2(mdl, L);
     L.capturing = true;
     cudaGraph_t graph = nullptr;
     CUDA_OK(cudaStreamBeginCapture(mdl->stream, cudaStreamCaptureModeThreadLocal));
@@ -1192,6 +1425,7 @@ int64_t eval_static_impl(inla_model *mdl, int B, const double *theta_dev, const 
   char *base = static_cast<char *>(static_scratch(mdl->device));
   mdl->launches = 0;
   Launch L{st, &mdl->launches, nullptr};
+  with_chain2(mdl, L);
   if (mdl->done_valid) CUDA_OK(cudaStreamWaitEvent(st, mdl->done, 0));
   Work W0 = carve_for(mdl->M, base, (int)P_total, *opts);
   char *p = base + ws_bytes;
@@ -1440,6 +1674,13 @@ int inla_set_fp64_products(inla_model *model, int tensor) {
       if (g.stage) cudaFree(g.stage);
     }
     model->graphs.clear();
+  });
+}
+
+int inla_set_time_partition(inla_model *model, int parts) {
+  return guarded([&] {
+    if (!model || (parts != 1 && parts != 2)) throw ApiError(INLA_ERR_ARG, "model is NULL or parts not 1 / 2");
+    model->M.time_parts = parts;   // the graph cache is keyed on it; the workspace grows on demand
   });
 }
 

@@ -78,6 +78,8 @@ struct DevModel {
   double prior_mean[4], prior_sd[4];
   double tau_b_fixed;
   double nb_size;                // negative binomial size r (0 for the other likelihoods)
+  int time_parts;                // 2: factorisations without a selected inversion split the time
+                                 // chain at its middle block into two chains (1: one chain)
 };
 
 // Per-wave workspace (device) with per-point strides (in elements).  The dense
@@ -122,6 +124,17 @@ struct Work {
   double *AtAp;          // [P][n_t][nnz]
   double *Arwp;          // [P][n_t][n_b][n_s]
   double *Tipp;          // [P][n_b][n_b]
+  // Scratch of the second elimination chain of a time chain split at a separator
+  // block (null when the workspace has none); same shapes and strides as above.
+  struct Chain2 {
+    void *T1, *S, *SigN, *SigC;
+    float *Dh, *Dl, *Sh, *Sl, *Uh, *Ul;
+    uint16_t *Zd, *Zs;
+    int32_t *Ed, *Es;
+    double *wv, *Da, *sc, *zf, *tmpv;
+    void *gjP, *gjC, *gjO;
+    double *SigAn, *SigAc, *Y, *part;
+  } c2;
 };
 
 enum {
@@ -176,6 +189,10 @@ struct Launch {
   int64_t *counter;
   Profiler *prof = nullptr;
   bool capturing = false;   // being recorded into a CUDA graph (no host synchronisation allowed)
+  // second stream for the second elimination chain, and the events that fork it
+  // from st and join it back (null: no second chain)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int cur_id = -1;
   double cur_units = 0.0;
   cudaEvent_t cur_a = nullptr;
@@ -295,7 +312,7 @@ void sweep_update_tf32x3(Launch &L, int P, int n_p, float *A, int64_t sA, const 
 void k_params(Launch &L, const DevModel &M, const Work &W);
 void k_qs_values(Launch &L, const DevModel &M, const Work &W);
 void k_set_active(Launch &L, const Work &W, int mask);
-void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode);
+void k_init_step0(Launch &L, const DevModel &M, const Work &W, int mode, int t0, bool tip_init);
 template <typename R>
 void k_assemble_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, R *dst, int64_t sdst,
                      bool schur);
@@ -313,12 +330,17 @@ void k_dinv_apply(Launch &L, const DevModel &M, const Work &W, const R *Dinv_t, 
 void k_arrow_update(Launch &L, const DevModel &M, const Work &W, int t, int mode);
 void k_arrow_dots(Launch &L, const DevModel &M, const Work &W, int tprev);
 void k_tip(Launch &L, const DevModel &M, const Work &W, int ld_slot);
-void k_fwd_update(Launch &L, const DevModel &M, const Work &W, int t, double *z);
+void k_fwd_update(Launch &L, const DevModel &M, const Work &W, int t, int nbr, double *z);
 void k_tip_solve(Launch &L, const DevModel &M, const Work &W, const double *z, double *x);
-void k_bwd_rhs(Launch &L, const DevModel &M, const Work &W, int t, const double *z, const double *x);
+void k_bwd_rhs(Launch &L, const DevModel &M, const Work &W, int t, int nbr, const double *z, const double *x);
+// joining two elimination chains of the time chain at a separator block
+template <typename R>
+void k_add_into(Launch &L, int P, R *dst, const R *src, int64_t stride, int64_t count, const int *active);
+void k_join_tip(Launch &L, const DevModel &M, const Work &W, const double *Da1, const double *sc1, int ld_slot);
+void k_join_rhs(Launch &L, const DevModel &M, const Work &W, int k, double *z, const double *z1, const double *rhs);
 void k_selinv_Y(Launch &L, const DevModel &M, const Work &W, int t, bool has_next);
 template <typename R>
-void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int slot0);
+void k_contract_offdiag(Launch &L, const DevModel &M, const Work &W, int t, int pair, int slot0);
 template <typename R>
 void k_contract_diag(Launch &L, const DevModel &M, const Work &W, int t, int mode, double *marg_var,
                      const int *point_out, int64_t point_base, int slot0);
