@@ -345,30 +345,15 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_panel_kernel(const R *A,
   for (int e = threadIdx.x; e < G * G; e += S::THREADS) Ob[e] = Os[(e >> S::SHIFT) * S::LD + (e & (G - 1))];
 }
 
-// Rank-G update of every lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K;
-// the pivot row/column become C (resp. C^T) and the pivot block -P.  With
-// lookahead (K + 1 < nt) block 0 takes tile (K+1, K+1) and, once updated,
-// inverts it as the next pivot (slot (K+1)&1 of Pbuf), so no separate pivot
-// launch sits on the critical path.
+// Rank-G update of one lower tile (I, J): A_IJ -= C_I O_J^T for I, J != K; the
+// pivot row/column become C (resp. C^T) and the pivot block -P.  next_pivot: the
+// tile is (K+1, K+1), which is then inverted as the next pivot (slot (K+1)&1 of
+// Pbuf).  Cs / Os: the block's shared workspace.  Called by all threads of a block.
 template <typename R, int G>
-__global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int64_t sA, int n_p, int K, int nt,
-                                                                     R *Pbuf, const R *Cbuf, const R *Obuf,
-                                                                     int64_t sCO, double *logdet, int ld_stride,
-                                                                     int *status, const int *active) {
+__device__ void update_tile(R *A, int64_t sA, int n_p, int K, int I, int J, bool next_pivot, R *Pbuf,
+                            const R *Cbuf, const R *Obuf, int64_t sCO, double *logdet, int ld_stride, int *status,
+                            int b, R *Cs, R *Os) {
   using S = Sweep<G>;
-  const int b = blockIdx.x;   // points fastest: every point's lookahead tile is among the first blocks
-  if (active && !active[b]) return;
-  const bool look = K + 1 < nt;
-  int I, J;
-  if (look) {
-    const int nxt = (K + 1) * (K + 2) / 2 + (K + 1);   // linear index of tile (K+1, K+1)
-    int x = blockIdx.y;
-    if (x == 0) x = nxt;
-    else if (x <= nxt) x = x - 1;
-    tri_index(x, I, J);
-  } else {
-    tri_index(blockIdx.y, I, J);
-  }
   R *dst = A + b * sA + (int64_t)(I * G) * n_p + J * G;
   const R *Cb = Cbuf + b * sCO;
   if (I == K && J == K) {
@@ -391,10 +376,7 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
     }
     return;
   }
-  extern __shared__ __align__(16) unsigned char smraw[];
-  R *Cs = reinterpret_cast<R *>(smraw);   // [G][LD]  C_I[r][k]
-  R *Os = Cs + G * S::LD;                 // [G][LD]  O_J[c][k]
-  R *sm = Cs;                             // the fused pivot sweep's workspace
+  R *sm = Cs;   // the fused pivot sweep's workspace
   const R *ci = Cb + (int64_t)(I * G) * G;
   const R *oj = Obuf + b * sCO + (int64_t)(J * G) * G;
   for (int e = threadIdx.x; e < G * G; e += S::THREADS) {
@@ -426,8 +408,7 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
   }
-  const bool next_pivot = look && I == K + 1 && J == K + 1;
-  if (next_pivot) __syncthreads();   // Cs/Os are reused as the sweep's workspace
+  __syncthreads();   // every read of Cs / Os is done (they are rewritten next)
 #pragma unroll
   for (int i = 0; i < S::MI; ++i)
 #pragma unroll
@@ -441,6 +422,44 @@ __global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int6
     __syncthreads();
     sweep_tile<R, G>(sm, Pbuf + ((int64_t)b * 2 + ((K + 1) & 1)) * G * G, logdet + (int64_t)b * ld_stride,
                      status + b);
+  }
+}
+
+// Rank-G update of every lower tile of the block sweep at pivot K.  Grid (points,
+// blocks per point), points fastest.  With lookahead (K + 1 < nt) block 0 of each
+// point takes only tile (K+1, K+1) and, once updated, inverts it as the next pivot,
+// so no separate pivot launch sits on the critical path; the other blocks take the
+// remaining tiles in turn.  The launch sizes the blocks per point so that the whole
+// grid is about one block per SM: the lookahead block, whose serial pivot sweep sets
+// the launch length, then shares its SM's FP64 pipe with as few update blocks as
+// possible (one tile per block packed 2-3 blocks on each SM, and the lookahead
+// blocks ran at a fraction of the pipe).
+template <typename R, int G>
+__global__ void __launch_bounds__(Sweep<G>::THREADS) gj_update_kernel(R *A, int64_t sA, int n_p, int K, int nt,
+                                                                     R *Pbuf, const R *Cbuf, const R *Obuf,
+                                                                     int64_t sCO, double *logdet, int ld_stride,
+                                                                     int *status, const int *active) {
+  using S = Sweep<G>;
+  const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R *Cs = reinterpret_cast<R *>(smraw);   // [G][LD]  C_I[r][k]
+  R *Os = Cs + G * S::LD;                 // [G][LD]  O_J[c][k]
+  const bool look = K + 1 < nt;
+  const int ntri = nt * (nt + 1) / 2;
+  const int nxt = (K + 1) * (K + 2) / 2 + (K + 1);   // linear index of tile (K+1, K+1)
+  int I, J;
+  if (look && blockIdx.y == 0) {
+    tri_index(nxt, I, J);
+    update_tile<R, G>(A, sA, n_p, K, I, J, true, Pbuf, Cbuf, Obuf, sCO, logdet, ld_stride, status, b, Cs, Os);
+    return;
+  }
+  const int nrem = look ? ntri - 1 : ntri;
+  const int workers = look ? (int)gridDim.y - 1 : (int)gridDim.y;
+  for (int r = look ? (int)blockIdx.y - 1 : (int)blockIdx.y; r < nrem; r += workers) {
+    tri_index((look && r >= nxt) ? r + 1 : r, I, J);
+    update_tile<R, G>(A, sA, n_p, K, I, J, false, Pbuf, Cbuf, Obuf, sCO, logdet, ld_stride, status, b, Cs, Os);
+    __syncthreads();   // the next tile rewrites Cs / Os
   }
 }
 
@@ -826,6 +845,24 @@ void ensure_attrs() {
   done[dev] = true;
 }
 
+// Blocks per point of gj_update_kernel: about one block per SM over the grid, at
+// most MAX_TILES_PER_BLOCK tiles per update block (fine enough to balance large
+// batches), and the lookahead block on its own.
+constexpr int MAX_TILES_PER_BLOCK = 4;
+int update_blocks(int P, int ntri, bool look) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int tiles = look ? ntri - 1 : ntri;
+  int per = std::max((sms + P - 1) / P - (look ? 1 : 0), (tiles + MAX_TILES_PER_BLOCK - 1) / MAX_TILES_PER_BLOCK);
+  per = std::max(1, std::min(per, tiles));
+  return per + (look ? 1 : 0);
+}
+
 // Block sweep inversion with G x G pivots (see the kernels above) of the
 // nsub x nsub block at A (leading dimension ld; the kernels' n_p argument is
 // the leading dimension).
@@ -884,8 +921,9 @@ void gj_invert_g(Launch &L, const DevModel &M, const Work &W, R *A, int64_t stri
           reinterpret_cast<const float *>(Cb), reinterpret_cast<const float *>(Ob), sCO, logdet_out,
           logdet_slot_stride, W.status, W.active, 0);
     else
-      gj_update_kernel<R, G><<<dim3(P, ntri), S::THREADS, smem_update<R, G>(), L.st>>>(
-          A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride, W.status, W.active);
+      gj_update_kernel<R, G><<<dim3(P, update_blocks(P, ntri, K + 1 < nt)), S::THREADS, smem_update<R, G>(),
+                               L.st>>>(A, strideA, n_p, K, nt, Pb, Cb, Ob, sCO, logdet_out, logdet_slot_stride,
+                                       W.status, W.active);
     L.stop();
     L.tick();
   }
