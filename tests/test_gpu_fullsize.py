@@ -82,9 +82,6 @@ def check(r, ref, tf, tx, tv, tg, b=0):
     assert np.abs(g - ref["grad"]).max() <= tg * max(1.0, np.abs(ref["grad"]).max()), (g, ref["grad"])
 
 
-ORACLE_WAIT = 1500
-
-
 @pytest.mark.parametrize("key", ["c2", "c3s", "c4s", "c5s"])
 def test_fp64_adjoint_matches_oracle(pkg, oracle, key):
     """f, x*, all of diag(Q_c^-1) and the adjoint gradient, FP64."""
