@@ -655,6 +655,9 @@ def main():
     gemm_name = ("ozaki_gemm_kernel" if digit_products else
                  "gemm_tf32x3_tma_kernel" if tensor_gemm else "gemm_nn_kernel")
     kernels = {"gj_update_kernel": model.profile_read(upd_id), gemm_name: model.profile_read(capi.KERNEL_GEMM)}
+    # the sweep's other two launches per pivot, for their event-timed durations
+    sweep_aux = {"gj_pivot_kernel": model.profile_read(capi.KERNEL_GJ_PIVOT),
+                 "gj_panel_kernel": model.profile_read(capi.KERNEL_GJ_PANEL)}
     model.profile_enable(0)
     flop_per_unit = 2.0 * 64 ** 3
     peaks = measured_peaks_json()
@@ -780,9 +783,12 @@ def main():
                 "forms": forms,
                 "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32,
                                           "tf32x3_tensor_from_bf16_sustained": tf32x3_peak},
-                "kernels": {k: {"ms_sampled": v[0], "launches_sampled": v[1],
-                                "tflops": v[2] * flop_per_unit / (v[0] / 1e3) / 1e12 if v[0] else None}
-                            for k, v in kernels.items()}}
+                "kernels": dict({k: {"ms_sampled": v[0], "launches_sampled": v[1],
+                                     "tflops": v[2] * flop_per_unit / (v[0] / 1e3) / 1e12 if v[0] else None}
+                                 for k, v in kernels.items()},
+                                **{k: {"ms_sampled": v[0], "launches_sampled": v[1],
+                                       "us_per_launch": 1e3 * v[0] / v[1] if v[1] else None}
+                                   for k, v in sweep_aux.items()})}
         if args.nt or args.centres != 1:
             line["config"]["workload"] = f"profiling case: n_t={mdl.n_t}, {args.centres} stencil centres per step"
         print(json.dumps(line))

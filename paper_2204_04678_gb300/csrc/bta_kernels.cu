@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include <cstring>
+#include <mutex>
 
 #include "inla_internal.cuh"
 
@@ -1704,6 +1705,71 @@ void k_zero(Launch &L, double *p, int64_t n) {
   if (n <= 0) return;
   zero_kernel<<<blocks(n, 256), 256, 0, L.st>>>(p, n);
   L.tick();
+}
+
+template <typename R>
+void bta_prepare_r() {
+  prefer_shared(assemble_diag_kernel<R>);
+  prefer_shared(sparse_right_tiled_kernel<R>);
+  prefer_shared(sparse_right_kernel<R>);
+  prefer_shared(sparse_left_kernel<R>);
+  prefer_shared(dinv_gemv_kernel<R>);
+  prefer_shared(dinv_apply_kernel<R, DA_MAXV>);
+  prefer_shared(add_into_kernel<R>);
+  prefer_shared(contract_offdiag_kernel<R>);
+  prefer_shared(contract_diag_kernel<R>);
+  prefer_shared(poisson_qobs_kernel<R>);
+}
+
+void bta_prepare() {
+  static std::mutex mu;
+  static bool done[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  bta_prepare_r<double>();
+  bta_prepare_r<float>();
+  prefer_shared(params_kernel);
+  prefer_shared(qs_values_kernel);
+  prefer_shared(set_active_kernel);
+  prefer_shared(init_step0_kernel);
+  prefer_shared(arrow_update_kernel);
+  prefer_shared(arrow_dots_kernel);
+  prefer_shared(tip_kernel);
+  prefer_shared(fwd_update_kernel);
+  prefer_shared(tip_solve_kernel);
+  prefer_shared(bwd_rhs_kernel);
+  prefer_shared(join_tip_kernel);
+  prefer_shared(join_rhs_kernel);
+  prefer_shared(selinv_Y_kernel);
+  prefer_shared(reduce_parts_kernel);
+  prefer_shared(contract_tip_kernel);
+  prefer_shared(quadforms_kernel);
+  prefer_shared(rhs_gaussian_kernel);
+  prefer_shared(obs_reduce_kernel);
+  prefer_shared(qs_share_setup_kernel);
+  prefer_shared(qs_share_kernel);
+  prefer_shared(qs_traces_kernel);
+  prefer_shared(finalize_kernel);
+  prefer_shared(copy_mode_kernel);
+  prefer_shared(fd_points_kernel);
+  prefer_shared(outputs_kernel);
+  prefer_shared(poisson_eta_kernel);
+  prefer_shared(obs_assemble_pattern_kernel);
+  prefer_shared(obs_assemble_vertex_kernel);
+  prefer_shared(obs_assemble_tip_kernel);
+  prefer_shared(obs_assemble_tip_sum_kernel);
+  prefer_shared(poisson_step_kernel);
+  prefer_shared(poisson_wobs_kernel);
+  prefer_shared(qc_residual_kernel);
+  prefer_shared(qc_residual_tail_kernel);
+  prefer_shared(axpy_kernel);
+  prefer_shared(zero_kernel);
+  prefer_shared(newton_deta_kernel);
+  prefer_shared(newton_cap_kernel);
+  prefer_shared(newton_continue_kernel);
+  done[dev] = true;
 }
 
 }  // namespace inla

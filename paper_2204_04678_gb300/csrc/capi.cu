@@ -455,6 +455,10 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     // which must not happen inside inla_eval_batch_static.
     static_scratch(device);
     dense_prepare();
+    prefer_shared(point_out_kernel);
+    prefer_shared(flags_kernel);
+    prefer_shared(mask_failed_kernel);
+    prefer_shared(zero_slot_kernel);
     return mdl;
   } catch (...) {
     delete mdl;

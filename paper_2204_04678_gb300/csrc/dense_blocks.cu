@@ -28,6 +28,11 @@
 
 namespace inla {
 
+// defined with the blocked inversion below; declared here for ensure_attrs
+template <typename R>
+__global__ void transpose_kernel(const R *__restrict__ src, int64_t lds, int64_t ss, R *__restrict__ dst,
+                                 int64_t ldd, int64_t sd, int rows, int cols, const int *active);
+
 namespace {
 
 constexpr int T = TILE;     // 64
@@ -842,6 +847,22 @@ void ensure_attrs() {
   cudaFuncSetAttribute(gj_pivot_kernel<R, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pivot<R, 64>());
   if (sizeof(R) == 4)
     cudaFuncSetAttribute(gj_update_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, U32_SMEM);
+  prefer_shared(gemm_nn_kernel<R>);
+  prefer_shared(gj_pivot_kernel<R, 32>);
+  prefer_shared(gj_pivot_kernel<R, 64>);
+  prefer_shared(gj_panel_kernel<R, 32>);
+  prefer_shared(gj_panel_kernel<R, 64>);
+  prefer_shared(gj_panel_q_kernel<R, 32>);
+  prefer_shared(gj_panel_q_kernel<R, 64>);
+  prefer_shared(gj_update_kernel<R, 32>);
+  prefer_shared(gj_update_kernel<R, 64>);
+  prefer_shared(gj_finalize_kernel<R>);
+  prefer_shared(mirror_kernel<R>);
+  prefer_shared(transpose_kernel<R>);
+  if (sizeof(R) == 4) {
+    prefer_shared(gj_update_f32_kernel);
+    prefer_shared(gemm128_f32_kernel);
+  }
   done[dev] = true;
 }
 
@@ -938,6 +959,7 @@ void dense_prepare() {
   ensure_attrs<float>();
   tc_prepare();
   ozaki_prepare();
+  bta_prepare();
 }
 
 // Tile width per precision from the model (defaults: 32 for FP64, where short

@@ -360,6 +360,8 @@ void ozaki_prepare() {
   std::lock_guard<std::mutex> lock(mu);
   if (done[dev]) return;
   cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+  prefer_shared(ozaki_gemm_kernel);
+  prefer_shared(ozaki_split_kernel);
   done[dev] = true;
 }
 

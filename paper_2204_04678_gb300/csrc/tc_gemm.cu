@@ -559,6 +559,10 @@ void tc_prepare() {
   if (done[dev]) return;
   cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   cudaFuncSetAttribute(gemm_tf32x3_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_SMEM);
+  prefer_shared(gemm_tf32x3_kernel);
+  prefer_shared(gemm_tf32x3_tma_kernel);
+  prefer_shared(split_tf32_kernel);
+  prefer_shared(split_tf32_2d_kernel);
   done[dev] = true;
 }
 
