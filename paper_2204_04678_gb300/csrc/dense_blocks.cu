@@ -242,15 +242,22 @@ __device__ void sweep_tile_scalar(R *sm, R *Pout, double *logdet, int *status) {
       cinv[tid] = c * s_inv;
     }
     __syncthreads();
+    // every operand of this thread's entries is read before any entry is written (the
+    // arrays share one buffer, so reads interleaved with writes would run one entry at
+    // a time); the step's critical path is this phase's latency, not its FMAs
+    R nv[S::PER];
+    const R inv = s_inv;
 #pragma unroll
     for (int k = 0; k < S::PER; ++k) {
-      if (k >= ne) break;
-      const int i = ei[k], j = ej[k];
-      R *ap = &a[i * S::LD + j];
-      if (i == p) *ap = (j == p) ? -s_inv : cinv[j];
-      else if (j == p) *ap = cinv[i];
-      else *ap = fma(-cinv[i], colp[j], *ap);
+      if (k < ne) {
+        const int i = ei[k], j = ej[k];
+        const R ci = cinv[i], cj = cinv[j], pj = colp[j], old = a[i * S::LD + j];
+        nv[k] = (i == p) ? ((j == p) ? -inv : cj) : ((j == p) ? ci : fma(-ci, pj, old));
+      }
     }
+#pragma unroll
+    for (int k = 0; k < S::PER; ++k)
+      if (k < ne) a[ei[k] * S::LD + ej[k]] = nv[k];
     __syncthreads();
   }
   for (int e = tid; e < G * G; e += S::THREADS) {
