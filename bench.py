@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--time-parts", type=int, default=2, choices=[1, 2],
                     help="2 (the library default): the time chain split at its middle block into two "
                          "independent elimination chains; 1: one chain")
+    ap.add_argument("--point-groups", type=int, default=None, choices=[1, 2],
+                    help="the library's point groups (default: the library's own setting)")
     ap.add_argument("--nt", type=int, default=None, help="override n_t (profiling case only)")
     ap.add_argument("--centres", type=int, default=1,
                     help="stencil centres per step (FD mode) / copies of the batch (adjoint mode); profiling only")
@@ -584,6 +586,8 @@ def main():
     centre = theta_batch(cfg, mdl)[0] + 0.01 * rank
     model = pkg.Model(mdl, device=local)
     model.set_time_partition(args.time_parts)
+    if args.point_groups:
+        model.set_point_groups(args.point_groups)
     n_p = -(-mdl.n_s // 64) * 64
     tensor_sweep = n_p % 128 == 0 and args.sweep == "tensor"
     # the FP32 block inversion the model runs (the library default when no --sweep is given)

@@ -306,6 +306,18 @@ int inla_set_fp64_products(inla_model *model, int tensor);
  * Takes effect at the next call.  Errors: INLA_ERR_ARG. */
 int inla_set_time_partition(inla_model *model, int parts);
 
+/* Point groups (the paper's "level 1" parallelism over independent evaluation
+ * points, Sec. 3.1, applied inside one call).  groups = 2: for Gaussian data in
+ * calls with use_graph the factorisation of Q_c and the solve for the mode run
+ * as two groups of points (the first and second half of each wave), each on its
+ * own pair of streams, concurrently; the dense kernels of a wave are
+ * latency-bound, so two groups of half the points overlap (groups = 2 is the
+ * default; eager calls keep one group, whose launches cost half the host
+ * time).  Results are
+ * bit-identical to groups = 1: every point's arithmetic is unchanged.  Takes
+ * effect at the next call.  Errors: INLA_ERR_ARG. */
+int inla_set_point_groups(inla_model *model, int groups);
+
 /* Latent dimension n = n_t n_s + n_b of a model. */
 int64_t inla_model_latent_dim(const inla_model *model);
 

@@ -124,6 +124,11 @@ class Model:
         chain (parts = 1)."""
         C.check(self.lib.inla_set_time_partition(self.handle, int(parts)))
 
+    def set_point_groups(self, groups=2):
+        """Factorise a Gaussian call's points as two concurrent groups (groups = 2,
+        the default) or as one batch (groups = 1)."""
+        C.check(self.lib.inla_set_point_groups(self.handle, int(groups)))
+
     def last_launch_count(self):
         return int(self.lib.inla_last_launch_count(self.handle))
 

@@ -85,6 +85,7 @@ SIGNATURES = {
     "inla_set_wait_limit": (c_int, [c_double]),
     "inla_set_fp64_products": (c_int, [c_void_p, c_int]),
     "inla_set_time_partition": (c_int, [c_void_p, c_int]),
+    "inla_set_point_groups": (c_int, [c_void_p, c_int]),
     "inla_model_latent_dim": (c_int64, [c_void_p]),
     "inla_last_launch_count": (c_int64, [c_void_p]),
     "inla_model_destroy": (None, [c_void_p]),

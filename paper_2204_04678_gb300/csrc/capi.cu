@@ -99,12 +99,14 @@ struct inla_model {
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;   // the second elimination chain of a split time chain
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t stream3 = nullptr, stream4 = nullptr;   // the second point group's two chains
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr, ev_gfork = nullptr, ev_gjoin = nullptr;
   cudaEvent_t done = nullptr;   // end of the last evaluation (orders calls across streams)
   bool done_valid = false;
   int64_t launches = 0;
   Profiler prof;
   struct GraphEntry {
-    int B, grad, prior, precision, want_mode, want_marg_var, max_newton, time_parts;
+    int B, grad, prior, precision, want_mode, want_marg_var, max_newton, time_parts, point_groups;
     double fd_eps, newton_tol;
     void *ws, *bb;                 // workspace the graph was captured on
     cudaGraphExec_t exec = nullptr;
@@ -143,6 +145,10 @@ struct inla_model {
     if (hb) cudaFree(hb);
     if (stream) cudaStreamDestroy(stream);
     if (stream2) cudaStreamDestroy(stream2);
+    for (cudaStream_t q : {stream3, stream4})
+      if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : {ev_fork2, ev_join2, ev_gfork, ev_gjoin})
+      if (e) cudaEventDestroy(e);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (done) cudaEventDestroy(done);
@@ -326,6 +332,7 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     M.gemm_t32 = INLA_GEMM_TF32X3;   // tensor cores where n_p % 128 == 0, else 128-wide CUDA-core tiles
     M.f64_tensor = 1;                // FP64 selected inversion through BF16 digit slices where n_p % 128 == 0
     M.time_parts = 2;                // factorisations without a selected inversion: two chains
+    M.point_groups = 2;              // Gaussian factorisations: two concurrent point groups
     auto find = [&](int i, int j) -> int {
       auto b = pcol.begin() + prow[i], e = pcol.begin() + prow[i + 1];
       auto it = std::lower_bound(b, e, j);
@@ -434,6 +441,10 @@ inla_model *create_model(const inla_model_desc *d, int device) {
     M.consts = consts;
     CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream, cudaStreamNonBlocking));
     CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream2, cudaStreamNonBlocking));
+    CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream3, cudaStreamNonBlocking));
+    CUDA_OK(cudaStreamCreateWithFlags(&mdl->stream4, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&mdl->ev_fork2, &mdl->ev_join2, &mdl->ev_gfork, &mdl->ev_gjoin})
+      CUDA_OK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CUDA_OK(cudaEventCreateWithFlags(&mdl->ev_fork, cudaEventDisableTiming));
     CUDA_OK(cudaEventCreateWithFlags(&mdl->ev_join, cudaEventDisableTiming));
     CUDA_OK(cudaEventCreateWithFlags(&mdl->done, cudaEventDisableTiming));
@@ -526,7 +537,7 @@ int64_t chain2_bytes(const DevModel &M, int rb, bool mixed) {
 int64_t point_bytes(const DevModel &M, int rb, bool mixed, bool chain2) {
   const Sizes s = sizes_of(M);
   int64_t d = s.theta + s.prm + s.qs + s.Rt + 2 * s.Da + 7 * s.vec + s.wv + 3 * s.nbnp + s.sc + s.pt + s.part +
-              s.tippart + 5 * s.ints + 1;
+              s.tippart + 7 * s.ints + 1;
   if (M.lik != INLA_LIK_GAUSSIAN) d += 4 * s.m + s.AtAp + s.Arwp;
   d += s.gjP + 2 * s.gjCO + s.mat;   // sweep scratch (sized for double) and the FP64 Q_s^-1
   const int64_t split = (mixed && M.n_p % 128 == 0) ? 6 * s.mat * 4 : 0;   // TF32 hi / lo operands (bytes)
@@ -597,6 +608,8 @@ Work carve(const DevModel &M, void *base, int Pw, int rb, bool mixed, bool chain
   W.iters = reinterpret_cast<int *>(take(s.ints));
   W.qsrep = reinterpret_cast<int *>(take(s.ints));
   W.any_active = reinterpret_cast<int *>(take(1));
+  W.grp0 = reinterpret_cast<int *>(take(s.ints));
+  W.grp1 = reinterpret_cast<int *>(take(s.ints));
   if (M.lik != INLA_LIK_GAUSSIAN) {
     W.eta = take(s.m); W.mu = take(s.m); W.qobs = take(s.m); W.wobs = take(s.m); W.sM = s.m;
     W.AtAp = take(s.AtAp); W.sAtAp = s.AtAp;
@@ -834,8 +847,11 @@ template <typename R>
 void solve_once(Launch &L, const DevModel &M, const Work &W, const double *rhs, double *x, bool split) {
   const int64_t np2 = (int64_t)M.n_p * M.n_p;
   const R *Dinv = static_cast<const R *>(W.Dinv);
-  const int64_t vbytes = sizeof(double) * W.sVec * W.P;
-  CUDA_OK(cudaMemcpyAsync(W.zf, rhs, vbytes, cudaMemcpyDeviceToDevice, L.st));
+  // only the points of this pass: a concurrent pass of another point group owns the rest
+  const int lo = W.hi > 0 ? W.lo : 0, hi = W.hi > 0 ? W.hi : W.P;
+  const int64_t voff = (int64_t)lo * W.sVec;
+  const size_t vbytes = sizeof(double) * W.sVec * (size_t)(hi - lo);
+  CUDA_OK(cudaMemcpyAsync(W.zf + voff, rhs + voff, vbytes, cudaMemcpyDeviceToDevice, L.st));
   auto fwd = [&](Launch &Ls, const Work &Ws, int t, int nbr) {
     k_dinv_apply<R>(Ls, M, Ws, Dinv + t * np2, 1, Ws.zf + (int64_t)t * M.n_p, Ws.sVec, Ws.wv, Ws.sWV, 1.0);
     k_fwd_update(Ls, M, Ws, t, nbr, Ws.zf);
@@ -854,7 +870,7 @@ void solve_once(Launch &L, const DevModel &M, const Work &W, const double *rhs, 
   const Work W2 = chain2_work(W);
   Launch L2 = chain2_launch(L);
   fork_chain2(L);
-  CUDA_OK(cudaMemcpyAsync(W2.zf, rhs, vbytes, cudaMemcpyDeviceToDevice, L2.st));
+  CUDA_OK(cudaMemcpyAsync(W2.zf + voff, rhs + voff, vbytes, cudaMemcpyDeviceToDevice, L2.st));
   for (int t = last; t > k; --t) fwd(L2, W2, t, t - 1);
   for (int t = 0; t < k; ++t) fwd(L, W, t, t + 1);
   join_chain2(L);
@@ -1027,6 +1043,22 @@ void with_chain2(inla_model *mdl, Launch &L) {
   L.st2 = mdl->stream2;
   L.ev_fork = mdl->ev_fork;
   L.ev_join = mdl->ev_join;
+  L.gst = mdl->stream3;
+  L.gst2 = mdl->stream4;
+  L.gev_fork = mdl->ev_fork2;
+  L.gev_join = mdl->ev_join2;
+  L.gev_gfork = mdl->ev_gfork;
+  L.gev_gjoin = mdl->ev_gjoin;
+}
+
+// Point groups: the first half of the wave's points in grp0, the rest in grp1 (each
+// restricted to the points active now).
+__global__ void group_mask_kernel(Work W) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= W.P) return;
+  const int h = (W.P + 1) / 2, a = W.active[b];
+  W.grp0[b] = (a && b < h) ? 1 : 0;
+  W.grp1[b] = (a && b >= h) ? 1 : 0;
 }
 
 template <typename R>
@@ -1074,9 +1106,33 @@ void run_wave_t(inla_model *mdl, Launch &L, const Work &W, const inla_eval_opts 
     }
   }
   if (M.lik == INLA_LIK_GAUSSIAN) {
-    factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC, split);
     k_rhs_gaussian(L, M, W);
-    solve<R>(L, M, W, W.rhs, W.x, split);
+    if (M.point_groups >= 2 && W.P >= 2 && L.gst && L.capturing) {
+      // two point groups, each factorised and solved on its own stream pair: the
+      // launches are latency-bound, so two groups of half the points overlap.  Only in a
+      // CUDA graph: the groups double the launches, which eager calls pay for on the host
+      // (the FD step went from 184 to 254 ms eager while its graph went from 130 to 127 ms)
+      group_mask_kernel<<<(W.P + 63) / 64, 64, 0, L.st>>>(W);
+      L.tick();
+      const int h = (W.P + 1) / 2;
+      Work W0 = W, W1 = W;
+      W0.active = W.grp0; W0.lo = 0; W0.hi = h;
+      W1.active = W.grp1; W1.lo = h; W1.hi = W.P;
+      Launch L1 = L;
+      L1.st = L.gst; L1.st2 = L.gst2; L1.ev_fork = L.gev_fork; L1.ev_join = L.gev_join;
+      L1.cur_id = -1;
+      CUDA_OK(cudaEventRecord(L.gev_gfork, L.st));
+      CUDA_OK(cudaStreamWaitEvent(L1.st, L.gev_gfork, 0));
+      factor<R>(L1, M, W1, ASM_QC, SC_LOGDET_QC, split);
+      solve<R>(L1, M, W1, W.rhs, W.x, split);
+      factor<R>(L, M, W0, ASM_QC, SC_LOGDET_QC, split);
+      solve<R>(L, M, W0, W.rhs, W.x, split);
+      CUDA_OK(cudaEventRecord(L.gev_gjoin, L1.st));
+      CUDA_OK(cudaStreamWaitEvent(L.st, L.gev_gjoin, 0));
+    } else {
+      factor<R>(L, M, W, ASM_QC, SC_LOGDET_QC, split);
+      solve<R>(L, M, W, W.rhs, W.x, split);
+    }
     k_obs_reduce(L, M, W, 0);
     k_quadforms(L, M, W, W.x, W.x, PT_XD_C, SC_TIP_XX);
     if (need_sel) {
@@ -1288,13 +1344,14 @@ void replay_graph(inla_model *mdl, int B, const double *theta_dev, const inla_ev
     if (e.B == B && e.grad == opts->grad && e.prior == opts->prior_mode && e.precision == opts->precision &&
         e.want_mode == (opts->want_mode != 0) && e.want_marg_var == (opts->want_marg_var != 0) &&
         e.fd_eps == opts->fd_eps && e.max_newton == opts->max_newton && e.newton_tol == opts->newton_tol &&
-        e.time_parts == mdl->M.time_parts && e.ws == mdl->ws && e.bb == mdl->bb)
+        e.time_parts == mdl->M.time_parts && e.point_groups == mdl->M.point_groups && e.ws == mdl->ws &&
+        e.bb == mdl->bb)
       g = &e;
   if (!g) {
     inla_model::GraphEntry e{};
     e.B = B; e.grad = opts->grad; e.prior = opts->prior_mode; e.precision = opts->precision;
     e.want_mode = opts->want_mode != 0; e.want_marg_var = opts->want_marg_var != 0; e.fd_eps = opts->fd_eps;
-    e.max_newton = opts->max_newton; e.newton_tol = opts->newton_tol; e.time_parts = mdl->M.time_parts;
+    e.max_newton = opts->max_newton; e.newton_tol = opts->newton_tol; e.time_parts = mdl->M.time_parts; e.point_groups = mdl->M.point_groups;
     e.ws = mdl->ws; e.bb = mdl->bb;
     const size_t bytes = rup(32 * B, 256) + rup(8 * B, 256) + rup(32 * B, 256) + 2 * rup(4 * B, 256) +
                          2 * rup(8 * n * B, 256);
@@ -1685,6 +1742,13 @@ int inla_set_time_partition(inla_model *model, int parts) {
   return guarded([&] {
     if (!model || (parts != 1 && parts != 2)) throw ApiError(INLA_ERR_ARG, "model is NULL or parts not 1 / 2");
     model->M.time_parts = parts;   // the graph cache is keyed on it; the workspace grows on demand
+  });
+}
+
+int inla_set_point_groups(inla_model *model, int groups) {
+  return guarded([&] {
+    if (!model || (groups != 1 && groups != 2)) throw ApiError(INLA_ERR_ARG, "model is NULL or groups not 1 / 2");
+    model->M.point_groups = groups;
   });
 }
 

@@ -78,6 +78,8 @@ struct DevModel {
   double prior_mean[4], prior_sd[4];
   double tau_b_fixed;
   double nb_size;                // negative binomial size r (0 for the other likelihoods)
+  int point_groups;              // 2: a Gaussian wave's factorisation and mode run as two point
+                                 // groups on two stream pairs (1: one group)
   int time_parts;                // 2: factorisations without a selected inversion split the time
                                  // chain at its middle block into two chains (1: one chain)
 };
@@ -119,6 +121,8 @@ struct Work {
   int *iters;            // [P]
   int *qsrep;            // [P]  earlier point of the wave whose Q_s this point shares (or itself)
   int *any_active;       // [1]
+  int *grp0, *grp1;      // [P]  activity masks of two point groups factorised concurrently
+  int lo, hi;            // points [lo, hi) that a pass's whole-array copies cover (hi = 0: all)
   // Poisson
   double *eta, *mu, *qobs, *wobs;        // [P][m] eta, weight b''(eta), a_i^T Sigma a_i, adjoint weights
   double *AtAp;          // [P][n_t][nnz]
@@ -193,6 +197,10 @@ struct Launch {
   // from st and join it back (null: no second chain)
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the second point group's stream pair and events, and the events that fork it from st
+  // and join it back (null: one group)
+  cudaStream_t gst = nullptr, gst2 = nullptr;
+  cudaEvent_t gev_fork = nullptr, gev_join = nullptr, gev_gfork = nullptr, gev_gjoin = nullptr;
   int cur_id = -1;
   double cur_units = 0.0;
   cudaEvent_t cur_a = nullptr;

@@ -140,4 +140,5 @@ def test_null_arguments(lib):
     assert C.load_probe().inla_measure_fp64_peak(0, 0, None) == C.INLA_ERR_ARG
     assert lib.inla_set_wait_limit(0.0) == C.INLA_ERR_ARG
     assert lib.inla_set_time_partition(None, 2) == C.INLA_ERR_ARG
+    assert lib.inla_set_point_groups(None, 2) == C.INLA_ERR_ARG
     lib.inla_model_destroy(None)

@@ -176,3 +176,26 @@ def test_workspace_holds_a_second_chain(pkg):
     assert all(b > a for a, b in zip(w1, w2))
     with pytest.raises(Exception):
         model.set_time_partition(3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_point_groups_are_bit_identical(pkg, precision):
+    # two point groups (first and second half of the wave) factorised concurrently on two
+    # stream pairs: every point's arithmetic is the one-group arithmetic, eager and in a graph
+    mdl = build("tpg", 6, 9, 2, 800, "gaussian", seed=8)
+    th = thetas(mdl, 3, seed=4)
+    model = pkg.Model(mdl)
+    # the groups run inside CUDA graphs; eager calls keep one group
+    for kw in (dict(grad="fd", use_graph=True), dict(grad="none", want_mode=True, use_graph=True),
+               dict(grad="adjoint", want_marg_var=True, use_graph=True)):
+        model.set_point_groups(1)
+        a = model.eval(cuda(th), precision=precision, **kw)
+        model.set_point_groups(2)
+        b = model.eval(cuda(th), precision=precision, **kw)
+        torch.cuda.synchronize()
+        for key in ("f", "grad", "x_mode", "marg_var", "status"):
+            if key in a:
+                assert torch.equal(a[key], b[key]), (kw, key)
+    with pytest.raises(Exception):
+        model.set_point_groups(3)
+
