@@ -18,6 +18,9 @@ kernels as the steps:
       Sigma_IJ = delta_IJ L_II^-T L_II^-1 - L_II^-T sum_{K > I, L_KI != 0} L_KI^T Sigma_KJ,
     run from the bottom-right block to the top-left, computing only the
     blocks on the pattern of L (Sec. 2.4.2).
+  * one level of nested dissection of the time chain (Sec. 3.3): the same
+    factorisation, substitution and selected inversion in the split order
+    (cholesky_split, solve_split, selinv_split).
 Then f(theta), x*, diag(Q_c^-1) and the gradient for both likelihoods.
 
 The gradient is the adjoint form: for a Gaussian likelihood
@@ -164,6 +167,129 @@ def selinv(L):
         Linv = sla.solve_triangular(Lt, I, lower=True)
         Stt = Linv.T @ Linv - sla.solve_triangular(Lt, acc_tt, lower=True, trans="T")
         S.D[t] = 0.5 * (Stt + Stt.T)
+    return S
+
+
+# ---------------------------------------------------------------- one level of nested dissection
+#
+# Sec. 3.3: a nested-dissection order splits a matrix into two independent parts joined
+# by a separator; the parts are factorised independently, then the separator, and the
+# partial inverse runs the other way (the separator's entries first).  On the time chain
+# one level of it takes block k as the separator: blocks 0..k-1 are eliminated in order
+# towards k, blocks n_t-1..k+1 in reverse order towards k, then block k, then the tip.
+# Every block keeps one neighbour that is eliminated after it (t + 1 on the first part,
+# t - 1 on the second, none for k), so the factor has no fill outside the BTA pattern; it
+# is the Cholesky factor of the matrix with its time blocks permuted into that order.
+
+
+def split_order(n_t, k):
+    """The elimination order of the split chain and, per block, the neighbour eliminated
+    after it (None for the separator)."""
+    order = list(range(k)) + list(range(n_t - 1, k, -1)) + [k]
+    nxt = {t: (t + 1 if t < k else t - 1) for t in range(n_t) if t != k}
+    nxt[k] = None
+    return order, nxt
+
+
+def _coupling(Qb, t, s):
+    """Block (s, t) of the BTA matrix for neighbours s = t +- 1."""
+    return Qb.B[t] if s == t + 1 else Qb.B[s].T
+
+
+def cholesky_split(Qb, k):
+    """Block Cholesky in the split order.  Returns (factor, log|Q|); the factor holds
+    L_t (F.D[t]), L_{nxt(t), t} (F.C[t]), L_{a,t} (F.R[t]) and L_a (F.T)."""
+    n_t, n_s, n_b = Qb.n_t, Qb.n_s, Qb.n_b
+    order, nxt = split_order(n_t, k)
+    F = Blocks(n_t, n_s, n_b)
+    F.C = [None] * n_t
+    D = [d.copy() for d in Qb.D]
+    R = [r.copy() for r in Qb.R]
+    T = Qb.T.copy()
+    logdet = 0.0
+    for t in order:
+        Lt = np.linalg.cholesky(D[t])
+        F.D[t] = Lt
+        logdet += 2.0 * float(np.sum(np.log(np.diag(Lt))))
+        s = nxt[t]
+        if s is not None:
+            F.C[t] = sla.solve_triangular(Lt, _coupling(Qb, t, s).T, lower=True).T
+            D[s] = D[s] - F.C[t] @ F.C[t].T
+        F.R[t] = sla.solve_triangular(Lt, R[t].T, lower=True).T if n_b else np.zeros((0, n_s))
+        if n_b:
+            if s is not None:
+                R[s] = R[s] - F.R[t] @ F.C[t].T
+            T = T - F.R[t] @ F.R[t].T
+    F.T = np.linalg.cholesky(T) if n_b else np.zeros((0, 0))
+    if n_b:
+        logdet += 2.0 * float(np.sum(np.log(np.diag(F.T))))
+    F.order, F.nxt = order, nxt
+    return F, logdet
+
+
+def solve_split(F, b):
+    """x with (L L^T) x = b for the split factor: forward substitution in the split
+    order, the tip, then backward substitution in the reverse order."""
+    n_t, n_s, n_b = F.n_t, F.n_s, F.n_b
+    N = n_t * n_s
+    blk = lambda v, t: v[t * n_s:(t + 1) * n_s]
+    r = b.astype(float).copy()
+    z = [None] * n_t
+    for t in F.order:
+        z[t] = sla.solve_triangular(F.D[t], blk(r, t), lower=True)
+        s = F.nxt[t]
+        if s is not None:
+            r[s * n_s:(s + 1) * n_s] -= F.C[t] @ z[t]
+        if n_b:
+            r[N:] -= F.R[t] @ z[t]
+    x = np.empty(N + n_b)
+    if n_b:
+        za = sla.solve_triangular(F.T, r[N:], lower=True)
+        x[N:] = sla.solve_triangular(F.T, za, lower=True, trans="T")
+    for t in reversed(F.order):
+        rhs = z[t].copy()
+        s = F.nxt[t]
+        if s is not None:
+            rhs -= F.C[t].T @ blk(x, s)
+        if n_b:
+            rhs -= F.R[t].T @ x[N:]
+        x[t * n_s:(t + 1) * n_s] = sla.solve_triangular(F.D[t], rhs, lower=True, trans="T")
+    return x
+
+
+def selinv_split(F):
+    """Selected inverse (Eq. sel_inv_cov in block form) in the reverse split order: the
+    tip, the separator, then both parts outwards.  Returns BTA blocks (S.B[t] = block
+    (t+1, t))."""
+    n_t, n_s, n_b = F.n_t, F.n_s, F.n_b
+    S = Blocks(n_t, n_s, n_b)
+    off = {}                       # Sigma_{nxt(t), t}
+    if n_b:
+        Ti = sla.solve_triangular(F.T, np.eye(n_b), lower=True)
+        S.T = Ti.T @ Ti
+    else:
+        S.T = np.zeros((0, 0))
+    I = np.eye(n_s)
+    for t in reversed(F.order):
+        Lt, s = F.D[t], F.nxt[t]
+        # sum over the blocks K eliminated after t with L_{K,t} != 0: K in {nxt(t), a}
+        acc_a = F.R[t].T @ S.T if n_b else np.zeros((n_s, 0))
+        acc_s = None
+        if s is not None:
+            acc_s = F.C[t].T @ S.D[s]
+            if n_b:
+                acc_s = acc_s + F.R[t].T @ S.R[s]
+                acc_a = acc_a + F.C[t].T @ S.R[s].T
+        S.R[t] = (-sla.solve_triangular(Lt, acc_a, lower=True, trans="T")).T
+        acc_tt = F.R[t].T @ S.R[t] if n_b else np.zeros((n_s, n_s))
+        if acc_s is not None:
+            off[t] = (-sla.solve_triangular(Lt, acc_s, lower=True, trans="T")).T     # Sigma_{s,t}
+            acc_tt = acc_tt + F.C[t].T @ off[t]
+        Linv = sla.solve_triangular(Lt, I, lower=True)
+        Stt = Linv.T @ Linv - sla.solve_triangular(Lt, acc_tt, lower=True, trans="T")
+        S.D[t] = 0.5 * (Stt + Stt.T)
+    for t in range(n_t - 1):       # block (t+1, t) from whichever of the pair was eliminated first
+        S.B[t] = off[t] if F.nxt[t] == t + 1 else off[t + 1].T
     return S
 
 

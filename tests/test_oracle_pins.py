@@ -206,6 +206,48 @@ def test_bta_factor_equals_dense_factor():
     assert np.allclose(bta.solve(Lb, b), np.linalg.solve(Qc.toarray(), b), rtol=1e-11, atol=1e-11)
 
 
+@pytest.mark.parametrize("n_t,k,n_b", [(3, 1, 2), (5, 2, 2), (6, 3, 1), (6, 1, 0), (7, 5, 2)])
+def test_split_order_factor_is_the_dense_factor_of_the_permuted_matrix(n_t, k, n_b):
+    # one level of nested dissection of the time chain (Sec. 3.3): the block algorithm
+    # in the split order equals the dense Cholesky factor of Q_c with its time blocks
+    # permuted into that order (no fill outside the pattern), and its log-determinant,
+    # solve and selected inverse equal the dense definitions
+    mdl = small(n_t=n_t, nx=3, n_b=n_b, m=40 * n_t, seed=n_t + k)
+    A = M.obs_matrix(mdl)
+    Qc = (M.prior_Q(mdl, mdl.theta_true) + 2.3 * (A.T @ A)).tocsr()
+    blocks, _ = bta.from_sparse(Qc, mdl.n_t, mdl.n_s, mdl.n_b)
+    F, ld = bta.cholesky_split(blocks, k)
+    n_s, N = mdl.n_s, mdl.n_t * mdl.n_s
+    order, nxt = bta.split_order(n_t, k)
+    assert sorted(order) == list(range(n_t)) and order[-1] == k
+    perm = np.concatenate([np.arange(t * n_s, (t + 1) * n_s) for t in order] + [np.arange(N, N + n_b)])
+    Qd = Qc.toarray()
+    Lp = np.linalg.cholesky(Qd[np.ix_(perm, perm)])
+    pos = {t: i for i, t in enumerate(order)}
+    blk = lambda i, j: Lp[i * n_s:(i + 1) * n_s, j * n_s:(j + 1) * n_s]
+    for t in range(n_t):
+        assert np.allclose(F.D[t], blk(pos[t], pos[t]), atol=1e-12)
+        assert np.allclose(F.R[t], Lp[N:, pos[t] * n_s:(pos[t] + 1) * n_s], atol=1e-12)
+        later = [u for u in range(n_t) if pos[u] > pos[t]]
+        for u in later:
+            want = F.C[t] if nxt[t] == u else 0.0
+            assert np.allclose(blk(pos[u], pos[t]), want, atol=1e-12), (t, u)   # no fill
+    if n_b:
+        assert np.allclose(F.T, Lp[N:, N:], atol=1e-12)
+    assert np.isclose(ld, np.linalg.slogdet(Qd)[1], rtol=1e-13)
+    b = np.random.default_rng(1).normal(size=mdl.n)
+    assert np.allclose(bta.solve_split(F, b), np.linalg.solve(Qd, b), rtol=1e-11, atol=1e-11)
+    S = bta.selinv_split(F)
+    Sinv, _ = bta.from_sparse(sp.csr_matrix(np.linalg.inv(Qd)), mdl.n_t, mdl.n_s, mdl.n_b)
+    for t in range(n_t):
+        assert np.allclose(S.D[t], Sinv.D[t], rtol=1e-10, atol=1e-12)
+        assert np.allclose(S.R[t], Sinv.R[t], rtol=1e-10, atol=1e-12)
+        if t < n_t - 1:
+            assert np.allclose(S.B[t], Sinv.B[t], rtol=1e-10, atol=1e-12)
+    if n_b:
+        assert np.allclose(S.T, Sinv.T, rtol=1e-10, atol=1e-12)
+
+
 def test_kronecker_logdet_identity():
     for n_t, nx, n_b in ((1, 4, 0), (5, 5, 3), (8, 6, 2)):
         mdl = build("k", n_t, nx, n_b, 20)
