@@ -290,6 +290,18 @@ L2_NOTE_LARGE = "working set (GBs of factor storage per step) exceeds L2; no flu
 L2_NOTE_FLUSH = "working set below 2x L2: a 512 MiB buffer is rewritten before each timed step (outside its events)"
 
 
+def block_cholesky_rate(mdl, points, step_s, peak_dmma):
+    """The step as a block-Cholesky rate: the textbook BTA Cholesky's flops (per point and
+    time step 7/3 n_s^3 for POTRF, TRSM and SYRK of the n_s x n_s blocks) over the whole step
+    time, which also holds the mode solve and the rest of f: a lower bound on the
+    factorisation's own rate.  The library inverts its Schur blocks instead (n_p^3 flops per
+    time step), so this counts the work a Cholesky-based implementation would do."""
+    flops = points * mdl.n_t * (7.0 / 3.0) * float(mdl.n_s) ** 3
+    rate = flops / step_s / 1e12
+    return {"textbook_equivalent": rate, "vs_fp64_dmma_peak": rate / peak_dmma if peak_dmma else None,
+            "definition": "points x n_t x 7/3 n_s^3 flops per step / step time (the whole step)"}
+
+
 def config_dict(cfg, world, grad=None, precision=None, points=9, l2=L2_NOTE_LARGE):
     from synth import CONFIGS
     c = CONFIGS[cfg]
@@ -785,6 +797,7 @@ def main():
                 "grad_mode": grad,
                 "errors_vs_oracle": errors,
                 "forms": forms,
+                "block_cholesky_tflops": block_cholesky_rate(mdl, points, elapsed / args.steps, peak_dmma),
                 "measured_peaks_tflops": {"fp64_fma": peak_fp64, "fp64_dmma": peak_dmma, "fp32_fma": peak_fp32,
                                           "tf32x3_tensor_from_bf16_sustained": tf32x3_peak},
                 "kernels": dict({k: {"ms_sampled": v[0], "launches_sampled": v[1],
